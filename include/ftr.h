@@ -1,0 +1,187 @@
+/*
+ * ftr.h -- C ABI of the GB300 volumetric Fourier-transform reconstruction.
+ *
+ * The library implements, on one CUDA GPU (sm_103a), the per-frame
+ * reconstruction of Section III of Alexiadis et al., "An Integrated Platform
+ * for Live 3D Human Reconstruction and Motion Capturing" (IEEE TCSVT 2017,
+ * arXiv 1712.03084):
+ *
+ *   splat oriented points into a gradient field V         (Sec. III-B, eq. 1-2)
+ *   forward 3D FFT of V_x, V_y, V_z                       (Sec. III-B)
+ *   integration filter F(w) = j w / |w|^2, component sum  (Sec. III-B)
+ *   inverse 3D FFT -> indicator A                         (Sec. III-B)
+ *   level L = mean of A at the input samples              (Sec. III-B)
+ *   marching cubes on A = L -> mesh                       (Sec. III-B, [35])
+ *   per-vertex visibility, weights W_k, UVs               (Sec. III-C)
+ *
+ * Conventions shared by every entry point
+ *   - Pointers marked "host or device" may point to device memory (cudaMalloc,
+ *     torch CUDA tensors, managed memory) or to host memory (pinned or
+ *     pageable); the library tells them apart with cudaPointerGetAttributes
+ *     and stages host data through its own device buffers.  All arrays are
+ *     C-contiguous float32 unless stated otherwise.
+ *   - Every call is ordered on the context's stream.  Calls that return data
+ *     to the host (iso_level_out, mesh counts, host output buffers) wait for
+ *     the stream; the others only enqueue work.
+ *   - Inputs are caller-owned and only read.  Mesh buffers are context-owned
+ *     and stay valid until the next ftr_solve / ftr_reset / ftr_destroy.
+ *   - Errors: a negative ftr_status, with a message from ftr_last_error().
+ *     The context stays usable after FTR_EINVAL.
+ *   - A context is used by one host thread at a time.
+ *
+ * Grid: n = (n_x, n_y, n_z), each n_c in {32, 48, 64, 96, 128, 192, 256, 384,
+ * 512}; the field is indexed x-fastest (x + n_x (y + n_y z)).  Node q sits at
+ * the cell centre p(q) = b_min + (q + 1/2) h with h_c = (b_max,c - b_min,c) / n_c.
+ * A point is accepted iff t = (X - b_min) / h - 1/2 satisfies 1 <= t_c < n_c - 2
+ * on every axis, i.e. its whole 4^3 splat stencil lies inside the grid; other
+ * points are dropped and counted (not an error).
+ */
+#ifndef FTR_H
+#define FTR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ftr_ctx ftr_ctx;
+
+typedef enum {
+    FTR_OK = 0,
+    FTR_EINVAL = -1,    /* bad argument; nothing was enqueued                   */
+    FTR_ENOMEM = -2,    /* device allocation failed                             */
+    FTR_ECUDA = -3,     /* a CUDA call failed; the context may be unusable      */
+    FTR_ETIMEOUT = -4,  /* reserved for bounded device waits                    */
+    FTR_ESTATE = -5     /* call out of order (e.g. extract before solve)        */
+} ftr_status;
+
+enum { FTR_SPLAT_WEIGHTED = 0, FTR_SPLAT_SIMPLE = 1 };
+enum { FTR_PREC_FP32 = 0 };
+
+typedef struct {
+    float sigma1_scale;   /* sigma1 = scale * half voxel diagonal (Sec. III-B); default 1   */
+    float sigma2_ratio2;  /* sigma2^2 / sigma1^2 (Sec. III-B: 3/2); default 1.5              */
+    int splat_mode;       /* FTR_SPLAT_WEIGHTED eq.(1)(2) | FTR_SPLAT_SIMPLE nearest node   */
+    int precision;        /* FTR_PREC_FP32 (only value accepted)                             */
+    void* stream;         /* cudaStream_t to order all work on; NULL = context-owned stream  */
+} ftr_params;
+
+/* Fill *p with the defaults above. */
+void ftr_default_params(ftr_params* p);
+
+/*
+ * Create a context on the current CUDA device (Sec. III-B grid "inside the
+ * foreground object's bounding box", padded by the caller against circular
+ * convolution).  grid_n[3] = (n_x, n_y, n_z); bbox[6] = (min x, min y, min z,
+ * max x, max y, max z) in world units, max > min.  p may be NULL (defaults).
+ * Allocates every device buffer the grid needs (about 60 bytes per voxel).
+ * Returns FTR_EINVAL for an unsupported grid, FTR_ENOMEM if allocation fails.
+ */
+int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ftr_ctx** out);
+
+/* Release every resource of the context (NULL is a no-op). */
+void ftr_destroy(ftr_ctx* ctx);
+
+/* Start a new frame: forget the points of the previous frame. */
+int ftr_reset(ftr_ctx* ctx);
+
+/*
+ * Add n oriented points to the current frame (Sec. III-A/III-B: the raw
+ * X_k(u), N_k(u), W_k(u) of one or more cameras; call once per camera or
+ * once for all).  points, normals: n x 3 float32 (host or device);
+ * weights: n float32 (host or device), or NULL for W = 1.  The points are
+ * copied; the splat itself (eq. 1-2) runs in ftr_solve.  n = 0 is allowed.
+ */
+int ftr_splat(ftr_ctx* ctx, const float* points, const float* normals, const float* weights, int64_t n);
+
+/*
+ * Run the reconstruction of Sec. III-B on the points added since the last
+ * ftr_reset: splat eq.(1)(2) (or the simple nearest-node splat), forward 3D
+ * FFT of the three components, filter j w / |w|^2 with the components summed,
+ * inverse 3D FFT into A, and L = mean of trilinear A over the accepted points
+ * (0 when none).  If iso_level_out is not NULL, waits and stores L there.
+ */
+int ftr_solve(ftr_ctx* ctx, double* iso_level_out);
+
+typedef struct {
+    const float* vertices;   /* device, n_vertices x 3 (world units)                    */
+    const float* normals;    /* device, n_vertices x 3 (unit, outward = -grad A)        */
+    const int32_t* tris;     /* device, n_tris x 3 vertex ids (outward winding)          */
+    int64_t n_vertices;
+    int64_t n_tris;
+} ftr_mesh;
+
+/*
+ * Marching cubes (Sec. III-B, [35]) on the last solved indicator at level L.
+ * A vertex lies on every grid edge whose end values straddle L (inside iff
+ * A >= L); vertex ids follow (node index, axis) order and triangles follow
+ * cell order, so the mesh is deterministic.  Waits for the stream (the counts
+ * are returned).  *out stays valid until the next solve/reset/destroy.
+ * FTR_ESTATE if nothing was solved.
+ */
+int ftr_extract_mesh(ftr_ctx* ctx, ftr_mesh* out);
+
+/* Copy the extracted mesh into caller buffers (host or device, any may be NULL). */
+int ftr_mesh_copy(ftr_ctx* ctx, float* vertices, float* normals, int32_t* tris);
+
+typedef struct {
+    int w, h;                 /* depth image size                                         */
+    float K[9];               /* depth intrinsics, row-major 3x3                          */
+    float world_to_cam[12];   /* [R | t], row-major 3x4: x_cam = R X + t                 */
+    int rgb_w, rgb_h;         /* RGB image size                                           */
+    float K_rgb[9];
+    float world_to_rgb[12];
+    const float* depth;       /* h x w metres, 0 = background (host or device)            */
+    const float* conf;        /* h x w confidence W_k (Sec. III-A) (host or device)       */
+    const uint8_t* rgb;       /* rgb_h x rgb_w x 3 (host or device)                       */
+} ftr_view;
+
+typedef struct {
+    float* weights;           /* n_vertices x k: W_k at the vertex, 0 if not visible       */
+    float* uv;                /* n_vertices x k x 2: RGB pixel coords, (-1,-1) if w = 0    */
+    uint8_t* rgb;             /* n_vertices x 3: sum_k w_k RGB_k(uv_k) / sum_k w_k         */
+    uint8_t* textured;        /* n_vertices: 1 iff sum_k w_k > 0                           */
+} ftr_tex;                    /* caller-owned; host or device; any member may be NULL     */
+
+/*
+ * Per-vertex texture data of Sec. III-C for the extracted mesh and k <= 8
+ * views.  Vertex X is visible in camera k iff x_cam.z > 0, its nearest depth
+ * pixel floor(u + 1/2), floor(v + 1/2) is inside the image and foreground
+ * (D > 0), and |D - x_cam.z| <= depth_tol; its weight is W_k at that pixel,
+ * set to 0 when the RGB projection falls outside the RGB image.  Projections
+ * and the blend are evaluated in float64; the colour is floor(c + 1/2).
+ */
+int ftr_texture(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out);
+
+/* Points added since the last reset, and how many of them were dropped. */
+int ftr_stats(const ftr_ctx* ctx, int64_t* points_in, int64_t* points_dropped);
+
+/* Message of the last error on this context (never NULL). */
+const char* ftr_last_error(const ftr_ctx* ctx);
+
+/* ---- inspection hooks used by the tests and the benchmark ------------------ */
+
+/* Dense V (3 x n_z x n_y x n_x float32, component-major) of the last solve. */
+int ftr_get_field_V(ftr_ctx* ctx, float* out);
+/* Indicator A (n_z x n_y x n_x float32) of the last solve. */
+int ftr_get_field_A(ftr_ctx* ctx, float* out);
+/* Replace A and L (e.g. with another implementation's) before ftr_extract_mesh. */
+int ftr_set_indicator(ftr_ctx* ctx, const float* A, double level);
+/* Cube class (uint8) per cell, (n_z-1) x (n_y-1) x (n_x-1), of the current A, L. */
+int ftr_get_cube_classes(ftr_ctx* ctx, uint8_t* out);
+/* The generated marching-cubes table: ntri[256] and tris[256 * 5 * 3] (-1 padded). */
+int ftr_mc_table(int32_t* ntri, int32_t* tris);
+/* Per-stage device time accounting (CUDA events on the context stream). */
+int ftr_profile_enable(ftr_ctx* ctx, int on);
+/* Accumulated ms and launch counts per stage since the last read; returns #stages. */
+int ftr_profile_read(ftr_ctx* ctx, double* ms, int64_t* counts, int max_stages);
+const char* ftr_stage_name(int stage);
+/* Number of kernels this context has launched so far. */
+int64_t ftr_launch_count(const ftr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTR_H */

@@ -1,0 +1,700 @@
+// C ABI of the reconstruction library: context lifetime, staging of host
+// inputs, the per-frame call sequence and the inspection hooks.  See
+// include/ftr.h for the contract of every entry point.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ftr_internal.h"
+
+using namespace ftr;
+
+namespace ftr {
+
+int set_err(ftr_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_fail(ftr_ctx* c, cudaError_t e, const char* what) {
+    return set_err(c, e == cudaErrorMemoryAllocation ? FTR_ENOMEM : FTR_ECUDA, "%s: %s (%s)", what,
+                   cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void prof_begin(ftr_ctx* c, int st) {
+    if (!c->prof) return;
+    if (c->ev_pending[st]) {
+        float ms = 0.f;
+        cudaEventSynchronize(c->ev_stop[st]);
+        if (cudaEventElapsedTime(&ms, c->ev_start[st], c->ev_stop[st]) == cudaSuccess) {
+            c->prof_ms[st] += ms;
+            c->prof_n[st] += 1;
+        }
+        c->ev_pending[st] = false;
+    }
+    cudaEventRecord(c->ev_start[st], c->stream);
+}
+
+void prof_end(ftr_ctx* c, int st) {
+    if (!c->prof) return;
+    cudaEventRecord(c->ev_stop[st], c->stream);
+    c->ev_pending[st] = true;
+}
+
+}  // namespace ftr
+
+namespace {
+
+const char* kStageNames[ST_COUNT] = {"ingest", "splat_bin", "splat_accum", "fft_x_fwd", "fft_y_fwd",
+                                     "fft_z_filter_inv", "fft_y_inv", "fft_x_inv", "level", "mc_count",
+                                     "mc_scan", "mc_emit", "mc_tris", "texture"};
+
+bool supported_n(int n) {
+    switch (n) {
+        case 32: case 48: case 64: case 96: case 128: case 192: case 256: case 384: case 512: return true;
+        default: return false;
+    }
+}
+
+// one-time per-device constant setup (twiddle constants of every FFT unit, MC table)
+std::mutex g_init_mu;
+bool g_dev_ready[64] = {};
+
+cudaError_t ensure_device_ready(int dev) {
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (dev >= 0 && dev < 64 && g_dev_ready[dev]) return cudaSuccess;
+    cudaError_t e;
+    if ((e = fft_fx_init()) != cudaSuccess) return e;
+    if ((e = fft_fy_init()) != cudaSuccess) return e;
+    if ((e = fft_fz_init()) != cudaSuccess) return e;
+    if ((e = fft_iy_init()) != cudaSuccess) return e;
+    if ((e = fft_ix_init()) != cudaSuccess) return e;
+    if ((e = mc_init()) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) g_dev_ready[dev] = true;
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t ensure_stage(ftr_ctx* c, void** buf, size_t* cap, size_t bytes) {
+    if (*cap >= bytes) return cudaSuccess;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(buf, want);
+    if (e == cudaSuccess) *cap = want;
+    return e;
+}
+
+cudaError_t grow_points(ftr_ctx* c, int64_t need) {
+    if (need <= c->pts.cap) return cudaSuccess;
+    int64_t cap = c->pts.cap ? c->pts.cap : 1 << 16;
+    while (cap < need) cap *= 2;
+    int4* b;
+    float4 *f, *n;
+    cudaError_t e;
+    if ((e = dalloc(&b, cap)) != cudaSuccess) return e;
+    if ((e = dalloc(&f, cap)) != cudaSuccess) { cudaFree(b); return e; }
+    if ((e = dalloc(&n, cap)) != cudaSuccess) { cudaFree(b); cudaFree(f); return e; }
+    if (c->n_pts > 0) {
+        cudaMemcpyAsync(b, c->pts.base, sizeof(int4) * c->n_pts, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(f, c->pts.frac, sizeof(float4) * c->n_pts, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(n, c->pts.nrm, sizeof(float4) * c->n_pts, cudaMemcpyDeviceToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    dfree(c->pts.base);
+    dfree(c->pts.frac);
+    dfree(c->pts.nrm);
+    c->pts.base = b;
+    c->pts.frac = f;
+    c->pts.nrm = n;
+    c->pts.cap = cap;
+    return cudaSuccess;
+}
+
+cudaError_t grow_entries(ftr_ctx* c, int64_t need) {
+    if (need <= c->cap_entries) return cudaSuccess;
+    int64_t cap = c->cap_entries ? c->cap_entries : 1 << 18;
+    while (cap < need) cap *= 2;
+    cudaStreamSynchronize(c->stream);
+    dfree(c->d_entries);
+    cudaError_t e = dalloc(&c->d_entries, cap);
+    if (e == cudaSuccess) c->cap_entries = cap;
+    return e;
+}
+
+void free_all(ftr_ctx* c) {
+    dfree(c->pts.base);
+    dfree(c->pts.frac);
+    dfree(c->pts.nrm);
+    dfree(c->d_dropped);
+    if (c->d_stage) cudaFree(c->d_stage);
+    dfree(c->d_brick_cnt);
+    dfree(c->d_brick_off);
+    dfree(c->d_brick_cursor);
+    dfree(c->d_brick_slot);
+    dfree(c->d_active);
+    dfree(c->d_meta);
+    dfree(c->d_entries);
+    dfree(c->d_vpool);
+    dfree(c->d_s0);
+    dfree(c->d_s1);
+    dfree(c->d_A);
+    for (int a = 0; a < 3; ++a) dfree(c->d_tw[a]);
+    dfree(c->d_level);
+    dfree(c->d_level_part);
+    dfree(c->d_mc_blk);
+    dfree(c->d_mc_off);
+    if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
+    dfree(c->d_mc_nodes);
+    dfree(c->d_verts);
+    dfree(c->d_vnrm);
+    dfree(c->d_tris);
+    if (c->d_tex_stage) cudaFree(c->d_tex_stage);
+    for (int s = 0; s < ST_COUNT; ++s) {
+        if (c->ev_start[s]) cudaEventDestroy(c->ev_start[s]);
+        if (c->ev_stop[s]) cudaEventDestroy(c->ev_stop[s]);
+    }
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ftr_default_params(ftr_params* p) {
+    if (!p) return;
+    p->sigma1_scale = 1.0f;
+    p->sigma2_ratio2 = 1.5f;
+    p->splat_mode = FTR_SPLAT_WEIGHTED;
+    p->precision = FTR_PREC_FP32;
+    p->stream = nullptr;
+}
+
+int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ftr_ctx** out) {
+    if (!out) return FTR_EINVAL;
+    *out = nullptr;
+    if (!grid_n || !bbox) return FTR_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (!supported_n(grid_n[a])) return FTR_EINVAL;
+        if (!(bbox[3 + a] > bbox[a]) || !isfinite(bbox[a]) || !isfinite(bbox[3 + a])) return FTR_EINVAL;
+    }
+    ftr_params prm;
+    ftr_default_params(&prm);
+    if (p) prm = *p;
+    if (!(prm.sigma1_scale > 0.f) || !(prm.sigma2_ratio2 > 1.0f)) return FTR_EINVAL;
+    if (prm.splat_mode != FTR_SPLAT_WEIGHTED && prm.splat_mode != FTR_SPLAT_SIMPLE) return FTR_EINVAL;
+    if (prm.precision != FTR_PREC_FP32) return FTR_EINVAL;
+
+    ftr_ctx* c = new (std::nothrow) ftr_ctx();
+    if (!c) return FTR_ENOMEM;
+    c->p = prm;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) { delete c; return FTR_ECUDA; }
+    if ((e = ensure_device_ready(c->device)) != cudaSuccess) { delete c; return FTR_ECUDA; }
+
+    GridDev& g = c->g;
+    double diag2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = grid_n[a];
+        g.nb[a] = grid_n[a] / kBrick;
+        g.bmin[a] = (double)bbox[a];
+        g.h[a] = ((double)bbox[3 + a] - (double)bbox[a]) / grid_n[a];
+        g.inv_h[a] = 1.0 / g.h[a];
+        g.hf[a] = (float)g.h[a];
+        diag2 += g.h[a] * g.h[a];
+    }
+    const double s1 = (double)prm.sigma1_scale * 0.5 * sqrt(diag2);
+    const double s2 = sqrt((double)prm.sigma2_ratio2) * s1;
+    g.inv_s1sq = (float)(1.0 / (s1 * s1));
+    g.inv_s2sq = (float)(1.0 / (s2 * s2));
+    g.mode = prm.splat_mode;
+    g.v_scale = prm.splat_mode == FTR_SPLAT_WEIGHTED ? s2 / s1 : 1.0;
+    c->M = (int64_t)grid_n[0] * grid_n[1] * grid_n[2];
+    c->Mh = (int64_t)(grid_n[0] / 2 + 1) * grid_n[1] * grid_n[2];
+    c->n_bricks = g.nb[0] * g.nb[1] * g.nb[2];
+
+    if (prm.stream) {
+        c->stream = (cudaStream_t)prm.stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            delete c;
+            return FTR_ECUDA;
+        }
+        c->own_stream = true;
+    }
+#define ALLOC(ptr, n)                                       \
+    if ((e = dalloc(&(ptr), (size_t)(n))) != cudaSuccess) { \
+        free_all(c);                                        \
+        delete c;                                           \
+        return FTR_ENOMEM;                                  \
+    }
+    ALLOC(c->d_dropped, 1);
+    ALLOC(c->d_brick_cnt, c->n_bricks);
+    ALLOC(c->d_brick_off, c->n_bricks + 1);
+    ALLOC(c->d_brick_cursor, c->n_bricks);
+    ALLOC(c->d_brick_slot, c->n_bricks);
+    ALLOC(c->d_active, c->n_bricks);
+    ALLOC(c->d_meta, 4);
+    ALLOC(c->d_vpool, (size_t)c->n_bricks * 3 * kBrickVox);
+    ALLOC(c->d_s0, 3 * c->Mh);
+    ALLOC(c->d_s1, 2 * c->Mh);
+    ALLOC(c->d_A, c->M);
+    for (int a = 0; a < 3; ++a) ALLOC(c->d_tw[a], grid_n[a]);
+    c->level_blocks = 304;
+    ALLOC(c->d_level, 2);
+    ALLOC(c->d_level_part, 2 * c->level_blocks);
+    c->mc_blocks = (int)((c->M + kMcChunk - 1) / kMcChunk);
+    ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
+    ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
+#undef ALLOC
+    if ((e = cudaMallocHost((void**)&c->h_mc_tot, 4 * sizeof(int))) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return FTR_ENOMEM;
+    }
+    for (int a = 0; a < 3; ++a) {
+        const int n = grid_n[a];
+        std::vector<float2> tw(n);
+        for (int m = 0; m < n; ++m) {
+            const double ang = 2.0 * 3.14159265358979323846 * (double)m / (double)n;
+            tw[m] = make_float2((float)cos(ang), (float)(-sin(ang)));
+        }
+        if ((e = cudaMemcpy(c->d_tw[a], tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return FTR_ECUDA;
+        }
+    }
+    for (int s = 0; s < ST_COUNT; ++s) {
+        cudaEventCreate(&c->ev_start[s]);
+        cudaEventCreate(&c->ev_stop[s]);
+    }
+    cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
+    double zero2[2] = {0.0, 0.0};
+    cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return FTR_ECUDA;
+    }
+    *out = c;
+    return FTR_OK;
+}
+
+void ftr_destroy(ftr_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+int ftr_reset(ftr_ctx* c) {
+    if (!c) return FTR_EINVAL;
+    c->n_pts = 0;
+    c->points_in = 0;
+    c->solved = false;
+    c->meshed = false;
+    c->n_verts = c->n_tris = 0;
+    cudaError_t e = cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_reset");
+    return FTR_OK;
+}
+
+int ftr_splat(ftr_ctx* c, const float* points, const float* normals, const float* weights, int64_t n) {
+    if (!c) return FTR_EINVAL;
+    if (n < 0) return set_err(c, FTR_EINVAL, "ftr_splat: n < 0");
+    if (n == 0) return FTR_OK;
+    if (!points || !normals) return set_err(c, FTR_EINVAL, "ftr_splat: points and normals are required");
+    if (c->n_pts + n > (int64_t)0x3fffffff) return set_err(c, FTR_EINVAL, "ftr_splat: too many points per frame");
+    cudaError_t e;
+    if ((e = grow_points(c, c->n_pts + n)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat: point store");
+    const bool dp = is_device_ptr(points), dn = is_device_ptr(normals);
+    const bool dw = weights ? is_device_ptr(weights) : true;
+    const float* P = points;
+    const float* N = normals;
+    const float* W = weights;
+    if (!dp || !dn || !dw) {
+        const size_t need = sizeof(float) * (size_t)n * 7;
+        if ((e = ensure_stage(c, &c->d_stage, &c->stage_cap, need)) != cudaSuccess)
+            return cuda_fail(c, e, "ftr_splat: staging");
+        float* st = (float*)c->d_stage;
+        if (!dp) {
+            if ((e = cudaMemcpyAsync(st, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream)))
+                return cuda_fail(c, e, "ftr_splat: copy points");
+            P = st;
+        }
+        if (!dn) {
+            if ((e = cudaMemcpyAsync(st + 3 * n, normals, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream)))
+                return cuda_fail(c, e, "ftr_splat: copy normals");
+            N = st + 3 * n;
+        }
+        if (weights && !dw) {
+            if ((e = cudaMemcpyAsync(st + 6 * n, weights, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream)))
+                return cuda_fail(c, e, "ftr_splat: copy weights");
+            W = st + 6 * n;
+        }
+    }
+    prof_begin(c, ST_INGEST);
+    e = launch_ingest(c, P, N, W, n);
+    prof_end(c, ST_INGEST);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_splat: ingest");
+    c->n_pts += n;
+    c->points_in += n;
+    // the staging buffer is reused by the next call: keep host-staged calls ordered
+    if (!dp || !dn || !dw) {
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat");
+    }
+    return FTR_OK;
+}
+
+int ftr_solve(ftr_ctx* c, double* iso_level_out) {
+    if (!c) return FTR_EINVAL;
+    cudaError_t e;
+    // each point touches at most 8 bricks
+    if ((e = grow_entries(c, 8 * c->n_pts + 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: entries");
+    c->solved = false;
+    c->meshed = false;
+    if ((e = launch_splat(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: splat");
+    prof_begin(c, ST_FX);
+    e = launch_fx(c);
+    prof_end(c, ST_FX);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: fft x");
+    prof_begin(c, ST_FY);
+    e = launch_fy(c);
+    prof_end(c, ST_FY);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: fft y");
+    prof_begin(c, ST_FZ);
+    e = launch_fz(c);
+    prof_end(c, ST_FZ);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: fft z + filter");
+    prof_begin(c, ST_IY);
+    e = launch_iy(c);
+    prof_end(c, ST_IY);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: inverse y");
+    prof_begin(c, ST_IX);
+    e = launch_ix(c);
+    prof_end(c, ST_IX);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: inverse x");
+    prof_begin(c, ST_LEVEL);
+    e = launch_level(c);
+    prof_end(c, ST_LEVEL);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: level");
+    c->solved = true;
+    if (iso_level_out) {
+        if ((e = cudaMemcpyAsync(&c->level_host, c->d_level, sizeof(double), cudaMemcpyDeviceToHost, c->stream)))
+            return cuda_fail(c, e, "ftr_solve: level copy");
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve");
+        *iso_level_out = c->level_host;
+    }
+    return FTR_OK;
+}
+
+int ftr_extract_mesh(ftr_ctx* c, ftr_mesh* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_extract_mesh: nothing solved");
+    cudaError_t e;
+    if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: count");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
+    const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
+    if (na > c->cap_mc_nodes) {
+        dfree(c->d_mc_nodes);
+        int64_t cap = na + na / 2 + 1024;
+        if ((e = dalloc(&c->d_mc_nodes, cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: nodes");
+        c->cap_mc_nodes = cap;
+    }
+    if (nv > c->cap_verts) {
+        dfree(c->d_verts);
+        dfree(c->d_vnrm);
+        int64_t cap = nv + nv / 2 + 1024;
+        if ((e = dalloc(&c->d_verts, 3 * cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: vertices");
+        if ((e = dalloc(&c->d_vnrm, 3 * cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: normals");
+        c->cap_verts = cap;
+    }
+    if (nt > c->cap_tris) {
+        dfree(c->d_tris);
+        int64_t cap = nt + nt / 2 + 1024;
+        if ((e = dalloc(&c->d_tris, 3 * cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: tris");
+        c->cap_tris = cap;
+    }
+    c->n_verts = nv;
+    c->n_tris = nt;
+    if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
+    c->meshed = true;
+    out->vertices = c->d_verts;
+    out->normals = c->d_vnrm;
+    out->tris = c->d_tris;
+    out->n_vertices = nv;
+    out->n_tris = nt;
+    return FTR_OK;
+}
+
+int ftr_mesh_copy(ftr_ctx* c, float* vertices, float* normals, int32_t* tris) {
+    if (!c) return FTR_EINVAL;
+    if (!c->meshed) return set_err(c, FTR_ESTATE, "ftr_mesh_copy: no mesh");
+    cudaError_t e = cudaSuccess;
+    if (vertices && c->n_verts)
+        e = cudaMemcpyAsync(vertices, c->d_verts, sizeof(float) * 3 * c->n_verts, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && normals && c->n_verts)
+        e = cudaMemcpyAsync(normals, c->d_vnrm, sizeof(float) * 3 * c->n_verts, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && tris && c->n_tris)
+        e = cudaMemcpyAsync(tris, c->d_tris, sizeof(int32_t) * 3 * c->n_tris, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_mesh_copy");
+    return FTR_OK;
+}
+
+int ftr_texture(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_tex* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (k < 0 || k > kMaxViews || (k > 0 && !views)) return set_err(c, FTR_EINVAL, "ftr_texture: 0 <= k <= 8");
+    if (!c->meshed) return set_err(c, FTR_ESTATE, "ftr_texture: no mesh");
+    if (!(depth_tol >= 0.f)) return set_err(c, FTR_EINVAL, "ftr_texture: depth_tol < 0");
+    cudaError_t e;
+    ViewSet vs;
+    memset(&vs, 0, sizeof(vs));
+    vs.k = k;
+    // staging layout: per view depth | conf | rgb, then the outputs
+    size_t need = 0;
+    std::vector<size_t> offs(3 * k + 4);
+    for (int i = 0; i < k; ++i) {
+        const ftr_view& v = views[i];
+        if (v.w <= 0 || v.h <= 0 || v.rgb_w <= 0 || v.rgb_h <= 0 || !v.depth || !v.conf || !v.rgb)
+            return set_err(c, FTR_EINVAL, "ftr_texture: view %d incomplete", i);
+        offs[3 * i] = need;
+        need += is_device_ptr(v.depth) ? 0 : ((sizeof(float) * v.w * v.h + 255) & ~(size_t)255);
+        offs[3 * i + 1] = need;
+        need += is_device_ptr(v.conf) ? 0 : ((sizeof(float) * v.w * v.h + 255) & ~(size_t)255);
+        offs[3 * i + 2] = need;
+        need += is_device_ptr(v.rgb) ? 0 : (((size_t)3 * v.rgb_w * v.rgb_h + 255) & ~(size_t)255);
+    }
+    const int64_t nv = c->n_verts;
+    const bool hw = out->weights && !is_device_ptr(out->weights);
+    const bool huv = out->uv && !is_device_ptr(out->uv);
+    const bool hrgb = out->rgb && !is_device_ptr(out->rgb);
+    const bool htex = out->textured && !is_device_ptr(out->textured);
+    const size_t o_w = need;
+    need += hw ? ((sizeof(float) * nv * k + 255) & ~(size_t)255) : 0;
+    const size_t o_uv = need;
+    need += huv ? ((sizeof(float) * nv * k * 2 + 255) & ~(size_t)255) : 0;
+    const size_t o_rgb = need;
+    need += hrgb ? (((size_t)3 * nv + 255) & ~(size_t)255) : 0;
+    const size_t o_tex = need;
+    need += htex ? (((size_t)nv + 255) & ~(size_t)255) : 0;
+    if (need > 0 && (e = ensure_stage(c, &c->d_tex_stage, &c->tex_stage_cap, need)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_texture: staging");
+    char* st = (char*)c->d_tex_stage;
+    for (int i = 0; i < k; ++i) {
+        const ftr_view& v = views[i];
+        ViewDev& d = vs.v[i];
+        d.w = v.w;
+        d.h = v.h;
+        d.rgb_w = v.rgb_w;
+        d.rgb_h = v.rgb_h;
+        for (int j = 0; j < 9; ++j) {
+            d.K[j] = v.K[j];
+            d.Krgb[j] = v.K_rgb[j];
+        }
+        for (int j = 0; j < 12; ++j) {
+            d.RT[j] = v.world_to_cam[j];
+            d.RTrgb[j] = v.world_to_rgb[j];
+        }
+        d.depth = v.depth;
+        d.conf = v.conf;
+        d.rgb = v.rgb;
+        if (!is_device_ptr(v.depth)) {
+            float* dst = (float*)(st + offs[3 * i]);
+            if ((e = cudaMemcpyAsync(dst, v.depth, sizeof(float) * v.w * v.h, cudaMemcpyHostToDevice, c->stream)))
+                return cuda_fail(c, e, "ftr_texture: copy depth");
+            d.depth = dst;
+        }
+        if (!is_device_ptr(v.conf)) {
+            float* dst = (float*)(st + offs[3 * i + 1]);
+            if ((e = cudaMemcpyAsync(dst, v.conf, sizeof(float) * v.w * v.h, cudaMemcpyHostToDevice, c->stream)))
+                return cuda_fail(c, e, "ftr_texture: copy conf");
+            d.conf = dst;
+        }
+        if (!is_device_ptr(v.rgb)) {
+            uint8_t* dst = (uint8_t*)(st + offs[3 * i + 2]);
+            if ((e = cudaMemcpyAsync(dst, v.rgb, (size_t)3 * v.rgb_w * v.rgb_h, cudaMemcpyHostToDevice, c->stream)))
+                return cuda_fail(c, e, "ftr_texture: copy rgb");
+            d.rgb = dst;
+        }
+    }
+    float* w = hw ? (float*)(st + o_w) : out->weights;
+    float* uv = huv ? (float*)(st + o_uv) : out->uv;
+    uint8_t* rgb = hrgb ? (uint8_t*)(st + o_rgb) : out->rgb;
+    uint8_t* tex = htex ? (uint8_t*)(st + o_tex) : out->textured;
+    if ((e = launch_texture(c, vs, depth_tol, w, uv, rgb, tex)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_texture: kernel");
+    bool host_out = false;
+    if (hw && nv) { cudaMemcpyAsync(out->weights, w, sizeof(float) * nv * k, cudaMemcpyDeviceToHost, c->stream); host_out = true; }
+    if (huv && nv) { cudaMemcpyAsync(out->uv, uv, sizeof(float) * nv * k * 2, cudaMemcpyDeviceToHost, c->stream); host_out = true; }
+    if (hrgb && nv) { cudaMemcpyAsync(out->rgb, rgb, (size_t)3 * nv, cudaMemcpyDeviceToHost, c->stream); host_out = true; }
+    if (htex && nv) { cudaMemcpyAsync(out->textured, tex, (size_t)nv, cudaMemcpyDeviceToHost, c->stream); host_out = true; }
+    bool host_in = false;
+    for (int i = 0; i < k; ++i)
+        host_in = host_in || !is_device_ptr(views[i].depth) || !is_device_ptr(views[i].conf) ||
+                  !is_device_ptr(views[i].rgb);
+    if (host_out || host_in) {
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_texture");
+    }
+    return FTR_OK;
+}
+
+int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
+    if (!c) return FTR_EINVAL;
+    if (points_in) *points_in = c->points_in;
+    if (points_dropped) {
+        unsigned long long d = 0;
+        cudaError_t e = cudaMemcpyAsync(&d, c->d_dropped, sizeof(d), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return FTR_ECUDA;
+        *points_dropped = (int64_t)d;
+    }
+    return FTR_OK;
+}
+
+const char* ftr_last_error(const ftr_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int ftr_get_field_V(ftr_ctx* c, float* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_get_field_V: nothing solved");
+    cudaError_t e;
+    float* dst = out;
+    float* tmp = nullptr;
+    if (!is_device_ptr(out)) {
+        if ((e = cudaMalloc(&tmp, sizeof(float) * 3 * c->M)) != cudaSuccess) return cuda_fail(c, e, "get_field_V");
+        dst = tmp;
+    }
+    e = launch_dense_V(c, dst);
+    if (e == cudaSuccess && tmp)
+        e = cudaMemcpyAsync(out, tmp, sizeof(float) * 3 * c->M, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_get_field_V");
+    return FTR_OK;
+}
+
+int ftr_get_field_A(ftr_ctx* c, float* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_get_field_A: nothing solved");
+    cudaError_t e = cudaMemcpyAsync(out, c->d_A, sizeof(float) * c->M, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_get_field_A");
+    return FTR_OK;
+}
+
+int ftr_set_indicator(ftr_ctx* c, const float* A, double level) {
+    if (!c || !A) return FTR_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(c->d_A, A, sizeof(float) * c->M, cudaMemcpyDefault, c->stream);
+    double lv[2] = {level, 1.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_level, lv, sizeof(lv), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_set_indicator");
+    c->solved = true;
+    c->meshed = false;
+    return FTR_OK;
+}
+
+int ftr_get_cube_classes(ftr_ctx* c, uint8_t* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_get_cube_classes: nothing solved");
+    const size_t ncell = (size_t)(c->g.n[0] - 1) * (c->g.n[1] - 1) * (c->g.n[2] - 1);
+    cudaError_t e;
+    uint8_t* dst = out;
+    uint8_t* tmp = nullptr;
+    if (!is_device_ptr(out)) {
+        if ((e = cudaMalloc(&tmp, ncell)) != cudaSuccess) return cuda_fail(c, e, "get_cube_classes");
+        dst = tmp;
+    }
+    e = launch_mc_classes(c, dst);
+    if (e == cudaSuccess && tmp) e = cudaMemcpyAsync(out, tmp, ncell, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_get_cube_classes");
+    return FTR_OK;
+}
+
+int ftr_mc_table(int32_t* ntri, int32_t* tris) {
+    if (!ntri || !tris) return FTR_EINVAL;
+    mc_generate_table(ntri, tris);
+    return FTR_OK;
+}
+
+int ftr_profile_enable(ftr_ctx* c, int on) {
+    if (!c) return FTR_EINVAL;
+    c->prof = on != 0;
+    for (int s = 0; s < ST_COUNT; ++s) {
+        c->ev_pending[s] = false;
+        c->prof_ms[s] = 0.0;
+        c->prof_n[s] = 0;
+    }
+    return FTR_OK;
+}
+
+int ftr_profile_read(ftr_ctx* c, double* ms, int64_t* counts, int max_stages) {
+    if (!c) return FTR_EINVAL;
+    for (int s = 0; s < ST_COUNT; ++s) {
+        if (c->ev_pending[s]) {
+            float t = 0.f;
+            cudaEventSynchronize(c->ev_stop[s]);
+            if (cudaEventElapsedTime(&t, c->ev_start[s], c->ev_stop[s]) == cudaSuccess) {
+                c->prof_ms[s] += t;
+                c->prof_n[s] += 1;
+            }
+            c->ev_pending[s] = false;
+        }
+    }
+    for (int s = 0; s < ST_COUNT && s < max_stages; ++s) {
+        if (ms) ms[s] = c->prof_ms[s];
+        if (counts) counts[s] = c->prof_n[s];
+        c->prof_ms[s] = 0.0;
+        c->prof_n[s] = 0;
+    }
+    return ST_COUNT;
+}
+
+const char* ftr_stage_name(int s) {
+    if (s < 0 || s >= ST_COUNT) return "";
+    return kStageNames[s];
+}
+
+int64_t ftr_launch_count(const ftr_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

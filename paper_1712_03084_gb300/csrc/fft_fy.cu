@@ -1,0 +1,114 @@
+// Forward pass along y, with the x and y terms of the filter combined.
+//
+// Input: the x-pass half spectra [c][k_x][z][y] (j w_x already applied to
+// c = x).  Each CTA transforms 16 contiguous y lines (z0..z0+15 at one k_x)
+// of the three components.  Because the integration filter of Sec. III-B is
+// j (w . V^) / |w|^2 and w_y depends only on k_y, the x and y components can
+// be summed as soon as both are transformed along y:
+//   W(k_x, k_y, z) = Y[j w_x X V_x] + j w_y Y[X V_y]      (numerator w_y = 0 at Nyquist)
+// so only two fields leave this pass: W and Y[X V_z], both in the layout
+// [k_x][k_y][z] (z fastest) for the z pass.
+#include "fft_common.cuh"
+#include "ftr_internal.h"
+
+namespace ftr {
+namespace {
+
+constexpr int kLines = 16;
+
+template <int N>
+__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
+    k_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
+         const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta) {
+    using X = Xchg<N, kLines>;
+    extern __shared__ float2 smem[];
+    const int nz = g.n[2];
+    const int z0 = blockIdx.x * kLines;
+    const int kx = blockIdx.y;
+    const int tid = threadIdx.x;
+    // tiles outside the slab of touched bricks are zero; the z pass treats
+    // them as zero without reading, so nothing is read or written here
+    int zl, zh;
+    live_z_range(meta, zl, zh);
+    if (z0 < zl || z0 >= zh) return;
+    // step-1 mapping: element index fastest (contiguous y lines)
+    const int f1 = tid / X::NT, r1 = tid % X::NT;
+    // step-2 mapping: line index fastest (contiguous z in the output)
+    const int f2 = tid % kLines, i2 = tid / kLines;
+    const size_t out_base = (size_t)(z0 + f2) + (size_t)nz * ((size_t)N * kx);
+    // the transformed x component waits in shared memory (line index fastest)
+    float2* stash = smem + X::SIZE;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        if (r1 < X::N2) {
+            const float2* src = s0 + (size_t)c * Mh + (size_t)N * (z0 + f1 + (size_t)nz * kx);
+            float2 v[X::N1];
+#pragma unroll
+            for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = src[X::N2 * n1 + r1];
+            fft_step1<N, kLines, -1>(v, f1, r1, smem, tw);
+        }
+        __syncthreads();
+        float2 o[X::N2];
+        if (i2 < X::N1) fft_step2<N, kLines, -1>(o, f2, i2, smem);
+        __syncthreads();
+        if (i2 < X::N1) {
+            if (c == 0) {
+#pragma unroll
+                for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (kLines + 1) * (i2 + X::N1 * k2)] = o[k2];
+            } else if (c == 1) {
+#pragma unroll
+                for (int k2 = 0; k2 < X::N2; ++k2) {
+                    const int ky = i2 + X::N1 * k2;
+                    const float wy = (ky == N / 2) ? 0.f : wy_scale * (float)signed_bin(ky, N);
+                    const float2 w = stash[f2 + (kLines + 1) * ky];
+                    s1[out_base + (size_t)nz * ky] = make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x);
+                }
+            } else {
+#pragma unroll
+                for (int k2 = 0; k2 < X::N2; ++k2) {
+                    const int ky = i2 + X::N1 * k2;
+                    s1[Mh + out_base + (size_t)nz * ky] = o[k2];
+                }
+            }
+        }
+    }
+}
+
+template <int N>
+cudaError_t run_fy(ftr_ctx* c) {
+    using X = Xchg<N, kLines>;
+    const size_t smem = sizeof(float2) * (X::SIZE + (kLines + 1) * N);
+    static bool attr_done[64] = {};
+    if (!attr_done[c->device & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(k_fy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[c->device & 63] = true;
+    }
+    dim3 grid(c->g.n[2] / kLines, c->g.n[0] / 2 + 1);
+    const float wy_scale = (float)(2.0 * 3.14159265358979323846 / (c->g.n[1] * c->g.h[1]));
+    k_fy<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,
+                                                       c->d_meta);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fft_fy_init() { return upload_w96_table(); }
+
+cudaError_t launch_fy(ftr_ctx* c) {
+    switch (c->g.n[1]) {
+        case 32: return run_fy<32>(c);
+        case 48: return run_fy<48>(c);
+        case 64: return run_fy<64>(c);
+        case 96: return run_fy<96>(c);
+        case 128: return run_fy<128>(c);
+        case 192: return run_fy<192>(c);
+        case 256: return run_fy<256>(c);
+        case 384: return run_fy<384>(c);
+        case 512: return run_fy<512>(c);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ftr

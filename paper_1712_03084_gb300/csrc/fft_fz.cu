@@ -1,0 +1,126 @@
+// z pass: forward transform, integration filter, inverse transform, fused.
+//
+// Sec. III-B: A^(w) = j (w_x V^_x + w_y V^_y + w_z V^_z) / |w|^2, then the
+// inverse 3D FFT.  After the y pass two fields remain per (k_x, k_y, z):
+// W = j w_x V^_x + j w_y V^_y and V^_z (each transformed along x and y).  A CTA
+// takes 16 z lines (k_y0..k_y0+15 at one k_x), transforms both along z,
+// forms A^ = (W^ + j w_z V^_z^) / |w|^2 / M (numerator w_z = 0 at the Nyquist
+// bin, |k| = n/2 in the denominator, A^(0) = 0), and transforms A^ back along
+// z while it is still in registers.  The result overwrites the W line in
+// place.  z-planes outside the slab that the splat touched are zero and are
+// not read.
+#include "fft_common.cuh"
+#include "ftr_internal.h"
+
+namespace ftr {
+namespace {
+
+constexpr int kLines = 16;
+
+template <int N>
+__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
+    k_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
+         float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta) {
+    using X = Xchg<N, kLines>;
+    extern __shared__ float2 smem[];
+    const int ny = g.n[1], nx = g.n[0];
+    const int ky0 = blockIdx.x * kLines;
+    const int kx = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int f = tid / X::NT, r = tid % X::NT;
+    int zl, zh;
+    live_z_range(meta, zl, zh);
+    const size_t line = (size_t)N * ((size_t)(ky0 + f) + (size_t)ny * kx);
+    float2 xw[X::N2], xh[X::N2];
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+        if (r < X::N2) {
+            const float2* src = s1 + (size_t)c * Mh + line;
+            float2 v[X::N1];
+#pragma unroll
+            for (int n1 = 0; n1 < X::N1; ++n1) {
+                const int z = X::N2 * n1 + r;
+                v[n1] = (z >= zl && z < zh) ? src[z] : make_float2(0.f, 0.f);
+            }
+            fft_step1<N, kLines, -1>(v, f, r, smem, tw);
+        }
+        __syncthreads();
+        if (r < X::N1) {
+            if (c == 0)
+                fft_step2<N, kLines, -1>(xw, f, r, smem);
+            else
+                fft_step2<N, kLines, -1>(xh, f, r, smem);
+        }
+        __syncthreads();
+    }
+    if (r < X::N1) {
+        const int ky = ky0 + f;
+        const float wxd = wx_scale * (float)kx;                 // |k_x| <= n_x/2 already
+        const float wyd = wy_scale * (float)signed_bin(ky, ny);
+        const float base = wxd * wxd + wyd * wyd;
+#pragma unroll
+        for (int k2 = 0; k2 < X::N2; ++k2) {
+            const int kz = r + X::N1 * k2;
+            const float wzd = wz_scale * (float)signed_bin(kz, N);
+            const float wzn = (kz == N / 2) ? 0.f : wzd;
+            const float den = base + wzd * wzd;
+            const float s = den > 0.f ? inv_m / den : 0.f;
+            // S = W^ + j w_z V^_z
+            const float2 sv = make_float2(xw[k2].x - wzn * xh[k2].y, xw[k2].y + wzn * xh[k2].x);
+            xw[k2] = make_float2(sv.x * s, sv.y * s);
+        }
+        (void)nx;
+        fft_step1_swapped<N, kLines, +1>(xw, f, r, smem, tw);
+    }
+    __syncthreads();
+    if (r < X::N2) {
+        float2 o[X::N1];
+        fft_step2_swapped<N, kLines, +1>(o, f, r, smem);
+        float2* dst = s1 + line;
+#pragma unroll
+        for (int k2 = 0; k2 < X::N1; ++k2) dst[r + X::N2 * k2] = o[k2];
+    }
+}
+
+template <int N>
+cudaError_t run_fz(ftr_ctx* c) {
+    using X = Xchg<N, kLines>;
+    const size_t smem = sizeof(float2) * X::SIZE;
+    static bool attr_done[64] = {};
+    if (!attr_done[c->device & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(k_fz<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[c->device & 63] = true;
+    }
+    dim3 grid(c->g.n[1] / kLines, c->g.n[0] / 2 + 1);
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const float wx = (float)(two_pi / (c->g.n[0] * c->g.h[0]));
+    const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
+    const float wz = (float)(two_pi / (c->g.n[2] * c->g.h[2]));
+    const float inv_m = (float)(1.0 / (double)c->M);
+    k_fz<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
+                                                       c->d_meta);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fft_fz_init() { return upload_w96_table(); }
+
+cudaError_t launch_fz(ftr_ctx* c) {
+    switch (c->g.n[2]) {
+        case 32: return run_fz<32>(c);
+        case 48: return run_fz<48>(c);
+        case 64: return run_fz<64>(c);
+        case 96: return run_fz<96>(c);
+        case 128: return run_fz<128>(c);
+        case 192: return run_fz<192>(c);
+        case 256: return run_fz<256>(c);
+        case 384: return run_fz<384>(c);
+        case 512: return run_fz<512>(c);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ftr

@@ -1,0 +1,82 @@
+// Inverse pass along y (Sec. III-B inverse 3D FFT, second axis).
+//
+// Input: A^ transformed back along z, layout [k_x][k_y][z] (z fastest).  A CTA
+// takes 16 consecutive z at one k_x (contiguous 128-byte rows for every k_y),
+// transforms them along y and writes [k_x][z][y] (y fastest) for the final
+// complex-to-real x pass.
+#include "fft_common.cuh"
+#include "ftr_internal.h"
+
+namespace ftr {
+namespace {
+
+constexpr int kLines = 16;
+
+template <int N>
+__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
+    k_iy(GridDev g, const float2* __restrict__ src, float2* __restrict__ dst, const float2* __restrict__ tw) {
+    using X = Xchg<N, kLines>;
+    extern __shared__ float2 smem[];
+    const int nz = g.n[2];
+    const int z0 = blockIdx.x * kLines;
+    const int kx = blockIdx.y;
+    const int tid = threadIdx.x;
+    // step 1: line index fastest (the input is contiguous along z)
+    const int f1 = tid % kLines, j1 = tid / kLines;
+    if (j1 < X::N2) {
+        float2 v[X::N1];
+#pragma unroll
+        for (int n1 = 0; n1 < X::N1; ++n1) {
+            const int ky = X::N2 * n1 + j1;
+            v[n1] = src[(size_t)(z0 + f1) + (size_t)nz * ((size_t)ky + (size_t)N * kx)];
+        }
+        fft_step1<N, kLines, +1>(v, f1, j1, smem, tw);
+    }
+    __syncthreads();
+    // step 2: element index fastest (the output is contiguous along y)
+    const int f2 = tid / X::NT, i2 = tid % X::NT;
+    if (i2 < X::N1) {
+        float2 o[X::N2];
+        fft_step2<N, kLines, +1>(o, f2, i2, smem);
+        float2* out = dst + (size_t)N * ((size_t)(z0 + f2) + (size_t)nz * kx);
+#pragma unroll
+        for (int k2 = 0; k2 < X::N2; ++k2) out[i2 + X::N1 * k2] = o[k2];
+    }
+}
+
+template <int N>
+cudaError_t run_iy(ftr_ctx* c) {
+    using X = Xchg<N, kLines>;
+    const size_t smem = sizeof(float2) * X::SIZE;
+    static bool attr_done[64] = {};
+    if (!attr_done[c->device & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(k_iy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done[c->device & 63] = true;
+    }
+    dim3 grid(c->g.n[2] / kLines, c->g.n[0] / 2 + 1);
+    k_iy<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->d_s0, c->d_tw[1]);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fft_iy_init() { return upload_w96_table(); }
+
+cudaError_t launch_iy(ftr_ctx* c) {
+    switch (c->g.n[1]) {
+        case 32: return run_iy<32>(c);
+        case 48: return run_iy<48>(c);
+        case 64: return run_iy<64>(c);
+        case 96: return run_iy<96>(c);
+        case 128: return run_iy<128>(c);
+        case 192: return run_iy<192>(c);
+        case 256: return run_iy<256>(c);
+        case 384: return run_iy<384>(c);
+        case 512: return run_iy<512>(c);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ftr

@@ -1,0 +1,184 @@
+// Internal state and launch interfaces shared by the translation units of
+// the reconstruction library.  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ftr.h"
+
+namespace ftr {
+
+constexpr int kBrick = 8;                 // splat accumulation brick edge (nodes)
+constexpr int kBrickVox = kBrick * kBrick * kBrick;
+constexpr int kMaxViews = 8;
+constexpr int kMcChunk = 2048;            // nodes per marching-cubes CTA
+constexpr int kMcThreads = 256;           // 8 consecutive nodes per thread
+constexpr int kMaxTrisPerCase = 5;
+
+enum Stage {
+    ST_INGEST = 0,
+    ST_SPLAT_BIN,
+    ST_SPLAT_ACC,
+    ST_FX,
+    ST_FY,
+    ST_FZ,
+    ST_IY,
+    ST_IX,
+    ST_LEVEL,
+    ST_MC_COUNT,
+    ST_MC_SCAN,
+    ST_MC_EMIT,
+    ST_MC_TRIS,
+    ST_TEXTURE,
+    ST_COUNT
+};
+
+// Geometry handed to kernels by value.
+struct GridDev {
+    int n[3];
+    int nb[3];                 // bricks per axis
+    double bmin[3];
+    double h[3];
+    double inv_h[3];
+    float hf[3];
+    float inv_s1sq, inv_s2sq;  // 1/sigma1^2, 1/sigma2^2 (world units)
+    double v_scale;            // sigma2/sigma1 (weighted) or 1 (simple)
+    int mode;
+};
+
+// Per-point record written by the ingest kernel.
+//   base: floor(t) per axis, .w = flags (bit 0 accepted, bits 1..3 round-up
+//         of the nearest node per axis, i.e. floor(t + 1/2) - floor(t))
+//   frac: t - floor(t) per axis, .w = W
+//   nrm : N, .w unused
+struct PointStore {
+    int4* base = nullptr;
+    float4* frac = nullptr;
+    float4* nrm = nullptr;
+    int64_t cap = 0;
+};
+
+}  // namespace ftr
+
+struct ftr_ctx {
+    int device = 0;
+    ftr::GridDev g{};
+    int64_t M = 0;             // voxels
+    int64_t Mh = 0;            // half-spectrum bins (n_x/2 + 1) n_y n_z
+    ftr_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // points of the current frame
+    ftr::PointStore pts;
+    int64_t n_pts = 0;
+    int64_t points_in = 0;
+    unsigned long long* d_dropped = nullptr;
+    void* d_stage = nullptr;   // staging for host inputs
+    size_t stage_cap = 0;
+
+    // splat bricks
+    int n_bricks = 0;
+    int* d_brick_cnt = nullptr;
+    int* d_brick_off = nullptr;
+    int* d_brick_cursor = nullptr;
+    int* d_brick_slot = nullptr;
+    int* d_active = nullptr;
+    int* d_meta = nullptr;     // [0] active bricks, [1] entries, [2] min bz, [3] max bz
+    int* d_entries = nullptr;
+    int64_t cap_entries = 0;
+    float* d_vpool = nullptr;  // active bricks x 3 x 512 V values
+
+    // spectra and indicator
+    float2* d_s0 = nullptr;    // 3 x Mh  [kx][z][y]
+    float2* d_s1 = nullptr;    // 2 x Mh  [kx][ky][z]
+    float* d_A = nullptr;      // M       [z][y][x]
+    float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
+
+    // level
+    double* d_level = nullptr;     // [0] L, [1] accepted count
+    double* d_level_part = nullptr;
+    int level_blocks = 0;
+    bool solved = false;
+    double level_host = 0.0;
+
+    // marching cubes
+    int mc_blocks = 0;
+    int* d_mc_blk = nullptr;       // 3 x mc_blocks
+    int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
+    int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
+    int4* d_mc_nodes = nullptr;
+    int64_t cap_mc_nodes = 0;
+    float* d_verts = nullptr;
+    float* d_vnrm = nullptr;
+    int32_t* d_tris = nullptr;
+    int64_t cap_verts = 0, cap_tris = 0;
+    int64_t n_verts = 0, n_tris = 0;
+    bool meshed = false;
+
+    // texture staging (host views / outputs)
+    void* d_tex_stage = nullptr;
+    size_t tex_stage_cap = 0;
+
+    // profiling
+    bool prof = false;
+    cudaEvent_t ev_start[ftr::ST_COUNT] = {};
+    cudaEvent_t ev_stop[ftr::ST_COUNT] = {};
+    bool ev_pending[ftr::ST_COUNT] = {};
+    double prof_ms[ftr::ST_COUNT] = {};
+    int64_t prof_n[ftr::ST_COUNT] = {};
+    int64_t launches = 0;
+};
+
+namespace ftr {
+
+// error helpers (api.cu)
+int set_err(ftr_ctx* c, int code, const char* fmt, ...);
+int cuda_fail(ftr_ctx* c, cudaError_t e, const char* what);
+void prof_begin(ftr_ctx* c, int stage);
+void prof_end(ftr_ctx* c, int stage);
+
+// per translation unit one-time device setup
+cudaError_t fft_fx_init();
+cudaError_t fft_fy_init();
+cudaError_t fft_fz_init();
+cudaError_t fft_iy_init();
+cudaError_t fft_ix_init();
+cudaError_t mc_init();
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n);
+cudaError_t launch_splat(ftr_ctx* c);          // bin + accumulate into d_vpool
+cudaError_t launch_fx(ftr_ctx* c);
+cudaError_t launch_fy(ftr_ctx* c);
+cudaError_t launch_fz(ftr_ctx* c);
+cudaError_t launch_iy(ftr_ctx* c);
+cudaError_t launch_ix(ftr_ctx* c);
+cudaError_t launch_level(ftr_ctx* c);
+cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan; totals to h_mc_tot
+cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
+cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);
+cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev);
+
+struct ViewDev {
+    int w, h, rgb_w, rgb_h;
+    double K[9], RT[12], Krgb[9], RTrgb[12];
+    const float* depth;
+    const float* conf;
+    const uint8_t* rgb;
+};
+struct ViewSet {
+    int k;
+    ViewDev v[kMaxViews];
+};
+cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv,
+                           uint8_t* rgb, uint8_t* textured);
+
+// marching-cubes table (mc_table.cpp), generated from the face rule
+void mc_generate_table(int32_t ntri[256], int32_t tris[256 * kMaxTrisPerCase * 3]);
+
+}  // namespace ftr

@@ -1,0 +1,379 @@
+// Marching cubes on A at level L (Sec. III-B, [35]), scan-compacted.
+//
+// Corner bit = 1 iff A >= L, compared in float64 (A promoted).  A node owns the
+// grid edges toward +x, +y, +z; an edge carries a vertex when its two bits
+// differ.  Vertex ids are the rank of (node, axis) in linear node order and
+// triangles follow cell order then table order, so the mesh does not depend
+// on scheduling.  Three launches:
+//   count  one CTA per 2048 consecutive nodes: active nodes (owning a vertex
+//          or lower corner of a cell with triangles), vertices, triangles
+//   scan   one CTA: exclusive offsets of the per-CTA counts (+ totals)
+//   emit   same CTAs again: block-local scan, one 16-byte record per active
+//          node (node, edge bits | class << 8, first vertex, first triangle),
+//          vertex positions t = (L - A0)/(A1 - A0) in float64 and normals
+//          -grad A (central differences, one-sided at the border, lerped)
+//   tris   one thread per active node: triangle corners from the case table;
+//          an edge owned by another node is found by binary search in the
+//          sorted node records.
+#include <cuda_runtime.h>
+
+#include "ftr_internal.h"
+
+namespace ftr {
+namespace {
+
+__constant__ int c_ntri[256];
+__constant__ signed char c_tri[256][kMaxTrisPerCase][3];
+
+constexpr int kNodesPerThread = kMcChunk / kMcThreads;   // 8
+
+struct NodeInfo {
+    int flags;     // bit a: edge toward +a crosses
+    int cls;       // cube class, 0 if the node is not a cell's lower corner
+};
+
+__device__ __forceinline__ NodeInfo classify_node(const float* __restrict__ A, int64_t n, int x, int y, int z,
+                                                  const GridDev& g, double L) {
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const bool hx = x < nx - 1, hy = y < ny - 1, hz = z < nz - 1;
+    const int b0 = (double)A[n] >= L;
+    NodeInfo r;
+    r.flags = 0;
+    r.cls = 0;
+    const int bx = hx ? ((double)A[n + 1] >= L) : b0;
+    const int by = hy ? ((double)A[n + sy] >= L) : b0;
+    const int bz = hz ? ((double)A[n + sz] >= L) : b0;
+    r.flags = (bx != b0) | ((by != b0) << 1) | ((bz != b0) << 2);
+    if (hx && hy && hz) {
+        const int bxy = (double)A[n + 1 + sy] >= L;
+        const int bxz = (double)A[n + 1 + sz] >= L;
+        const int byz = (double)A[n + sy + sz] >= L;
+        const int bxyz = (double)A[n + 1 + sy + sz] >= L;
+        r.cls = b0 | (bx << 1) | (by << 2) | (bxy << 3) | (bz << 4) | (bxz << 5) | (byz << 6) | (bxyz << 7);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void node_xyz(int64_t n, const GridDev& g, int& x, int& y, int& z) {
+    x = (int)(n % g.n[0]);
+    const int64_t r = n / g.n[0];
+    y = (int)(r % g.n[1]);
+    z = (int)(r / g.n[1]);
+}
+
+// Block-wide exclusive scan of 3 ints (kMcThreads threads); returns totals.
+__device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int3 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, inc.x, o);
+        const int b = __shfl_up_sync(0xffffffffu, inc.y, o);
+        const int c = __shfl_up_sync(0xffffffffu, inc.z, o);
+        if (lane >= o) {
+            inc.x += a;
+            inc.y += b;
+            inc.z += c;
+        }
+    }
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int3 w = lane < kMcThreads / 32 ? sh[lane] : make_int3(0, 0, 0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, w.x, o);
+            const int b = __shfl_up_sync(0xffffffffu, w.y, o);
+            const int c = __shfl_up_sync(0xffffffffu, w.z, o);
+            if (lane >= o) {
+                w.x += a;
+                w.y += b;
+                w.z += c;
+            }
+        }
+        if (lane < kMcThreads / 32) sh[lane] = w;
+    }
+    __syncthreads();
+    const int3 before = wid ? sh[wid - 1] : make_int3(0, 0, 0);
+    total = sh[kMcThreads / 32 - 1];
+    __syncthreads();
+    return make_int3(before.x + inc.x - v.x, before.y + inc.y - v.y, before.z + inc.z - v.z);
+}
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
+                                                         const double* __restrict__ level, int64_t M,
+                                                         int* __restrict__ blk, int nblocks) {
+    __shared__ int3 sh[kMcThreads / 32];
+    const double L = level[0];
+    const int64_t n0 = (int64_t)blockIdx.x * kMcChunk + (int64_t)threadIdx.x * kNodesPerThread;
+    int3 cnt = make_int3(0, 0, 0);
+    for (int k = 0; k < kNodesPerThread; ++k) {
+        const int64_t n = n0 + k;
+        if (n >= M) break;
+        int x, y, z;
+        node_xyz(n, g, x, y, z);
+        const NodeInfo ni = classify_node(A, n, x, y, z, g, L);
+        const int nt = c_ntri[ni.cls];
+        cnt.x += (ni.flags != 0 || nt > 0);
+        cnt.y += __popc(ni.flags);
+        cnt.z += nt;
+    }
+    int3 tot;
+    block_scan3(cnt, tot, sh);
+    if (threadIdx.x == 0) {
+        blk[blockIdx.x] = tot.x;
+        blk[nblocks + blockIdx.x] = tot.y;
+        blk[2 * nblocks + blockIdx.x] = tot.z;
+    }
+}
+
+constexpr int kScanThreads = 1024;
+
+// Exclusive scan of the 3 per-CTA count arrays; totals to off[3 * (nb + 1) ..]
+__global__ void __launch_bounds__(kScanThreads) k_mc_scan(const int* __restrict__ blk, int nb, int* off,
+                                                          int* totals) {
+    __shared__ int sh[kScanThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int b0 = min(nb, t * per), b1 = min(nb, b0 + per);
+    for (int a = 0; a < 3; ++a) {
+        const int* src = blk + (size_t)a * nb;
+        int* dst = off + (size_t)a * (nb + 1);
+        int s = 0;
+        for (int b = b0; b < b1; ++b) s += src[b];
+        int inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) sh[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int w = sh[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += v;
+            }
+            sh[lane] = w;
+        }
+        __syncthreads();
+        int run = inc - s + (wid ? sh[wid - 1] : 0);
+        for (int b = b0; b < b1; ++b) {
+            dst[b] = run;
+            run += src[b];
+        }
+        if (t == kScanThreads - 1) {
+            dst[nb] = run;
+            totals[a] = run;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t n, int q, int nq, int64_t stride,
+                                           float inv_h) {
+    if (q == 0) return (A[n + stride] - A[n]) * inv_h;
+    if (q == nq - 1) return (A[n] - A[n - stride]) * inv_h;
+    return (A[n + stride] - A[n - stride]) * (0.5f * inv_h);
+}
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
+                                                        const double* __restrict__ level, int64_t M,
+                                                        const int* __restrict__ off, int nblocks,
+                                                        int4* __restrict__ nodes, float* __restrict__ verts,
+                                                        float* __restrict__ vnrm) {
+    __shared__ int3 sh[kMcThreads / 32];
+    const double L = level[0];
+    const int64_t n0 = (int64_t)blockIdx.x * kMcChunk + (int64_t)threadIdx.x * kNodesPerThread;
+    NodeInfo info[kNodesPerThread];
+    int3 cnt = make_int3(0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < kNodesPerThread; ++k) {
+        const int64_t n = n0 + k;
+        info[k].flags = 0;
+        info[k].cls = 0;
+        if (n < M) {
+            int x, y, z;
+            node_xyz(n, g, x, y, z);
+            info[k] = classify_node(A, n, x, y, z, g, L);
+        }
+        const int nt = c_ntri[info[k].cls];
+        cnt.x += (info[k].flags != 0 || nt > 0);
+        cnt.y += __popc(info[k].flags);
+        cnt.z += nt;
+    }
+    int3 tot;
+    int3 ex = block_scan3(cnt, tot, sh);
+    int ia = off[blockIdx.x] + ex.x;
+    int iv = off[(nblocks + 1) + blockIdx.x] + ex.y;
+    int it = off[2 * (nblocks + 1) + blockIdx.x] + ex.z;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t st[3] = {1, (int64_t)nx, (int64_t)nx * ny};
+    const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
+#pragma unroll
+    for (int k = 0; k < kNodesPerThread; ++k) {
+        const int nt = c_ntri[info[k].cls];
+        if (info[k].flags == 0 && nt == 0) continue;
+        const int64_t n = n0 + k;
+        nodes[ia] = make_int4((int)n, info[k].flags | (info[k].cls << 8), iv, it);
+        ++ia;
+        it += nt;
+        if (info[k].flags == 0) continue;
+        int q[3];
+        node_xyz(n, g, q[0], q[1], q[2]);
+        const int nn[3] = {nx, ny, nz};
+        float g0[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
+        for (int a = 0; a < 3; ++a) {
+            if (!((info[k].flags >> a) & 1)) continue;
+            const int64_t n1 = n + st[a];
+            const double a0 = A[n], a1 = A[n1];
+            const double t = (L - a0) / (a1 - a0);
+            int q1[3] = {q[0], q[1], q[2]};
+            q1[a] += 1;
+            float g1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
+            float p[3], nv[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
+                if (c == a) pc += t * g.h[c];
+                p[c] = (float)pc;
+                const float tf = (float)t;
+                nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
+            }
+            const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+            const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
+            verts[3 * (int64_t)iv + 0] = p[0];
+            verts[3 * (int64_t)iv + 1] = p[1];
+            verts[3 * (int64_t)iv + 2] = p[2];
+            vnrm[3 * (int64_t)iv + 0] = nv[0] * inv;
+            vnrm[3 * (int64_t)iv + 1] = nv[1] * inv;
+            vnrm[3 * (int64_t)iv + 2] = nv[2] * inv;
+            ++iv;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restrict__ nodes, int n_nodes,
+                                                 int32_t* __restrict__ tris) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_nodes) return;
+    const int4 rec = nodes[r];
+    const int cls = rec.y >> 8;
+    const int nt = c_ntri[cls];
+    if (nt == 0) return;
+    const int nx = g.n[0];
+    const int64_t sxy = (int64_t)nx * g.n[1];
+    for (int t = 0; t < nt; ++t) {
+        for (int j = 0; j < 3; ++j) {
+            const int e = c_tri[cls][t][j];
+            const int axis = e >> 2;
+            const int cu = e & 1, cv = (e >> 1) & 1;
+            // owner offset: the edge's fixed coordinates on the two other axes
+            int o[3] = {0, 0, 0};
+            if (axis == 0) {
+                o[1] = cu;
+                o[2] = cv;
+            } else if (axis == 1) {
+                o[0] = cu;
+                o[2] = cv;
+            } else {
+                o[0] = cu;
+                o[1] = cv;
+            }
+            const int64_t owner = (int64_t)rec.x + o[0] + (int64_t)nx * o[1] + sxy * o[2];
+            int4 orec = rec;
+            if (owner != rec.x) {
+                int lo = r + 1, hi = n_nodes - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((int64_t)nodes[mid].x < owner) lo = mid + 1; else hi = mid;
+                }
+                orec = nodes[lo];
+            }
+            const int below = (orec.y & 7) & ((1 << axis) - 1);
+            tris[3 * (int64_t)(rec.w + t) + j] = orec.z + __popc(below);
+        }
+    }
+}
+
+__global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const double* __restrict__ level,
+                             uint8_t* out) {
+    const int cx = g.n[0] - 1, cy = g.n[1] - 1, cz = g.n[2] - 1;
+    const int64_t ncell = (int64_t)cx * cy * cz;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell) return;
+    const int x = (int)(i % cx);
+    const int y = (int)((i / cx) % cy);
+    const int z = (int)(i / ((int64_t)cx * cy));
+    const int64_t n = x + (int64_t)g.n[0] * (y + (int64_t)g.n[1] * z);
+    out[i] = (uint8_t)classify_node(A, n, x, y, z, g, level[0]).cls;
+}
+
+}  // namespace
+
+cudaError_t mc_init() {
+    int32_t ntri[256];
+    int32_t tris[256 * kMaxTrisPerCase * 3];
+    mc_generate_table(ntri, tris);
+    signed char t8[256][kMaxTrisPerCase][3];
+    for (int c = 0; c < 256; ++c)
+        for (int t = 0; t < kMaxTrisPerCase; ++t)
+            for (int j = 0; j < 3; ++j) t8[c][t][j] = (signed char)tris[(c * kMaxTrisPerCase + t) * 3 + j];
+    cudaError_t e = cudaMemcpyToSymbol(c_ntri, ntri, sizeof(ntri));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_tri, t8, sizeof(t8));
+}
+
+cudaError_t launch_mc_count(ftr_ctx* c) {
+    prof_begin(c, ST_MC_COUNT);
+    k_mc_count<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->M, c->d_mc_blk,
+                                                          c->mc_blocks);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, ST_MC_COUNT);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, ST_MC_SCAN);
+    k_mc_scan<<<1, kScanThreads, 0, c->stream>>>(c->d_mc_blk, c->mc_blocks, c->d_mc_off,
+                                                c->d_mc_off + 3 * (c->mc_blocks + 1));
+    c->launches++;
+    e = cudaGetLastError();
+    prof_end(c, ST_MC_SCAN);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->h_mc_tot, c->d_mc_off + 3 * (c->mc_blocks + 1), 3 * sizeof(int),
+                           cudaMemcpyDeviceToHost, c->stream);
+}
+
+cudaError_t launch_mc_emit(ftr_ctx* c) {
+    prof_begin(c, ST_MC_EMIT);
+    k_mc_emit<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->M, c->d_mc_off,
+                                                         c->mc_blocks, c->d_mc_nodes, c->d_verts, c->d_vnrm);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    prof_end(c, ST_MC_EMIT);
+    if (e != cudaSuccess) return e;
+    const int n_nodes = c->h_mc_tot[0];
+    if (n_nodes > 0 && c->n_tris > 0) {
+        prof_begin(c, ST_MC_TRIS);
+        k_mc_tris<<<(n_nodes + 255) / 256, 256, 0, c->stream>>>(c->g, c->d_mc_nodes, n_nodes, c->d_tris);
+        c->launches++;
+        e = cudaGetLastError();
+        prof_end(c, ST_MC_TRIS);
+    }
+    return e;
+}
+
+cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev) {
+    const int64_t ncell = (int64_t)(c->g.n[0] - 1) * (c->g.n[1] - 1) * (c->g.n[2] - 1);
+    k_mc_classes<<<(unsigned)((ncell + 255) / 256), 256, 0, c->stream>>>(c->g, c->d_A, c->d_level, out_dev);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace ftr

@@ -1,0 +1,350 @@
+"""Python binding of the C ABI in include/ftr.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: all the reconstruction work runs in the CUDA kernels
+of libftr.so.  Arrays may be numpy arrays (host memory) or torch tensors
+(host or CUDA); they must be C-contiguous with the dtype the C ABI states.
+Loading fails loudly when the library has not been built: there is no CPU
+fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libftr.so")
+
+FTR_OK = 0
+FTR_SPLAT_WEIGHTED = 0
+FTR_SPLAT_SIMPLE = 1
+MAX_TRIS_PER_CASE = 5
+
+_lib = None
+
+
+class FtrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ftr error {code}: {msg}")
+        self.code = code
+
+
+class ftr_params(ctypes.Structure):
+    _fields_ = [("sigma1_scale", ctypes.c_float), ("sigma2_ratio2", ctypes.c_float),
+                ("splat_mode", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class ftr_mesh(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("normals", ctypes.c_void_p), ("tris", ctypes.c_void_p),
+                ("n_vertices", ctypes.c_int64), ("n_tris", ctypes.c_int64)]
+
+
+class ftr_view(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int), ("h", ctypes.c_int), ("K", ctypes.c_float * 9),
+                ("world_to_cam", ctypes.c_float * 12), ("rgb_w", ctypes.c_int), ("rgb_h", ctypes.c_int),
+                ("K_rgb", ctypes.c_float * 9), ("world_to_rgb", ctypes.c_float * 12),
+                ("depth", ctypes.c_void_p), ("conf", ctypes.c_void_p), ("rgb", ctypes.c_void_p)]
+
+
+class ftr_tex(ctypes.Structure):
+    _fields_ = [("weights", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
+                ("textured", ctypes.c_void_p)]
+
+
+# (name, restype, argtypes) of every exported symbol
+_SIGNATURES = [
+    ("ftr_default_params", None, [ctypes.POINTER(ftr_params)]),
+    ("ftr_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ftr_params), ctypes.POINTER(ctypes.c_void_p)]),
+    ("ftr_destroy", None, [ctypes.c_void_p]),
+    ("ftr_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("ftr_splat", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_int64]),
+    ("ftr_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("ftr_extract_mesh", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_mesh)]),
+    ("ftr_mesh_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_texture", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
+                                   ctypes.POINTER(ftr_tex)]),
+    ("ftr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_get_field_A", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_set_indicator", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    ("ftr_get_cube_classes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_mc_table", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("ftr_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("ftr_stage_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("ftr_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+]
+
+EXPORTED = [s[0] for s in _SIGNATURES]
+
+
+def load():
+    """Load libftr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1712_03084_gb300.build.build() "
+                           "(the reconstruction has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype=None):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {a.dtype}")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None:
+            want = {np.float32: "torch.float32", np.uint8: "torch.uint8", np.int32: "torch.int32"}[dtype]
+            if str(a.dtype) != want:
+                raise TypeError(f"expected {want}, got {a.dtype}")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _check(code, ctx=None):
+    if code != FTR_OK:
+        msg = load().ftr_last_error(ctx).decode() if ctx else ""
+        raise FtrError(code, msg)
+
+
+# ---------------------------------------------------------------- C-named calls
+
+def ftr_default_params():
+    p = ftr_params()
+    load().ftr_default_params(ctypes.byref(p))
+    return p
+
+
+def ftr_create(grid_n, bbox, params=None):
+    lib = load()
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid_n])
+    b = (ctypes.c_float * 6)(*[float(v) for v in bbox])
+    out = ctypes.c_void_p()
+    code = lib.ftr_create(g, b, ctypes.byref(params) if params is not None else None, ctypes.byref(out))
+    if code != FTR_OK:
+        raise FtrError(code, "ftr_create failed (unsupported grid, bad box or no device memory)")
+    return out.value
+
+
+def ftr_destroy(ctx):
+    load().ftr_destroy(ctx)
+
+
+def ftr_reset(ctx):
+    _check(load().ftr_reset(ctx), ctx)
+
+
+def ftr_splat(ctx, points, normals, weights=None):
+    n = int(points.shape[0])
+    _check(load().ftr_splat(ctx, _ptr(points, np.float32), _ptr(normals, np.float32),
+                            _ptr(weights, np.float32), n), ctx)
+
+
+def ftr_solve(ctx, want_level=True):
+    lv = ctypes.c_double(0.0)
+    _check(load().ftr_solve(ctx, ctypes.byref(lv) if want_level else None), ctx)
+    return lv.value if want_level else None
+
+
+def ftr_extract_mesh(ctx):
+    m = ftr_mesh()
+    _check(load().ftr_extract_mesh(ctx, ctypes.byref(m)), ctx)
+    return m
+
+
+def ftr_mesh_copy(ctx, vertices=None, normals=None, tris=None):
+    _check(load().ftr_mesh_copy(ctx, _ptr(vertices, np.float32), _ptr(normals, np.float32),
+                                _ptr(tris, np.int32)), ctx)
+
+
+def make_view(view):
+    """ftr_view from a dict(depth, conf, rgb, K, world_to_cam, K_rgb, world_to_rgb)."""
+    v = ftr_view()
+    depth, conf, rgb = view["depth"], view["conf"], view["rgb"]
+    v.h, v.w = int(depth.shape[0]), int(depth.shape[1])
+    v.rgb_h, v.rgb_w = int(rgb.shape[0]), int(rgb.shape[1])
+    v.K[:] = [float(x) for x in np.asarray(view["K"], dtype=np.float32).reshape(-1)]
+    v.world_to_cam[:] = [float(x) for x in np.asarray(view["world_to_cam"], dtype=np.float32).reshape(-1)]
+    v.K_rgb[:] = [float(x) for x in np.asarray(view["K_rgb"], dtype=np.float32).reshape(-1)]
+    v.world_to_rgb[:] = [float(x) for x in np.asarray(view["world_to_rgb"], dtype=np.float32).reshape(-1)]
+    v.depth = _ptr(depth, np.float32)
+    v.conf = _ptr(conf, np.float32)
+    v.rgb = _ptr(rgb, np.uint8)
+    return v
+
+
+def ftr_texture(ctx, views, depth_tol, weights=None, uv=None, rgb=None, textured=None):
+    arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
+    t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
+    _check(load().ftr_texture(ctx, arr, len(views), float(depth_tol), ctypes.byref(t)), ctx)
+
+
+def ftr_stats(ctx):
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().ftr_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
+
+
+def ftr_last_error(ctx):
+    return load().ftr_last_error(ctx).decode()
+
+
+def ftr_get_field_V(ctx, out):
+    _check(load().ftr_get_field_V(ctx, _ptr(out, np.float32)), ctx)
+
+
+def ftr_get_field_A(ctx, out):
+    _check(load().ftr_get_field_A(ctx, _ptr(out, np.float32)), ctx)
+
+
+def ftr_set_indicator(ctx, A, level):
+    _check(load().ftr_set_indicator(ctx, _ptr(A, np.float32), float(level)), ctx)
+
+
+def ftr_get_cube_classes(ctx, out):
+    _check(load().ftr_get_cube_classes(ctx, _ptr(out, np.uint8)), ctx)
+
+
+def ftr_mc_table():
+    ntri = np.zeros(256, np.int32)
+    tris = np.zeros(256 * MAX_TRIS_PER_CASE * 3, np.int32)
+    _check(load().ftr_mc_table(ntri.ctypes.data, tris.ctypes.data))
+    return ntri, tris.reshape(256, MAX_TRIS_PER_CASE, 3)
+
+
+def ftr_profile_enable(ctx, on=True):
+    _check(load().ftr_profile_enable(ctx, 1 if on else 0), ctx)
+
+
+def ftr_profile_read(ctx):
+    ms = np.zeros(64, np.float64)
+    cnt = np.zeros(64, np.int64)
+    n = load().ftr_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data, 64)
+    if n < 0:
+        _check(n, ctx)
+    return {ftr_stage_name(s): (float(ms[s]), int(cnt[s])) for s in range(n)}
+
+
+def ftr_stage_name(s):
+    return load().ftr_stage_name(int(s)).decode()
+
+
+def ftr_launch_count(ctx):
+    return int(load().ftr_launch_count(ctx))
+
+
+# ---------------------------------------------------------------- convenience
+
+class Context:
+    """Owns one ftr_ctx; methods forward to the C-named calls above."""
+
+    def __init__(self, grid_n, bbox, sigma1_scale=1.0, sigma2_ratio2=1.5, splat_mode=FTR_SPLAT_WEIGHTED,
+                 stream=None):
+        p = ftr_default_params()
+        p.sigma1_scale = sigma1_scale
+        p.sigma2_ratio2 = sigma2_ratio2
+        p.splat_mode = splat_mode
+        p.stream = stream
+        self.grid_n = tuple(int(v) for v in grid_n)
+        self.bbox = tuple(float(v) for v in bbox)
+        self.h = ftr_create(self.grid_n, self.bbox, p)
+
+    def close(self):
+        if self.h:
+            ftr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        ftr_reset(self.h)
+
+    def splat(self, points, normals, weights=None):
+        ftr_splat(self.h, points, normals, weights)
+
+    def solve(self, want_level=True):
+        return ftr_solve(self.h, want_level)
+
+    def extract_mesh(self):
+        return ftr_extract_mesh(self.h)
+
+    def mesh_numpy(self):
+        m = ftr_extract_mesh(self.h)
+        v = np.zeros((m.n_vertices, 3), np.float32)
+        n = np.zeros((m.n_vertices, 3), np.float32)
+        t = np.zeros((m.n_tris, 3), np.int32)
+        ftr_mesh_copy(self.h, v, n, t)
+        return {"vertices": v, "normals": n, "tris": t}
+
+    def texture_numpy(self, views, depth_tol, n_vertices):
+        k = len(views)
+        w = np.zeros((n_vertices, k), np.float32)
+        uv = np.zeros((n_vertices, k, 2), np.float32)
+        rgb = np.zeros((n_vertices, 3), np.uint8)
+        tex = np.zeros(n_vertices, np.uint8)
+        ftr_texture(self.h, views, depth_tol, w, uv, rgb, tex)
+        return {"weights": w, "uv": uv, "rgb": rgb, "textured": tex}
+
+    def stats(self):
+        return ftr_stats(self.h)
+
+    def field_V(self):
+        nx, ny, nz = self.grid_n
+        out = np.zeros((3, nz, ny, nx), np.float32)
+        ftr_get_field_V(self.h, out)
+        return out
+
+    def field_A(self):
+        nx, ny, nz = self.grid_n
+        out = np.zeros((nz, ny, nx), np.float32)
+        ftr_get_field_A(self.h, out)
+        return out
+
+    def set_indicator(self, A, level):
+        ftr_set_indicator(self.h, np.ascontiguousarray(A, dtype=np.float32), level)
+
+    def cube_classes(self):
+        nx, ny, nz = self.grid_n
+        out = np.zeros((nz - 1, ny - 1, nx - 1), np.uint8)
+        ftr_get_cube_classes(self.h, out)
+        return out
+
+    def profile_enable(self, on=True):
+        ftr_profile_enable(self.h, on)
+
+    def profile_read(self):
+        return ftr_profile_read(self.h)
+
+    def launch_count(self):
+        return ftr_launch_count(self.h)

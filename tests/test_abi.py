@@ -1,0 +1,64 @@
+"""The C-ABI library loads, exports every declared entry point, and its
+host-generated marching-cubes table equals the oracle's (no GPU needed)."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mc_table
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1712_03084_gb300 import build, ftr
+    build.build()
+    return ftr.load()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ftr.h")) as f:
+        txt = f.read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ftr_[a-z_A-Z0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1712_03084_gb300 import ftr
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(ftr.EXPORTED) == names
+
+
+def test_library_table_matches_oracle_table(lib):
+    from paper_1712_03084_gb300 import ftr
+    ntri, tris = ftr.ftr_mc_table()
+    ont, otr = mc_table.table()
+    assert np.array_equal(ntri, ont)
+    assert otr.shape[1] <= ftr.MAX_TRIS_PER_CASE
+    for c in range(256):
+        assert np.array_equal(tris[c, :ntri[c]], otr[c, :ont[c]]), c
+        assert np.all(tris[c, ntri[c]:] == -1)
+
+
+def test_create_rejects_bad_grids_without_gpu(lib):
+    from paper_1712_03084_gb300 import ftr
+    for grid, box in [((100, 64, 64), (0, 0, 0, 1, 1, 1)), ((64, 64, 64), (0, 0, 0, 0, 1, 1)),
+                      ((64, 64, 16), (0, 0, 0, 1, 1, 1))]:
+        with pytest.raises(ftr.FtrError):
+            ftr.ftr_create(grid, box)
+
+
+def test_product_path_does_not_touch_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1712_03084_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                with open(os.path.join(dirpath, f)) as fh:
+                    src = fh.read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", src).replace("the oracle", ""), f
