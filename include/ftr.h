@@ -164,6 +164,10 @@ const char* ftr_last_error(const ftr_ctx* ctx);
 
 /* Dense V (3 x n_z x n_y x n_x float32, component-major) of the last solve. */
 int ftr_get_field_V(ftr_ctx* ctx, float* out);
+/* Replace the splat: the next ftr_solve transforms this dense V (3 x n_z x n_y
+ * x n_x float32, host or device) instead of splatting points; L is then 0
+ * (no samples).  Cleared by ftr_reset. */
+int ftr_set_field_V(ftr_ctx* ctx, const float* V);
 /* Indicator A (n_z x n_y x n_x float32) of the last solve. */
 int ftr_get_field_A(ftr_ctx* ctx, float* out);
 /* Replace A and L (e.g. with another implementation's) before ftr_extract_mesh. */

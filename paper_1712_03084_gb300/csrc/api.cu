@@ -327,6 +327,7 @@ int ftr_reset(ftr_ctx* c) {
     c->n_pts = 0;
     c->points_in = 0;
     c->solved = false;
+    c->v_external = false;
     c->meshed = false;
     c->n_verts = c->n_tris = 0;
     cudaError_t e = cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
@@ -388,7 +389,9 @@ int ftr_solve(ftr_ctx* c, double* iso_level_out) {
     if ((e = grow_entries(c, 8 * c->n_pts + 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: entries");
     c->solved = false;
     c->meshed = false;
-    if ((e = launch_splat(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: splat");
+    if (!c->v_external) {
+        if ((e = launch_splat(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: splat");
+    }
     prof_begin(c, ST_FX);
     e = launch_fx(c);
     prof_end(c, ST_FX);
@@ -617,6 +620,28 @@ int ftr_get_field_A(ftr_ctx* c, float* out) {
     cudaError_t e = cudaMemcpyAsync(out, c->d_A, sizeof(float) * c->M, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_get_field_A");
+    return FTR_OK;
+}
+
+int ftr_set_field_V(ftr_ctx* c, const float* V) {
+    if (!c || !V) return FTR_EINVAL;
+    cudaError_t e;
+    const float* src = V;
+    float* tmp = nullptr;
+    if (!is_device_ptr(V)) {
+        if ((e = cudaMalloc(&tmp, sizeof(float) * 3 * c->M)) != cudaSuccess) return cuda_fail(c, e, "set_field_V");
+        if ((e = cudaMemcpyAsync(tmp, V, sizeof(float) * 3 * c->M, cudaMemcpyHostToDevice, c->stream))) {
+            cudaFree(tmp);
+            return cuda_fail(c, e, "set_field_V");
+        }
+        src = tmp;
+    }
+    e = launch_load_dense_V(c, src);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_set_field_V");
+    c->n_pts = 0;
+    c->v_external = true;
     return FTR_OK;
 }
 

@@ -104,6 +104,7 @@ struct ftr_ctx {
     double* d_level_part = nullptr;
     int level_blocks = 0;
     bool solved = false;
+    bool v_external = false;   // V was set with ftr_set_field_V: solve skips the splat
     double level_host = 0.0;
 
     // marching cubes
@@ -163,6 +164,7 @@ cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan; totals to h_mc_t
 cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
 cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);
 cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev);
+cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);
 
 struct ViewDev {
     int w, h, rgb_w, rgb_h;

@@ -278,6 +278,23 @@ __global__ void k_dense_V(GridDev g, const int* __restrict__ slot, const float* 
         out[c * M + q] = s >= 0 ? vpool[(size_t)s * 3 * kBrickVox + c * kBrickVox + li] : 0.f;
 }
 
+__global__ void k_load_dense_V(GridDev g, const float* __restrict__ V, int64_t M, int* slot, int* active,
+                               float* vpool) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= M) return;
+    const int x = (int)(q % g.n[0]);
+    const int y = (int)((q / g.n[0]) % g.n[1]);
+    const int z = (int)(q / ((int64_t)g.n[0] * g.n[1]));
+    const int b = (x >> 3) + g.nb[0] * ((y >> 3) + g.nb[1] * (z >> 3));
+    const int li = (x & 7) + 8 * ((y & 7) + 8 * (z & 7));
+    if (li == 0) {
+        slot[b] = b;
+        active[b] = b;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vpool[(size_t)b * 3 * kBrickVox + c * kBrickVox + li] = V[c * M + q];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -321,6 +338,16 @@ cudaError_t launch_splat(ftr_ctx* c) {
     c->launches++;
     prof_end(c, ST_SPLAT_ACC);
     return cudaGetLastError();
+}
+
+cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev) {
+    k_load_dense_V<<<blocks_for(c->M, 256), 256, 0, c->stream>>>(c->g, V_dev, c->M, c->d_brick_slot, c->d_active,
+                                                                 c->d_vpool);
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int meta[4] = {c->n_bricks, 0, 0, c->g.nb[2] - 1};
+    return cudaMemcpyAsync(c->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, c->stream);
 }
 
 cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev) {

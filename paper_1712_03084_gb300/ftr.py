@@ -70,6 +70,7 @@ _SIGNATURES = [
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_field_A", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_indicator", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     ("ftr_get_cube_classes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_mc_table", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -218,6 +219,10 @@ def ftr_get_field_A(ctx, out):
     _check(load().ftr_get_field_A(ctx, _ptr(out, np.float32)), ctx)
 
 
+def ftr_set_field_V(ctx, V):
+    _check(load().ftr_set_field_V(ctx, _ptr(V, np.float32)), ctx)
+
+
 def ftr_set_indicator(ctx, A, level):
     _check(load().ftr_set_indicator(ctx, _ptr(A, np.float32), float(level)), ctx)
 
@@ -330,6 +335,9 @@ class Context:
         out = np.zeros((nz, ny, nx), np.float32)
         ftr_get_field_A(self.h, out)
         return out
+
+    def set_field_V(self, V):
+        ftr_set_field_V(self.h, np.ascontiguousarray(V, dtype=np.float32))
 
     def set_indicator(self, A, level):
         ftr_set_indicator(self.h, np.ascontiguousarray(A, dtype=np.float32), level)
