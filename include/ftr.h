@@ -174,6 +174,10 @@ int ftr_get_field_A(ftr_ctx* ctx, float* out);
 int ftr_set_indicator(ftr_ctx* ctx, const float* A, double level);
 /* Cube class (uint8) per cell, (n_z-1) x (n_y-1) x (n_x-1), of the current A, L. */
 int ftr_get_cube_classes(ftr_ctx* ctx, uint8_t* out);
+/* Raw copy of an internal spectrum buffer after ftr_solve: which = 0 the
+ * x-pass / inverse-y buffer (3 x (n_x/2+1) n_y n_z complex64), which = 1 the
+ * y-pass / z-pass buffer (2 x (n_x/2+1) n_y n_z complex64). */
+int ftr_debug_buffer(ftr_ctx* ctx, int which, void* out, int64_t bytes);
 /* The generated marching-cubes table: ntri[256] and tris[256 * 5 * 3] (-1 padded). */
 int ftr_mc_table(int32_t* ntri, int32_t* tris);
 /* Per-stage device time accounting (CUDA events on the context stream). */

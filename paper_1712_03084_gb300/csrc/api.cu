@@ -676,6 +676,23 @@ int ftr_get_cube_classes(ftr_ctx* c, uint8_t* out) {
     return FTR_OK;
 }
 
+int ftr_debug_buffer(ftr_ctx* c, int which, void* out, int64_t bytes) {
+    if (!c || !out) return FTR_EINVAL;
+    const void* src = nullptr;
+    int64_t have = 0;
+    switch (which) {
+        case 0: src = c->d_s0; have = (int64_t)sizeof(float2) * 3 * c->Mh; break;
+        case 1: src = c->d_s1; have = (int64_t)sizeof(float2) * 2 * c->Mh; break;
+        default: return set_err(c, FTR_EINVAL, "ftr_debug_buffer: unknown buffer %d", which);
+    }
+    if (bytes > have) return set_err(c, FTR_EINVAL, "ftr_debug_buffer: %lld > %lld bytes", (long long)bytes,
+                                     (long long)have);
+    cudaError_t e = cudaMemcpyAsync(out, src, (size_t)bytes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_debug_buffer");
+    return FTR_OK;
+}
+
 int ftr_mc_table(int32_t* ntri, int32_t* tris) {
     if (!ntri || !tris) return FTR_EINVAL;
     mc_generate_table(ntri, tris);

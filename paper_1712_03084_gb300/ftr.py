@@ -73,6 +73,7 @@ _SIGNATURES = [
     ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_indicator", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     ("ftr_get_cube_classes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_debug_buffer", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
     ("ftr_mc_table", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ftr_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -229,6 +230,10 @@ def ftr_set_indicator(ctx, A, level):
 
 def ftr_get_cube_classes(ctx, out):
     _check(load().ftr_get_cube_classes(ctx, _ptr(out, np.uint8)), ctx)
+
+
+def ftr_debug_buffer(ctx, which, out):
+    _check(load().ftr_debug_buffer(ctx, int(which), _ptr(out), int(out.nbytes)), ctx)
 
 
 def ftr_mc_table():
