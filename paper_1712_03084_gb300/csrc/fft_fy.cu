@@ -16,6 +16,17 @@ namespace {
 
 constexpr int kLines = 16;
 
+// Load line f's elements y = N2 n1 + r (contiguous) and run step 1.
+template <int N>
+__device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r, int f, float2* smem,
+                                           const float2* __restrict__ tw) {
+    using X = Xchg<N, kLines>;
+    float2 v[X::N1];
+#pragma unroll
+    for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = src[X::N2 * n1 + r];
+    fft_step1<N, kLines, -1>(v, f, r, smem, tw);
+}
+
 template <int N>
 __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     k_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
@@ -38,39 +49,38 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     const size_t out_base = (size_t)(z0 + f2) + (size_t)nz * ((size_t)N * kx);
     // the transformed x component waits in shared memory (line index fastest)
     float2* stash = smem + X::SIZE;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-        if (r1 < X::N2) {
-            const float2* src = s0 + (size_t)c * Mh + (size_t)N * (z0 + f1 + (size_t)nz * kx);
-            float2 v[X::N1];
+    const float2* line = s0 + (size_t)N * (z0 + f1 + (size_t)nz * kx);
+    // x component: transform along y and park it (line index fastest)
+    if (r1 < X::N2) load_step1<N>(line, r1, f1, smem, tw);
+    __syncthreads();
+    float2 o[X::N2];
+    if (i2 < X::N1) fft_step2<N, kLines, -1>(o, f2, i2, smem);
+    __syncthreads();
+    if (i2 < X::N1) {
 #pragma unroll
-            for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = src[X::N2 * n1 + r1];
-            fft_step1<N, kLines, -1>(v, f1, r1, smem, tw);
+        for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (kLines + 1) * (i2 + X::N1 * k2)] = o[k2];
+    }
+    // y component: transform, then W = x + j w_y y goes out as field 0
+    if (r1 < X::N2) load_step1<N>(line + Mh, r1, f1, smem, tw);
+    __syncthreads();
+    if (i2 < X::N1) fft_step2<N, kLines, -1>(o, f2, i2, smem);
+    __syncthreads();
+    if (i2 < X::N1) {
+#pragma unroll
+        for (int k2 = 0; k2 < X::N2; ++k2) {
+            const int ky = i2 + X::N1 * k2;
+            const float wy = (ky == N / 2) ? 0.f : wy_scale * (float)signed_bin(ky, N);
+            const float2 w = stash[f2 + (kLines + 1) * ky];
+            s1[out_base + (size_t)nz * ky] = make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x);
         }
-        __syncthreads();
-        float2 o[X::N2];
-        if (i2 < X::N1) fft_step2<N, kLines, -1>(o, f2, i2, smem);
-        __syncthreads();
-        if (i2 < X::N1) {
-            if (c == 0) {
+    }
+    // z component: transform and write as field 1
+    if (r1 < X::N2) load_step1<N>(line + 2 * Mh, r1, f1, smem, tw);
+    __syncthreads();
+    if (i2 < X::N1) {
+        fft_step2<N, kLines, -1>(o, f2, i2, smem);
 #pragma unroll
-                for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (kLines + 1) * (i2 + X::N1 * k2)] = o[k2];
-            } else if (c == 1) {
-#pragma unroll
-                for (int k2 = 0; k2 < X::N2; ++k2) {
-                    const int ky = i2 + X::N1 * k2;
-                    const float wy = (ky == N / 2) ? 0.f : wy_scale * (float)signed_bin(ky, N);
-                    const float2 w = stash[f2 + (kLines + 1) * ky];
-                    s1[out_base + (size_t)nz * ky] = make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x);
-                }
-            } else {
-#pragma unroll
-                for (int k2 = 0; k2 < X::N2; ++k2) {
-                    const int ky = i2 + X::N1 * k2;
-                    s1[Mh + out_base + (size_t)nz * ky] = o[k2];
-                }
-            }
-        }
+        for (int k2 = 0; k2 < X::N2; ++k2) s1[Mh + out_base + (size_t)nz * (i2 + X::N1 * k2)] = o[k2];
     }
 }
 

@@ -17,6 +17,20 @@ namespace {
 
 constexpr int kLines = 16;
 
+// Load line f's elements z = N2 n1 + r (zero outside [zl, zh)) and run step 1.
+template <int N>
+__device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r, int f, int zl, int zh,
+                                           float2* smem, const float2* __restrict__ tw) {
+    using X = Xchg<N, kLines>;
+    float2 v[X::N1];
+#pragma unroll
+    for (int n1 = 0; n1 < X::N1; ++n1) {
+        const int z = X::N2 * n1 + r;
+        v[n1] = (z >= zl && z < zh) ? src[z] : make_float2(0.f, 0.f);
+    }
+    fft_step1<N, kLines, -1>(v, f, r, smem, tw);
+}
+
 template <int N>
 __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     k_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
@@ -31,28 +45,17 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     int zl, zh;
     live_z_range(meta, zl, zh);
     const size_t line = (size_t)N * ((size_t)(ky0 + f) + (size_t)ny * kx);
-    float2 xw[X::N2], xh[X::N2];
-#pragma unroll 1
-    for (int c = 0; c < 2; ++c) {
-        if (r < X::N2) {
-            const float2* src = s1 + (size_t)c * Mh + line;
-            float2 v[X::N1];
-#pragma unroll
-            for (int n1 = 0; n1 < X::N1; ++n1) {
-                const int z = X::N2 * n1 + r;
-                v[n1] = (z >= zl && z < zh) ? src[z] : make_float2(0.f, 0.f);
-            }
-            fft_step1<N, kLines, -1>(v, f, r, smem, tw);
-        }
-        __syncthreads();
-        if (r < X::N1) {
-            if (c == 0)
-                fft_step2<N, kLines, -1>(xw, f, r, smem);
-            else
-                fft_step2<N, kLines, -1>(xh, f, r, smem);
-        }
-        __syncthreads();
-    }
+    // forward z transforms of W (field 0) and of the x/y-transformed V_z (field 1)
+    if (r < X::N2) load_step1<N>(s1 + line, r, f, zl, zh, smem, tw);
+    __syncthreads();
+    float2 xw[X::N2];
+    if (r < X::N1) fft_step2<N, kLines, -1>(xw, f, r, smem);
+    __syncthreads();
+    if (r < X::N2) load_step1<N>(s1 + Mh + line, r, f, zl, zh, smem, tw);
+    __syncthreads();
+    float2 xh[X::N2];
+    if (r < X::N1) fft_step2<N, kLines, -1>(xh, f, r, smem);
+    __syncthreads();
     if (r < X::N1) {
         const int ky = ky0 + f;
         const float wxd = wx_scale * (float)kx;                 // |k_x| <= n_x/2 already
