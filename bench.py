@@ -1,0 +1,532 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 volumetric Fourier-transform reconstruction.
+
+Workload: one synthetic 4-camera human frame on a 256^3 grid over a 2.0 m
+cube (512x424 depth maps, fx = fy = 365, ring radius 2.5 m, 1.2 m high,
+depth noise 0.0012 z^2, 1920x1080 RGB views), i.e. the single-frame FP32
+configuration.  One step = the whole per-frame path: splat eq.(1)(2),
+forward 3D FFT, integration filter, inverse 3D FFT, iso-level, marching
+cubes and per-vertex texture (Sec. III-B, III-C), through the C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is frames/s of the whole job with
+inputs resident in HBM; ``e2e`` is the same metric through the C ABI with
+pinned host buffers (inputs copied in, mesh and texture copied out inside
+the timed region).  L2 is flushed (256 MiB write) between timed steps, outside
+the timed intervals.  Multi-GPU runs are independent replicas (frames do not
+shard), launched with torch.distributed.run; the max over ranks is taken.
+``--impl reference`` times the FP64 CPU oracle on the same frame instead
+(rank 0 only), each step a bounded sample of one frame's work.
+"""
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s at 256^3 grid (4-camera synthetic human frame, FP32)"
+UNIT = "frames/s"
+GRID = 256
+SEED = 1
+SAMPLE_S = 16          # the oracle sample covers 1/SAMPLE_S of the transform and MC work
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=SEED)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (quick runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_frame(seed):
+    from datagen import frame_config, human_frame
+    cfg = frame_config(f"human{GRID}")
+    fr = human_frame(seed=seed, K=cfg["K"], ring=cfg["ring"], height=cfg["height"])
+    return cfg, fr
+
+
+def depth_tol(cfg):
+    h = [(cfg["bbox"][3 + a] - cfg["bbox"][a]) / cfg["grid_n"][a] for a in range(3)]
+    return float(np.float32(max(3.0 * max(h), 0.02)))
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 10:
+                    continue
+                if self.uuid and self.uuid not in p[1]:
+                    continue
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        pw = [num(r[4]) for r in rows if num(r[4]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[6 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+STAGE_SOURCES = {
+    "fft_x_fwd": ["fft_fx.cu", "fft_common.cuh"],
+    "fft_y_fwd": ["fft_fy.cu", "fft_common.cuh"],
+    "fft_z_filter_inv": ["fft_fz.cu", "fft_common.cuh"],
+    "fft_y_inv": ["fft_iy.cu", "fft_common.cuh"],
+    "fft_x_inv": ["fft_ix.cu", "fft_common.cuh"],
+    "splat_accum": ["splat.cu"],
+    "mc_count": ["mc.cu"],
+    "mc_emit": ["mc.cu"],
+    "texture": ["texture.cu"],
+}
+
+
+def source_sha(stage):
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES.get(stage, []):
+        with open(os.path.join(ROOT, "paper_1712_03084_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(stage):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+    want = source_sha(stage)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for m in re.finditer(r"<!--\s*traffic:\s*(\S+)\s+(\d+)\s+sha:(\w+)\s*-->", f.read()):
+                if m.group(1) == stage and m.group(3) == want:
+                    return int(m.group(2))
+    return None
+
+
+def algorithmic_bytes(stage, info, grid, k_views):
+    """Bytes a stage must move once per launch (inputs read once, outputs written once)."""
+    nx, ny, nz = grid
+    M = nx * ny * nz
+    mh_full = (nx // 2 + 1) * ny * nz
+    mh_live = (nx // 2 + 1) * ny * max(0, info["z_hi"] - info["z_lo"])
+    c8 = 8
+    if stage == "fft_x_fwd":
+        return info["bricks"] * 512 * 3 * 4 + 3 * c8 * mh_live
+    if stage == "fft_y_fwd":
+        return 3 * c8 * mh_live + 2 * c8 * mh_live
+    if stage == "fft_z_filter_inv":
+        return 2 * c8 * mh_live + c8 * mh_full
+    if stage == "fft_y_inv":
+        return 2 * c8 * mh_full
+    if stage == "fft_x_inv":
+        return c8 * mh_full + 4 * M
+    if stage == "splat_accum":
+        return info["pairs"] * (4 + 48) + info["bricks"] * 512 * 3 * 4
+    if stage == "mc_count":
+        return 4 * M
+    if stage == "mc_emit":
+        return 4 * M + 24 * info["n_vertices"]
+    if stage == "texture":
+        return info["n_vertices"] * (12 + k_views * 12 + 4)
+    return None
+
+
+# ----------------------------------------------------------------------------- oracle sample
+
+def oracle_sample_step(ctx_o, rng_index):
+    """Time 1/S of one frame's transform and MC work plus the full splat, level and
+    texture on the CPU oracle; returns the estimated seconds per full frame."""
+    from oracle import fft as offt, level as olevel, mc as omc, spectral, splat as osplat, texture as otex
+    cfg, fr, A, L, verts = ctx_o["cfg"], ctx_o["fr"], ctx_o["A"], ctx_o["L"], ctx_o["verts"]
+    grid, box = cfg["grid_n"], cfg["bbox"]
+    nx, ny, nz = grid
+    S = SAMPLE_S
+    t = {}
+    t0 = time.perf_counter()
+    V = osplat.splat_weighted(fr["points"], fr["normals"], fr["weights"], grid, box)
+    t["splat"] = time.perf_counter() - t0
+    # 3 forward + 1 inverse 3D transforms = 12 axis passes over M/n lines each;
+    # the sample transforms every S-th z-slab (x, y passes) or y-row (z pass)
+    sl = slice(rng_index % S, None, S)
+    t0 = time.perf_counter()
+    for c in range(4):
+        f = V[c % 3][sl]                                   # [nz/S, ny, nx]
+        inv = c == 3
+        a = offt.fft(f, axis=2, inverse=inv)
+        a = offt.fft(a, axis=1, inverse=inv)
+        b = offt.fft(V[c % 3][:, sl, :], axis=0, inverse=inv)
+    t["fft"] = (time.perf_counter() - t0) * S
+    t0 = time.perf_counter()
+    Vh = np.stack([b.astype(np.complex128)] * 3)
+    spectral.filter_spectrum(Vh, (nx, ny // S if ny // S else 1, nz), box)
+    t["filter"] = (time.perf_counter() - t0) * S
+    t0 = time.perf_counter()
+    olevel.iso_level(A, fr["points"], grid, box)
+    t["level"] = time.perf_counter() - t0
+    z0 = (rng_index * (nz // S)) % (nz - nz // S)
+    zb = (box[0], box[1], box[2] + z0 * (box[5] - box[2]) / nz,
+          box[3], box[4], box[2] + (z0 + nz // S + 1) * (box[5] - box[2]) / nz)
+    t0 = time.perf_counter()
+    omc.marching_cubes(A[z0:z0 + nz // S + 1], L, (nx, ny, nz // S + 1), zb)
+    t["mc"] = (time.perf_counter() - t0) * S
+    t0 = time.perf_counter()
+    otex.texture(verts, fr["views"], depth_tol(cfg))
+    t["texture"] = time.perf_counter() - t0
+    return sum(t.values()), t
+
+
+def oracle_setup(cfg, fr):
+    """Untimed: the oracle's own A, L and mesh for the sampled MC and texture stages."""
+    from oracle import pipeline
+    r = pipeline.reconstruct(fr["points"], fr["normals"], fr["weights"], cfg["grid_n"], cfg["bbox"])
+    return {"cfg": cfg, "fr": fr, "A": r["A"], "L": r["L"], "verts": r["mesh"]["vertices"]}
+
+
+def oracle_baseline(cfg, fr, steps=1):
+    ctx_o = oracle_setup(cfg, fr)
+    w0, c0 = time.perf_counter(), time.process_time()
+    est = [oracle_sample_step(ctx_o, i)[0] for i in range(steps)]
+    wall, cpu = time.perf_counter() - w0, time.process_time() - c0
+    return 1.0 / float(np.mean(est)), round(cpu / max(wall, 1e-9), 2), est
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1712_03084_gb300 import build as pbuild
+    from paper_1712_03084_gb300 import ftr
+
+    pbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg, fr = make_frame(args.seed + rank)
+    grid, box = cfg["grid_n"], cfg["bbox"]
+    tol = depth_tol(cfg)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ftr.Context(grid, box, stream=stream.cuda_stream)
+    K = len(fr["views"])
+
+    # device-resident inputs
+    P = torch.from_numpy(fr["points"]).to(dev)
+    N = torch.from_numpy(fr["normals"]).to(dev)
+    W = torch.from_numpy(fr["weights"]).to(dev)
+    cams = [(s, n) for (s, n) in fr["per_camera"]]
+    dviews = []
+    for v in fr["views"]:
+        d = dict(v)
+        d["depth"] = torch.from_numpy(v["depth"]).to(dev)
+        d["conf"] = torch.from_numpy(v["conf"]).to(dev)
+        d["rgb"] = torch.from_numpy(v["rgb"]).to(dev)
+        dviews.append(d)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    cap = [0]
+    outs = {}
+
+    def ensure_out(nv):
+        if nv > cap[0]:
+            cap[0] = int(nv * 1.5) + 1024
+            outs["w"] = torch.empty((cap[0], K), dtype=torch.float32, device=dev)
+            outs["uv"] = torch.empty((cap[0], K, 2), dtype=torch.float32, device=dev)
+            outs["rgb"] = torch.empty((cap[0], 3), dtype=torch.uint8, device=dev)
+            outs["tex"] = torch.empty((cap[0],), dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.reset()
+        for (s, n) in cams:
+            ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+        ctx.solve(want_level=False)
+        m = ctx.extract_mesh()
+        ensure_out(m.n_vertices)
+        ftr.ftr_texture(ctx.h, dviews, tol, outs["w"], outs["uv"], outs["rgb"], outs["tex"])
+        return m
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    ctx.profile_enable(True)
+    l0 = ctx.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            m = step()
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    info = ctx.frame_info()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # dominant kernel and its roofline
+    per_launch = {k: (ms / n if n else 0.0, n) for k, (ms, n) in prof.items()}
+    dom = max(per_launch, key=lambda k: per_launch[k][0] * per_launch[k][1])
+    dom_ms = per_launch[dom][0]
+    alg = algorithmic_bytes(dom, info, grid, K)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (dom_ms * 1e-3) / 1e9 if alg and dom_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None,
+                "traffic": profiled_traffic(dom), "algorithmic_bytes": alg,
+                "ms_per_launch": round(dom_ms, 5)}
+    stages = {}
+    for k, (ms_l, n) in per_launch.items():
+        if n == 0:
+            continue
+        b = algorithmic_bytes(k, info, grid, K)
+        stages[k] = {"ms": round(ms_l, 5), "launches": n,
+                     "gbs": round(b / (ms_l * 1e-3) / 1e9, 1) if b and ms_l > 0 else None}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, est = oracle_baseline(cfg, fr, steps=1)
+        cpu = {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 NumPy oracle on the same frame: full splat, level and texture, 1/{SAMPLE_S} of "
+                         f"the 12 axis passes of the 3D transforms, of the filter and of the marching-cubes slabs, "
+                         f"scaled to one frame ({est[0]:.1f} s/frame estimated)"}
+    ctx.close()
+    if rank != 0:
+        return None
+    step_ms_sorted = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "human256: 4-camera synthetic human frame, 256^3 grid over a 2.0 m cube, "
+                               "512x424 depth (fx=fy=365), 1920x1080 RGB, ring 2.5 m",
+                   "grid": list(grid), "points": int(info["points_in"]), "vertices": int(info["n_vertices"]),
+                   "triangles": int(info["n_tris"]), "cameras": K, "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (256 MiB write, untimed)"},
+        "latency_ms": {"p50": round(float(np.percentile(step_ms_sorted, 50)), 4),
+                       "p99": round(float(np.percentile(step_ms_sorted, 99)), 4)},
+        "roofline": roofline, "stages": stages, "e2e": e2e, "cpu_baseline": cpu,
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+    return line
+
+
+def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
+    import torch
+    from paper_1712_03084_gb300 import ftr
+
+    def pin(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t
+    P, N, W = pin(fr["points"]), pin(fr["normals"]), pin(fr["weights"])
+    hviews = []
+    bi = P.numel() * 4 + N.numel() * 4 + W.numel() * 4
+    for v in fr["views"]:
+        d = dict(v)
+        d["depth"], d["conf"], d["rgb"] = pin(v["depth"]), pin(v["conf"]), pin(v["rgb"])
+        bi += d["depth"].numel() * 4 + d["conf"].numel() * 4 + d["rgb"].numel()
+        hviews.append(d)
+    cap = 400000
+    hv = torch.empty((cap, 3), dtype=torch.float32).pin_memory()
+    hn = torch.empty((cap, 3), dtype=torch.float32).pin_memory()
+    ht = torch.empty((2 * cap, 3), dtype=torch.int32).pin_memory()
+    hw = torch.empty((cap, K), dtype=torch.float32).pin_memory()
+    huv = torch.empty((cap, K, 2), dtype=torch.float32).pin_memory()
+    hrgb = torch.empty((cap, 3), dtype=torch.uint8).pin_memory()
+    htex = torch.empty((cap,), dtype=torch.uint8).pin_memory()
+    bo = [0]
+
+    def step():
+        ctx.reset()
+        for (s, n) in cams:
+            ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+        ctx.solve(want_level=False)
+        m = ctx.extract_mesh()
+        if m.n_vertices > cap or m.n_tris > 2 * cap:
+            raise RuntimeError("e2e host buffers too small")
+        ftr.ftr_mesh_copy(ctx.h, hv, hn, ht)
+        ftr.ftr_texture(ctx.h, hviews, tol, hw, huv, hrgb, htex)
+        bo[0] = m.n_vertices * (24 + K * 12 + 4) + m.n_tris * 12
+        return m
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        times = []
+        if world > 1:
+            torch.distributed.barrier()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    total = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    return {"value": round(world * args.steps / total, 2), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+            "d2h_bytes_per_step": int(bo[0]), "ms_per_step": round(1000 * total / args.steps, 4),
+            "timing": "host wall clock per step (synchronised), pinned host buffers"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cfg, fr = make_frame(args.seed)
+    ctx_o = oracle_setup(cfg, fr)
+    for i in range(args.warmup):
+        oracle_sample_step(ctx_o, i)
+    w0, c0 = time.perf_counter(), time.process_time()
+    est = []
+    for i in range(args.steps):
+        est.append(oracle_sample_step(ctx_o, args.warmup + i)[0])
+    wall, cpu = time.perf_counter() - w0, time.process_time() - c0
+    value = 1.0 / float(np.mean(est))
+    sample = (f"each step: FP64 NumPy oracle on the same frame, full splat, level and texture plus 1/{SAMPLE_S} "
+              f"of the transform passes, filter and marching-cubes slabs, scaled to one frame")
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * float(np.mean(est)), 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "human256: 4-camera synthetic human frame, 256^3 grid over a 2.0 m cube",
+                   "grid": list(cfg["grid_n"]), "points": int(len(fr["points"])), "parallelism": "host"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": round(cpu / max(wall, 1e-9), 2),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

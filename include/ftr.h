@@ -157,6 +157,13 @@ int ftr_texture(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr
 /* Points added since the last reset, and how many of them were dropped. */
 int ftr_stats(const ftr_ctx* ctx, int64_t* points_in, int64_t* points_dropped);
 
+/* Facts about the current frame (waits for the stream): info[0] points in,
+ * [1] dropped, [2] bricks touched by the splat, [3] (point, brick) pairs,
+ * [4], [5] the slab of z-planes z_lo <= z < z_hi that can hold non-zero V
+ * (the forward x/y passes work on it only), [6] vertices, [7] triangles of
+ * the last mesh.  Writes min(n, 8) values. */
+int ftr_frame_info(ftr_ctx* ctx, int64_t* info, int n);
+
 /* Message of the last error on this context (never NULL). */
 const char* ftr_last_error(const ftr_ctx* ctx);
 

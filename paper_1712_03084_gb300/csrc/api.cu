@@ -676,6 +676,24 @@ int ftr_get_cube_classes(ftr_ctx* c, uint8_t* out) {
     return FTR_OK;
 }
 
+int ftr_frame_info(ftr_ctx* c, int64_t* info, int n) {
+    if (!c || !info || n < 0) return FTR_EINVAL;
+    int meta[4] = {0, 0, 0, -1};
+    unsigned long long dropped = 0;
+    cudaError_t e = cudaMemcpyAsync(meta, c->d_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&dropped, c->d_dropped, sizeof(dropped), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_frame_info");
+    int zl = 0, zh = 0;
+    if (meta[3] >= 0) {
+        zl = (meta[2] * kBrick) & ~15;
+        zh = ((meta[3] + 1) * kBrick + 15) & ~15;
+    }
+    const int64_t v[8] = {c->points_in, (int64_t)dropped, meta[0], meta[1], zl, zh, c->n_verts, c->n_tris};
+    for (int i = 0; i < n && i < 8; ++i) info[i] = v[i];
+    return FTR_OK;
+}
+
 int ftr_debug_buffer(ftr_ctx* c, int which, void* out, int64_t bytes) {
     if (!c || !out) return FTR_EINVAL;
     const void* src = nullptr;

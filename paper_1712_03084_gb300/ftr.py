@@ -68,6 +68,7 @@ _SIGNATURES = [
                                    ctypes.POINTER(ftr_tex)]),
     ("ftr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("ftr_frame_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_field_A", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -208,6 +209,15 @@ def ftr_stats(ctx):
     return a.value, b.value
 
 
+FRAME_INFO_KEYS = ("points_in", "dropped", "bricks", "pairs", "z_lo", "z_hi", "n_vertices", "n_tris")
+
+
+def ftr_frame_info(ctx):
+    out = np.zeros(8, np.int64)
+    _check(load().ftr_frame_info(ctx, out.ctypes.data, 8), ctx)
+    return dict(zip(FRAME_INFO_KEYS, (int(v) for v in out)))
+
+
 def ftr_last_error(ctx):
     return load().ftr_last_error(ctx).decode()
 
@@ -328,6 +338,9 @@ class Context:
 
     def stats(self):
         return ftr_stats(self.h)
+
+    def frame_info(self):
+        return ftr_frame_info(self.h)
 
     def field_V(self):
         nx, ny, nz = self.grid_n
