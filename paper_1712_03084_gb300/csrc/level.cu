@@ -57,15 +57,24 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
     }
 }
 
+// One warp: lane l sums partials l, l + 32, ... in order, then a fixed
+// shuffle tree combines the lanes.
 __global__ void k_level_final(const double* __restrict__ part, int nblocks, double* level) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int lane = threadIdx.x;
     double s = 0.0, c = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = lane; b < nblocks; b += 32) {
         s += part[2 * b];
         c += part[2 * b + 1];
     }
-    level[0] = c > 0.0 ? s / c : 0.0;
-    level[1] = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+        level[0] = c > 0.0 ? s / c : 0.0;
+        level[1] = c;
+    }
 }
 
 }  // namespace

@@ -1,6 +1,8 @@
 // Marching cubes on A at level L (Sec. III-B, [35]), scan-compacted.
 //
-// Corner bit = 1 iff A >= L, compared in float64 (A promoted).  A node owns the
+// Corner bit = 1 iff A >= L with A promoted to float64.  Because A is float32,
+// that is the same as A >= Lf with Lf = L rounded up to float32, so the
+// kernels compare in float32 and still take the float64 decision.  A node owns the
 // grid edges toward +x, +y, +z; an edge carries a vertex when its two bits
 // differ.  Vertex ids are the rank of (node, axis) in linear node order and
 // triangles follow cell order then table order, so the mesh does not depend
@@ -33,23 +35,23 @@ struct NodeInfo {
 };
 
 __device__ __forceinline__ NodeInfo classify_node(const float* __restrict__ A, int64_t n, int x, int y, int z,
-                                                  const GridDev& g, double L) {
+                                                  const GridDev& g, float L) {
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     const bool hx = x < nx - 1, hy = y < ny - 1, hz = z < nz - 1;
-    const int b0 = (double)A[n] >= L;
+    const int b0 = A[n] >= L;
     NodeInfo r;
     r.flags = 0;
     r.cls = 0;
-    const int bx = hx ? ((double)A[n + 1] >= L) : b0;
-    const int by = hy ? ((double)A[n + sy] >= L) : b0;
-    const int bz = hz ? ((double)A[n + sz] >= L) : b0;
+    const int bx = hx ? (A[n + 1] >= L) : b0;
+    const int by = hy ? (A[n + sy] >= L) : b0;
+    const int bz = hz ? (A[n + sz] >= L) : b0;
     r.flags = (bx != b0) | ((by != b0) << 1) | ((bz != b0) << 2);
     if (hx && hy && hz) {
-        const int bxy = (double)A[n + 1 + sy] >= L;
-        const int bxz = (double)A[n + 1 + sz] >= L;
-        const int byz = (double)A[n + sy + sz] >= L;
-        const int bxyz = (double)A[n + 1 + sy + sz] >= L;
+        const int bxy = A[n + 1 + sy] >= L;
+        const int bxz = A[n + 1 + sz] >= L;
+        const int byz = A[n + sy + sz] >= L;
+        const int bxyz = A[n + 1 + sy + sz] >= L;
         r.cls = b0 | (bx << 1) | (by << 2) | (bxy << 3) | (bz << 4) | (bxz << 5) | (byz << 6) | (bxyz << 7);
     }
     return r;
@@ -105,11 +107,11 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float*
                                                          const double* __restrict__ level, int64_t M,
                                                          int* __restrict__ blk, int nblocks) {
     __shared__ int3 sh[kMcThreads / 32];
-    const double L = level[0];
-    const int64_t n0 = (int64_t)blockIdx.x * kMcChunk + (int64_t)threadIdx.x * kNodesPerThread;
+    const float L = __double2float_ru(level[0]);
     int3 cnt = make_int3(0, 0, 0);
+#pragma unroll 2
     for (int k = 0; k < kNodesPerThread; ++k) {
-        const int64_t n = n0 + k;
+        const int64_t n = (int64_t)blockIdx.x * kMcChunk + k * kMcThreads + threadIdx.x;
         if (n >= M) break;
         int x, y, z;
         node_xyz(n, g, x, y, z);
@@ -182,81 +184,75 @@ __device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t 
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
                                                         const double* __restrict__ level, int64_t M,
-                                                        const int* __restrict__ off, int nblocks,
-                                                        int4* __restrict__ nodes, float* __restrict__ verts,
-                                                        float* __restrict__ vnrm) {
+                                                        const int* __restrict__ blk, const int* __restrict__ off,
+                                                        int nblocks, int4* __restrict__ nodes,
+                                                        float* __restrict__ verts, float* __restrict__ vnrm) {
     __shared__ int3 sh[kMcThreads / 32];
-    const double L = level[0];
-    const int64_t n0 = (int64_t)blockIdx.x * kMcChunk + (int64_t)threadIdx.x * kNodesPerThread;
-    NodeInfo info[kNodesPerThread];
-    int3 cnt = make_int3(0, 0, 0);
-#pragma unroll
-    for (int k = 0; k < kNodesPerThread; ++k) {
-        const int64_t n = n0 + k;
-        info[k].flags = 0;
-        info[k].cls = 0;
-        if (n < M) {
-            int x, y, z;
-            node_xyz(n, g, x, y, z);
-            info[k] = classify_node(A, n, x, y, z, g, L);
-        }
-        const int nt = c_ntri[info[k].cls];
-        cnt.x += (info[k].flags != 0 || nt > 0);
-        cnt.y += __popc(info[k].flags);
-        cnt.z += nt;
-    }
-    int3 tot;
-    int3 ex = block_scan3(cnt, tot, sh);
-    int ia = off[blockIdx.x] + ex.x;
-    int iv = off[(nblocks + 1) + blockIdx.x] + ex.y;
-    int it = off[2 * (nblocks + 1) + blockIdx.x] + ex.z;
+    if (blk[blockIdx.x] == 0) return;           // no surface in this chunk (block-uniform)
+    const double Ld = level[0];
+    const float L = __double2float_ru(Ld);
+    int ia = off[blockIdx.x];
+    int iv = off[(nblocks + 1) + blockIdx.x];
+    int it = off[2 * (nblocks + 1) + blockIdx.x];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int64_t st[3] = {1, (int64_t)nx, (int64_t)nx * ny};
     const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
-#pragma unroll
+    const int nn[3] = {nx, ny, nz};
     for (int k = 0; k < kNodesPerThread; ++k) {
-        const int nt = c_ntri[info[k].cls];
-        if (info[k].flags == 0 && nt == 0) continue;
-        const int64_t n = n0 + k;
-        nodes[ia] = make_int4((int)n, info[k].flags | (info[k].cls << 8), iv, it);
-        ++ia;
-        it += nt;
-        if (info[k].flags == 0) continue;
-        int q[3];
-        node_xyz(n, g, q[0], q[1], q[2]);
-        const int nn[3] = {nx, ny, nz};
-        float g0[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
-        for (int a = 0; a < 3; ++a) {
-            if (!((info[k].flags >> a) & 1)) continue;
-            const int64_t n1 = n + st[a];
-            const double a0 = A[n], a1 = A[n1];
-            const double t = (L - a0) / (a1 - a0);
-            int q1[3] = {q[0], q[1], q[2]};
-            q1[a] += 1;
-            float g1[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
-            float p[3], nv[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
-                if (c == a) pc += t * g.h[c];
-                p[c] = (float)pc;
-                const float tf = (float)t;
-                nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
-            }
-            const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
-            const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
-            verts[3 * (int64_t)iv + 0] = p[0];
-            verts[3 * (int64_t)iv + 1] = p[1];
-            verts[3 * (int64_t)iv + 2] = p[2];
-            vnrm[3 * (int64_t)iv + 0] = nv[0] * inv;
-            vnrm[3 * (int64_t)iv + 1] = nv[1] * inv;
-            vnrm[3 * (int64_t)iv + 2] = nv[2] * inv;
-            ++iv;
+        const int64_t n = (int64_t)blockIdx.x * kMcChunk + k * kMcThreads + threadIdx.x;
+        NodeInfo info;
+        info.flags = 0;
+        info.cls = 0;
+        int q[3] = {0, 0, 0};
+        if (n < M) {
+            node_xyz(n, g, q[0], q[1], q[2]);
+            info = classify_node(A, n, q[0], q[1], q[2], g, L);
         }
+        const int nt = c_ntri[info.cls];
+        const int act = (info.flags != 0 || nt > 0);
+        int3 tot;
+        const int3 ex = block_scan3(make_int3(act, __popc(info.flags), nt), tot, sh);
+        if (act) {
+            int vi = iv + ex.y;
+            nodes[ia + ex.x] = make_int4((int)n, info.flags | (info.cls << 8), vi, it + ex.z);
+            if (info.flags) {
+                float g0[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
+                for (int a = 0; a < 3; ++a) {
+                    if (!((info.flags >> a) & 1)) continue;
+                    const int64_t n1 = n + st[a];
+                    const double a0 = A[n], a1 = A[n1];
+                    const double t = (Ld - a0) / (a1 - a0);
+                    int q1[3] = {q[0], q[1], q[2]};
+                    q1[a] += 1;
+                    float g1[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
+                    float p[3], nv[3];
+                    const float tf = (float)t;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
+                        if (c == a) pc += t * g.h[c];
+                        p[c] = (float)pc;
+                        nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
+                    }
+                    const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+                    const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
+                    verts[3 * (int64_t)vi + 0] = p[0];
+                    verts[3 * (int64_t)vi + 1] = p[1];
+                    verts[3 * (int64_t)vi + 2] = p[2];
+                    vnrm[3 * (int64_t)vi + 0] = nv[0] * inv;
+                    vnrm[3 * (int64_t)vi + 1] = nv[1] * inv;
+                    vnrm[3 * (int64_t)vi + 2] = nv[2] * inv;
+                    ++vi;
+                }
+            }
+        }
+        ia += tot.x;
+        iv += tot.y;
+        it += tot.z;
     }
 }
 
@@ -313,7 +309,7 @@ __global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const doubl
     const int y = (int)((i / cx) % cy);
     const int z = (int)(i / ((int64_t)cx * cy));
     const int64_t n = x + (int64_t)g.n[0] * (y + (int64_t)g.n[1] * z);
-    out[i] = (uint8_t)classify_node(A, n, x, y, z, g, level[0]).cls;
+    out[i] = (uint8_t)classify_node(A, n, x, y, z, g, __double2float_ru(level[0])).cls;
 }
 
 }  // namespace
@@ -352,8 +348,9 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
 
 cudaError_t launch_mc_emit(ftr_ctx* c) {
     prof_begin(c, ST_MC_EMIT);
-    k_mc_emit<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->M, c->d_mc_off,
-                                                         c->mc_blocks, c->d_mc_nodes, c->d_verts, c->d_vnrm);
+    k_mc_emit<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->M, c->d_mc_blk,
+                                                         c->d_mc_off, c->mc_blocks, c->d_mc_nodes, c->d_verts,
+                                                         c->d_vnrm);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);
