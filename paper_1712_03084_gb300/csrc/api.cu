@@ -168,6 +168,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_brick_slot);
     dfree(c->d_active);
     dfree(c->d_meta);
+    dfree(c->d_tile);
     dfree(c->d_entries);
     dfree(c->d_vpool);
     dfree(c->d_s0);
@@ -177,6 +178,8 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_level);
     dfree(c->d_level_part);
     dfree(c->d_mc_blk);
+    dfree(c->d_mc_mask);
+    dfree(c->d_mc_tile);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
     dfree(c->d_mc_nodes);
@@ -269,6 +272,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_brick_slot, c->n_bricks);
     ALLOC(c->d_active, c->n_bricks);
     ALLOC(c->d_meta, 4);
+    ALLOC(c->d_tile, (c->n_bricks + 2047) / 2048 + 1);
     ALLOC(c->d_vpool, (size_t)c->n_bricks * 3 * kBrickVox);
     ALLOC(c->d_s0, 3 * c->Mh);
     ALLOC(c->d_s1, 2 * c->Mh);
@@ -277,8 +281,10 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     c->level_blocks = 304;
     ALLOC(c->d_level, 2);
     ALLOC(c->d_level_part, 2 * c->level_blocks);
-    c->mc_blocks = (int)((c->M + kMcChunk - 1) / kMcChunk);
+    c->mc_blocks = (grid_n[1] / 8) * grid_n[2];
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
+    ALLOC(c->d_mc_mask, c->mc_blocks);
+    ALLOC(c->d_mc_tile, (c->mc_blocks + 2047) / 2048 + 1);
     ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
 #undef ALLOC
     if ((e = cudaMallocHost((void**)&c->h_mc_tot, 4 * sizeof(int))) != cudaSuccess) {
@@ -527,12 +533,12 @@ int ftr_texture(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_t
         d.rgb_w = v.rgb_w;
         d.rgb_h = v.rgb_h;
         for (int j = 0; j < 9; ++j) {
-            d.K[j] = v.K[j];
-            d.Krgb[j] = v.K_rgb[j];
+            d.K[j] = d.Kf[j] = v.K[j];
+            d.Krgb[j] = d.Krgbf[j] = v.K_rgb[j];
         }
         for (int j = 0; j < 12; ++j) {
-            d.RT[j] = v.world_to_cam[j];
-            d.RTrgb[j] = v.world_to_rgb[j];
+            d.RT[j] = d.RTf[j] = v.world_to_cam[j];
+            d.RTrgb[j] = d.RTrgbf[j] = v.world_to_rgb[j];
         }
         d.depth = v.depth;
         d.conf = v.conf;

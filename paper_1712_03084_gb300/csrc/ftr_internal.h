@@ -14,8 +14,7 @@ namespace ftr {
 constexpr int kBrick = 8;                 // splat accumulation brick edge (nodes)
 constexpr int kBrickVox = kBrick * kBrick * kBrick;
 constexpr int kMaxViews = 8;
-constexpr int kMcChunk = 2048;            // nodes per marching-cubes CTA
-constexpr int kMcThreads = 256;           // 8 consecutive nodes per thread
+constexpr int kMcThreads = 256;           // marching-cubes CTA size (chunks of 8 grid rows)
 constexpr int kMaxTrisPerCase = 5;
 
 enum Stage {
@@ -89,6 +88,7 @@ struct ftr_ctx {
     int* d_brick_slot = nullptr;
     int* d_active = nullptr;
     int* d_meta = nullptr;     // [0] active bricks, [1] entries, [2] min bz, [3] max bz
+    int2* d_tile = nullptr;    // per-tile sums / offsets of the brick scan
     int* d_entries = nullptr;
     int64_t cap_entries = 0;
     float* d_vpool = nullptr;  // active bricks x 3 x 512 V values
@@ -110,6 +110,8 @@ struct ftr_ctx {
     // marching cubes
     int mc_blocks = 0;
     int* d_mc_blk = nullptr;       // 3 x mc_blocks
+    int* d_mc_mask = nullptr;      // per chunk: rounds holding surface
+    int3* d_mc_tile = nullptr;     // tile sums / offsets of the chunk scan
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
     int4* d_mc_nodes = nullptr;
@@ -169,6 +171,7 @@ cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);
 struct ViewDev {
     int w, h, rgb_w, rgb_h;
     double K[9], RT[12], Krgb[9], RTrgb[12];
+    float Kf[9], RTf[12], Krgbf[9], RTrgbf[12];
     const float* depth;
     const float* conf;
     const uint8_t* rgb;

@@ -6,11 +6,13 @@
 // grid edges toward +x, +y, +z; an edge carries a vertex when its two bits
 // differ.  Vertex ids are the rank of (node, axis) in linear node order and
 // triangles follow cell order then table order, so the mesh does not depend
-// on scheduling.  Three launches:
-//   count  one CTA per 2048 consecutive nodes: active nodes (owning a vertex
-//          or lower corner of a cell with triangles), vertices, triangles
-//   scan   one CTA: exclusive offsets of the per-CTA counts (+ totals)
-//   emit   same CTAs again: block-local scan, one 16-byte record per active
+// on scheduling.  Launches:
+//   count  one CTA per chunk of 8 consecutive grid rows: active nodes (owning
+//          a vertex or lower corner of a cell with triangles), vertices,
+//          triangles, and a mask of the 256-node rounds that hold any
+//   scan   three coalesced launches: exclusive offsets of the chunk counts
+//   emit   same chunks again, skipping empty chunks and empty rounds:
+//          block-local scan, one 16-byte record per active
 //          node (node, edge bits | class << 8, first vertex, first triangle),
 //          vertex positions t = (L - A0)/(A1 - A0) in float64 and normals
 //          -grad A (central differences, one-sided at the border, lerped)
@@ -27,7 +29,6 @@ namespace {
 __constant__ int c_ntri[256];
 __constant__ signed char c_tri[256][kMaxTrisPerCase][3];
 
-constexpr int kNodesPerThread = kMcChunk / kMcThreads;   // 8
 
 struct NodeInfo {
     int flags;     // bit a: edge toward +a crosses
@@ -57,11 +58,21 @@ __device__ __forceinline__ NodeInfo classify_node(const float* __restrict__ A, i
     return r;
 }
 
-__device__ __forceinline__ void node_xyz(int64_t n, const GridDev& g, int& x, int& y, int& z) {
-    x = (int)(n % g.n[0]);
-    const int64_t r = n / g.n[0];
-    y = (int)(r % g.n[1]);
-    z = (int)(r / g.n[1]);
+// Chunk c covers rows y0 .. y0+7 of plane z (8 n_x consecutive nodes).
+struct Chunk {
+    int z, y0;
+    int64_t base;   // linear index of its first node
+    int nodes;
+};
+
+__device__ __forceinline__ Chunk chunk_of(const GridDev& g, int c) {
+    const int rows8 = g.n[1] / 8;
+    Chunk k;
+    k.z = c / rows8;
+    k.y0 = (c - k.z * rows8) * 8;
+    k.base = (int64_t)g.n[0] * (k.y0 + (int64_t)g.n[1] * k.z);
+    k.nodes = 8 * g.n[0];
+    return k;
 }
 
 // Block-wide exclusive scan of 3 ints (kMcThreads threads); returns totals.
@@ -104,22 +115,29 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
 }
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
-                                                         const double* __restrict__ level, int64_t M,
-                                                         int* __restrict__ blk, int nblocks) {
+                                                         const double* __restrict__ level, int* __restrict__ blk,
+                                                         int* __restrict__ mask, int nblocks) {
     __shared__ int3 sh[kMcThreads / 32];
     const float L = __double2float_ru(level[0]);
+    const Chunk ch = chunk_of(g, blockIdx.x);
+    const int nx = g.n[0];
+    const int rounds = (ch.nodes + kMcThreads - 1) / kMcThreads;
     int3 cnt = make_int3(0, 0, 0);
-#pragma unroll 2
-    for (int k = 0; k < kNodesPerThread; ++k) {
-        const int64_t n = (int64_t)blockIdx.x * kMcChunk + k * kMcThreads + threadIdx.x;
-        if (n >= M) break;
-        int x, y, z;
-        node_xyz(n, g, x, y, z);
-        const NodeInfo ni = classify_node(A, n, x, y, z, g, L);
-        const int nt = c_ntri[ni.cls];
-        cnt.x += (ni.flags != 0 || nt > 0);
-        cnt.y += __popc(ni.flags);
-        cnt.z += nt;
+    int m = 0;
+    for (int k = 0; k < rounds; ++k) {
+        const int l = k * kMcThreads + threadIdx.x;
+        int act = 0;
+        if (l < ch.nodes) {
+            const int r = l / nx;
+            const int x = l - r * nx;
+            const NodeInfo ni = classify_node(A, ch.base + l, x, ch.y0 + r, ch.z, g, L);
+            const int nt = c_ntri[ni.cls];
+            act = (ni.flags != 0 || nt > 0);
+            cnt.x += act;
+            cnt.y += __popc(ni.flags);
+            cnt.z += nt;
+        }
+        if (__syncthreads_or(act)) m |= 1 << k;
     }
     int3 tot;
     block_scan3(cnt, tot, sh);
@@ -127,51 +145,71 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float*
         blk[blockIdx.x] = tot.x;
         blk[nblocks + blockIdx.x] = tot.y;
         blk[2 * nblocks + blockIdx.x] = tot.z;
+        mask[blockIdx.x] = m;
     }
 }
 
-constexpr int kScanThreads = 1024;
+// Exclusive scan of the three chunk-count arrays (length nb) in tiles of
+// kScanTile: tile sums, one CTA over the tile sums, then each tile writes
+// off[a * (nb + 1) + i]; totals go to off[a * (nb + 1) + nb].
+constexpr int kScanTile = 2048;
 
-// Exclusive scan of the 3 per-CTA count arrays; totals to off[3 * (nb + 1) ..]
-__global__ void __launch_bounds__(kScanThreads) k_mc_scan(const int* __restrict__ blk, int nb, int* off,
-                                                          int* totals) {
-    __shared__ int sh[kScanThreads / 32];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int per = (nb + kScanThreads - 1) / kScanThreads;
-    const int b0 = min(nb, t * per), b1 = min(nb, b0 + per);
-    for (int a = 0; a < 3; ++a) {
-        const int* src = blk + (size_t)a * nb;
-        int* dst = off + (size_t)a * (nb + 1);
-        int s = 0;
-        for (int b = b0; b < b1; ++b) s += src[b];
-        int inc = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += v;
+__global__ void __launch_bounds__(kMcThreads) k_mc_tile_sums(const int* __restrict__ blk, int nb, int3* tile) {
+    __shared__ int3 sh[kMcThreads / 32];
+    int3 v = make_int3(0, 0, 0);
+    for (int k = 0; k < kScanTile / kMcThreads; ++k) {
+        const int i = blockIdx.x * kScanTile + k * kMcThreads + threadIdx.x;
+        if (i < nb) {
+            v.x += blk[i];
+            v.y += blk[nb + i];
+            v.z += blk[2 * nb + i];
         }
-        if (lane == 31) sh[wid] = inc;
-        __syncthreads();
-        if (wid == 0) {
-            int w = sh[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += v;
-            }
-            sh[lane] = w;
+    }
+    int3 tot;
+    block_scan3(v, tot, sh);
+    if (threadIdx.x == 0) tile[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_tile_scan(int3* tile, int ntiles, int nb, int* off) {
+    __shared__ int3 sh[kMcThreads / 32];
+    int3 carry = make_int3(0, 0, 0);
+    for (int base = 0; base < ntiles; base += kMcThreads) {
+        const int i = base + threadIdx.x;
+        const int3 v = i < ntiles ? tile[i] : make_int3(0, 0, 0);
+        int3 tot;
+        const int3 ex = block_scan3(v, tot, sh);
+        if (i < ntiles) tile[i] = make_int3(carry.x + ex.x, carry.y + ex.y, carry.z + ex.z);
+        carry.x += tot.x;
+        carry.y += tot.y;
+        carry.z += tot.z;
+    }
+    if (threadIdx.x == 0) {
+        off[nb] = carry.x;
+        off[(nb + 1) + nb] = carry.y;
+        off[2 * (nb + 1) + nb] = carry.z;
+        off[3 * (nb + 1) + 0] = carry.x;     // totals for the host
+        off[3 * (nb + 1) + 1] = carry.y;
+        off[3 * (nb + 1) + 2] = carry.z;
+    }
+}
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_tile_write(const int* __restrict__ blk, int nb,
+                                                              const int3* __restrict__ tile, int* off) {
+    __shared__ int3 sh[kMcThreads / 32];
+    int3 run = tile[blockIdx.x];
+    for (int k = 0; k < kScanTile / kMcThreads; ++k) {
+        const int i = blockIdx.x * kScanTile + k * kMcThreads + threadIdx.x;
+        const int3 v = i < nb ? make_int3(blk[i], blk[nb + i], blk[2 * nb + i]) : make_int3(0, 0, 0);
+        int3 tot;
+        const int3 ex = block_scan3(v, tot, sh);
+        if (i < nb) {
+            off[i] = run.x + ex.x;
+            off[(nb + 1) + i] = run.y + ex.y;
+            off[2 * (nb + 1) + i] = run.z + ex.z;
         }
-        __syncthreads();
-        int run = inc - s + (wid ? sh[wid - 1] : 0);
-        for (int b = b0; b < b1; ++b) {
-            dst[b] = run;
-            run += src[b];
-        }
-        if (t == kScanThreads - 1) {
-            dst[nb] = run;
-            totals[a] = run;
-        }
-        __syncthreads();
+        run.x += tot.x;
+        run.y += tot.y;
+        run.z += tot.z;
     }
 }
 
@@ -183,14 +221,17 @@ __device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t 
 }
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
-                                                        const double* __restrict__ level, int64_t M,
-                                                        const int* __restrict__ blk, const int* __restrict__ off,
-                                                        int nblocks, int4* __restrict__ nodes,
-                                                        float* __restrict__ verts, float* __restrict__ vnrm) {
+                                                        const double* __restrict__ level,
+                                                        const int* __restrict__ blk, const int* __restrict__ mask,
+                                                        const int* __restrict__ off, int nblocks,
+                                                        int4* __restrict__ nodes, float* __restrict__ verts,
+                                                        float* __restrict__ vnrm) {
     __shared__ int3 sh[kMcThreads / 32];
     if (blk[blockIdx.x] == 0) return;           // no surface in this chunk (block-uniform)
+    const int m = mask[blockIdx.x];
     const double Ld = level[0];
     const float L = __double2float_ru(Ld);
+    const Chunk ch = chunk_of(g, blockIdx.x);
     int ia = off[blockIdx.x];
     int iv = off[(nblocks + 1) + blockIdx.x];
     int it = off[2 * (nblocks + 1) + blockIdx.x];
@@ -198,14 +239,20 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
     const int64_t st[3] = {1, (int64_t)nx, (int64_t)nx * ny};
     const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
     const int nn[3] = {nx, ny, nz};
-    for (int k = 0; k < kNodesPerThread; ++k) {
-        const int64_t n = (int64_t)blockIdx.x * kMcChunk + k * kMcThreads + threadIdx.x;
+    const int rounds = (ch.nodes + kMcThreads - 1) / kMcThreads;
+    for (int k = 0; k < rounds; ++k) {
+        if (!((m >> k) & 1)) continue;          // block-uniform
+        const int l = k * kMcThreads + threadIdx.x;
         NodeInfo info;
         info.flags = 0;
         info.cls = 0;
         int q[3] = {0, 0, 0};
-        if (n < M) {
-            node_xyz(n, g, q[0], q[1], q[2]);
+        const int64_t n = ch.base + l;
+        if (l < ch.nodes) {
+            const int r = l / nx;
+            q[0] = l - r * nx;
+            q[1] = ch.y0 + r;
+            q[2] = ch.z;
             info = classify_node(A, n, q[0], q[1], q[2], g, L);
         }
         const int nt = c_ntri[info.cls];
@@ -305,9 +352,10 @@ __global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const doubl
     const int64_t ncell = (int64_t)cx * cy * cz;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ncell) return;
-    const int x = (int)(i % cx);
-    const int y = (int)((i / cx) % cy);
     const int z = (int)(i / ((int64_t)cx * cy));
+    const int rem = (int)(i - (int64_t)z * cx * cy);
+    const int y = rem / cx;
+    const int x = rem - y * cx;
     const int64_t n = x + (int64_t)g.n[0] * (y + (int64_t)g.n[1] * z);
     out[i] = (uint8_t)classify_node(A, n, x, y, z, g, __double2float_ru(level[0])).cls;
 }
@@ -328,27 +376,29 @@ cudaError_t mc_init() {
 }
 
 cudaError_t launch_mc_count(ftr_ctx* c) {
+    const int nb = c->mc_blocks;
     prof_begin(c, ST_MC_COUNT);
-    k_mc_count<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->M, c->d_mc_blk,
-                                                          c->mc_blocks);
+    k_mc_count<<<nb, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, c->d_mc_mask, nb);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
     if (e != cudaSuccess) return e;
     prof_begin(c, ST_MC_SCAN);
-    k_mc_scan<<<1, kScanThreads, 0, c->stream>>>(c->d_mc_blk, c->mc_blocks, c->d_mc_off,
-                                                c->d_mc_off + 3 * (c->mc_blocks + 1));
-    c->launches++;
+    const int ntiles = (nb + kScanTile - 1) / kScanTile;
+    k_mc_tile_sums<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nb, c->d_mc_tile);
+    k_mc_tile_scan<<<1, kMcThreads, 0, c->stream>>>(c->d_mc_tile, ntiles, nb, c->d_mc_off);
+    k_mc_tile_write<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nb, c->d_mc_tile, c->d_mc_off);
+    c->launches += 3;
     e = cudaGetLastError();
     prof_end(c, ST_MC_SCAN);
     if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(c->h_mc_tot, c->d_mc_off + 3 * (c->mc_blocks + 1), 3 * sizeof(int),
-                           cudaMemcpyDeviceToHost, c->stream);
+    return cudaMemcpyAsync(c->h_mc_tot, c->d_mc_off + 3 * (nb + 1), 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream);
 }
 
 cudaError_t launch_mc_emit(ftr_ctx* c) {
     prof_begin(c, ST_MC_EMIT);
-    k_mc_emit<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->M, c->d_mc_blk,
+    k_mc_emit<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, c->d_mc_mask,
                                                          c->d_mc_off, c->mc_blocks, c->d_mc_nodes, c->d_verts,
                                                          c->d_vnrm);
     c->launches++;

@@ -96,95 +96,124 @@ __global__ void k_brick_fill(const int4* __restrict__ pbase, int64_t n, GridDev 
             }
 }
 
-// One CTA of 1024 threads: exclusive scan of the brick counts, dense slots
-// for the touched bricks, and the z-range of touched bricks.
-constexpr int kScanThreads = 1024;
+// Exclusive scan of the brick counts in three coalesced launches over tiles
+// of kTile bricks: (1) per-tile sums of the counts and of the touched
+// bricks, (2) one CTA scans the tile sums, (3) each tile rescans itself
+// with its offset and writes the brick offsets, the dense slot of every
+// touched brick (-1 otherwise), the list of touched bricks and the z-range.
+constexpr int kScanT = 256;
+constexpr int kTile = 2048;
 
-__global__ void __launch_bounds__(kScanThreads) k_brick_scan(const int* __restrict__ cnt, int nb, int nbxy,
-                                                             int* off, int* cursor, int* slot, int* active,
-                                                             int* meta) {
-    __shared__ int s_sum[kScanThreads / 32], s_act[kScanThreads / 32];
-    __shared__ int s_zmin, s_zmax;
-    const int t = threadIdx.x;
-    const int per = (nb + kScanThreads - 1) / kScanThreads;
-    const int b0 = min(nb, t * per), b1 = min(nb, b0 + per);
-    if (t == 0) {
-        s_zmin = 0x7fffffff;
-        s_zmax = -1;
-    }
-    int sum = 0, act = 0;
-    for (int b = b0; b < b1; ++b) {
-        int c = cnt[b];
-        sum += c;
-        act += (c > 0);
-    }
-    // block exclusive scan of (sum, act)
-    const int lane = t & 31, wid = t >> 5;
-    int is = sum, ia = act;
+__device__ __forceinline__ int2 block_scan2(int2 v, int2& total, int2* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int2 inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int vs = __shfl_up_sync(0xffffffffu, is, o);
-        int va = __shfl_up_sync(0xffffffffu, ia, o);
+        const int a = __shfl_up_sync(0xffffffffu, inc.x, o);
+        const int b = __shfl_up_sync(0xffffffffu, inc.y, o);
         if (lane >= o) {
-            is += vs;
-            ia += va;
+            inc.x += a;
+            inc.y += b;
         }
     }
-    if (lane == 31) {
-        s_sum[wid] = is;
-        s_act[wid] = ia;
-    }
+    if (lane == 31) sh[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        int ws = s_sum[lane], wa = s_act[lane];
+        int2 w = lane < kScanT / 32 ? sh[lane] : make_int2(0, 0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int vs = __shfl_up_sync(0xffffffffu, ws, o);
-            int va = __shfl_up_sync(0xffffffffu, wa, o);
+            const int a = __shfl_up_sync(0xffffffffu, w.x, o);
+            const int b = __shfl_up_sync(0xffffffffu, w.y, o);
             if (lane >= o) {
-                ws += vs;
-                wa += va;
+                w.x += a;
+                w.y += b;
             }
         }
-        s_sum[lane] = ws;
-        s_act[lane] = wa;
+        if (lane < kScanT / 32) sh[lane] = w;
     }
     __syncthreads();
-    int es = is - sum + (wid ? s_sum[wid - 1] : 0);
-    int ea = ia - act + (wid ? s_act[wid - 1] : 0);
-    int zmin = 0x7fffffff, zmax = -1;
-    for (int b = b0; b < b1; ++b) {
-        int c = cnt[b];
-        off[b] = es;
-        cursor[b] = es;
-        if (c > 0) {
-            slot[b] = ea;
-            active[ea] = b;
-            ++ea;
-            int bz = b / nbxy;
-            zmin = min(zmin, bz);
-            zmax = max(zmax, bz);
-        } else {
-            slot[b] = -1;
+    const int2 before = wid ? sh[wid - 1] : make_int2(0, 0);
+    total = sh[kScanT / 32 - 1];
+    __syncthreads();
+    return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
+}
+
+__global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restrict__ cnt, int nb, int2* tile_sum) {
+    __shared__ int2 sh[kScanT / 32];
+    int2 v = make_int2(0, 0);
+    for (int k = 0; k < kTile / kScanT; ++k) {
+        const int b = blockIdx.x * kTile + k * kScanT + threadIdx.x;
+        if (b < nb) {
+            const int c = cnt[b];
+            v.x += c;
+            v.y += (c > 0);
         }
-        es += c;
+    }
+    int2 tot;
+    block_scan2(v, tot, sh);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// One CTA: exclusive scan of the tile sums in place; totals into meta.
+__global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int2* tile_sum, int ntiles, int nb, int* off,
+                                                            int* meta) {
+    __shared__ int2 sh[kScanT / 32];
+    int2 carry = make_int2(0, 0);
+    for (int base = 0; base < ntiles; base += kScanT) {
+        const int i = base + threadIdx.x;
+        const int2 v = i < ntiles ? tile_sum[i] : make_int2(0, 0);
+        int2 tot;
+        const int2 ex = block_scan2(v, tot, sh);
+        if (i < ntiles) tile_sum[i] = make_int2(carry.x + ex.x, carry.y + ex.y);
+        carry.x += tot.x;
+        carry.y += tot.y;
+    }
+    if (threadIdx.x == 0) {
+        off[nb] = carry.x;
+        meta[0] = carry.y;
+        meta[1] = carry.x;
+        meta[2] = 0x7fffffff;
+        meta[3] = -1;
+    }
+}
+
+__global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restrict__ cnt, int nb, int nbxy,
+                                                             const int2* __restrict__ tile_off, int* off,
+                                                             int* cursor, int* slot, int* active, int* meta) {
+    __shared__ int2 sh[kScanT / 32];
+    int2 run = tile_off[blockIdx.x];
+    int zmin = 0x7fffffff, zmax = -1;
+    for (int k = 0; k < kTile / kScanT; ++k) {
+        const int b = blockIdx.x * kTile + k * kScanT + threadIdx.x;
+        const int c = b < nb ? cnt[b] : 0;
+        int2 tot;
+        const int2 ex = block_scan2(make_int2(c, c > 0), tot, sh);
+        if (b < nb) {
+            off[b] = run.x + ex.x;
+            cursor[b] = run.x + ex.x;
+            if (c > 0) {
+                slot[b] = run.y + ex.y;
+                active[run.y + ex.y] = b;
+                const int bz = b / nbxy;
+                zmin = min(zmin, bz);
+                zmax = max(zmax, bz);
+            } else {
+                slot[b] = -1;
+            }
+        }
+        run.x += tot.x;
+        run.y += tot.y;
     }
     if (zmax >= 0) {
-        atomicMin(&s_zmin, zmin);
-        atomicMax(&s_zmax, zmax);
-    }
-    __syncthreads();
-    if (t == kScanThreads - 1) {
-        off[nb] = es;
-        meta[0] = ea;
-        meta[1] = es;
-        meta[2] = s_zmax >= 0 ? s_zmin : 0;
-        meta[3] = s_zmax;
+        atomicMin(&meta[2], zmin);
+        atomicMax(&meta[3], zmax);
     }
 }
 
 constexpr int kAccThreads = 256;
 constexpr float kFix = 1099511627776.0f;    // 2^40
+
+constexpr int kStage = 128;   // point records staged in shared memory per batch
 
 __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const int* __restrict__ active,
                                                              const int* __restrict__ meta,
@@ -195,6 +224,9 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const float4* __restrict__ pnrm,
                                                              float* __restrict__ vpool) {
     __shared__ unsigned long long acc[4][kBrickVox];
+    __shared__ int4 s_base[kStage];
+    __shared__ float4 s_frac[kStage];
+    __shared__ float4 s_nrm[kStage];
     const int nact = meta[0];
     const int tid = threadIdx.x;
     const int o = tid & 63;
@@ -203,41 +235,47 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
     for (int s = blockIdx.x; s < nact; s += gridDim.x) {
         const int b = active[s];
         const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
-        const int org[3] = {bx * kBrick, by * kBrick, bz * kBrick};
+        const int orgx = bx * kBrick, orgy = by * kBrick, orgz = bz * kBrick;
         for (int k = tid; k < 4 * kBrickVox; k += kAccThreads) (&acc[0][0])[k] = 0ull;
-        __syncthreads();
         const int e0 = off[b], e1 = off[b + 1];
-        if (g.mode == FTR_SPLAT_WEIGHTED) {
-            for (int e = e0 + pl; e < e1; e += kAccThreads / 64) {
-                const int i = entries[e];
-                const int4 pb = pbase[i];
-                const int lx = pb.x - 1 + ox - org[0];
-                const int ly = pb.y - 1 + oy - org[1];
-                const int lz = pb.z - 1 + oz - org[2];
-                if ((unsigned)lx >= kBrick || (unsigned)ly >= kBrick || (unsigned)lz >= kBrick) continue;
-                const float4 fr = pfrac[i];
-                const float4 nr = pnrm[i];
-                // X - p(q) = (t - q) h with t - q = frac + 1 - offset
-                const float dx = (fr.x + 1.0f - (float)ox) * g.hf[0];
-                const float dy = (fr.y + 1.0f - (float)oy) * g.hf[1];
-                const float dz = (fr.z + 1.0f - (float)oz) * g.hf[2];
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
-                const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
-                const int li = lx + kBrick * (ly + kBrick * lz);
-                atomicAdd(&acc[0][li], (unsigned long long)__float2ll_rn(e1v * nr.x * kFix));
-                atomicAdd(&acc[1][li], (unsigned long long)__float2ll_rn(e1v * nr.y * kFix));
-                atomicAdd(&acc[2][li], (unsigned long long)__float2ll_rn(e1v * nr.z * kFix));
-                atomicAdd(&acc[3][li], (unsigned long long)__float2ll_rn(e2v * kFix));
+        for (int eb = e0; eb < e1; eb += kStage) {
+            const int nbatch = min(kStage, e1 - eb);
+            __syncthreads();
+            if (tid < nbatch) {
+                const int i = entries[eb + tid];
+                s_base[tid] = pbase[i];
+                s_frac[tid] = pfrac[i];
+                s_nrm[tid] = pnrm[i];
             }
-        } else {
-            for (int e = e0 + tid; e < e1; e += kAccThreads) {
-                const int i = entries[e];
-                const int4 pb = pbase[i];
-                const int lx = pb.x + ((pb.w >> 1) & 1) - org[0];
-                const int ly = pb.y + ((pb.w >> 2) & 1) - org[1];
-                const int lz = pb.z + ((pb.w >> 3) & 1) - org[2];
-                const float4 nr = pnrm[i];
+            __syncthreads();
+            if (g.mode == FTR_SPLAT_WEIGHTED) {
+                for (int p = pl; p < nbatch; p += kAccThreads / 64) {
+                    const int4 pb = s_base[p];
+                    const int lx = pb.x - 1 + ox - orgx;
+                    const int ly = pb.y - 1 + oy - orgy;
+                    const int lz = pb.z - 1 + oz - orgz;
+                    if ((unsigned)lx >= kBrick || (unsigned)ly >= kBrick || (unsigned)lz >= kBrick) continue;
+                    const float4 fr = s_frac[p];
+                    const float4 nr = s_nrm[p];
+                    // X - p(q) = (t - q) h with t - q = frac + 1 - offset
+                    const float dx = (fr.x + 1.0f - (float)ox) * g.hf[0];
+                    const float dy = (fr.y + 1.0f - (float)oy) * g.hf[1];
+                    const float dz = (fr.z + 1.0f - (float)oz) * g.hf[2];
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
+                    const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
+                    const int li = lx + kBrick * (ly + kBrick * lz);
+                    atomicAdd(&acc[0][li], (unsigned long long)__float2ll_rn(e1v * nr.x * kFix));
+                    atomicAdd(&acc[1][li], (unsigned long long)__float2ll_rn(e1v * nr.y * kFix));
+                    atomicAdd(&acc[2][li], (unsigned long long)__float2ll_rn(e1v * nr.z * kFix));
+                    atomicAdd(&acc[3][li], (unsigned long long)__float2ll_rn(e2v * kFix));
+                }
+            } else if (tid < nbatch) {
+                const int4 pb = s_base[tid];
+                const int lx = pb.x + ((pb.w >> 1) & 1) - orgx;
+                const int ly = pb.y + ((pb.w >> 2) & 1) - orgy;
+                const int lz = pb.z + ((pb.w >> 3) & 1) - orgz;
+                const float4 nr = s_nrm[tid];
                 const int li = lx + kBrick * (ly + kBrick * lz);
                 atomicAdd(&acc[0][li], (unsigned long long)__float2ll_rn(nr.x * kFix));
                 atomicAdd(&acc[1][li], (unsigned long long)__float2ll_rn(nr.y * kFix));
@@ -317,10 +355,13 @@ cudaError_t launch_splat(ftr_ctx* c) {
         c->launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_brick_scan<<<1, kScanThreads, 0, c->stream>>>(c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
-                                                   c->d_brick_off, c->d_brick_cursor, c->d_brick_slot,
-                                                   c->d_active, c->d_meta);
-    c->launches++;
+    const int ntiles = (c->n_bricks + kTile - 1) / kTile;
+    k_brick_tile_sums<<<ntiles, kScanT, 0, c->stream>>>(c->d_brick_cnt, c->n_bricks, c->d_tile);
+    k_brick_tile_scan<<<1, kScanT, 0, c->stream>>>(c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta);
+    k_brick_tile_write<<<ntiles, kScanT, 0, c->stream>>>(c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
+                                                        c->d_tile, c->d_brick_off, c->d_brick_cursor,
+                                                        c->d_brick_slot, c->d_active, c->d_meta);
+    c->launches += 3;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (n > 0) {
         k_brick_fill<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->pts.base, n, c->g, c->d_brick_cursor,

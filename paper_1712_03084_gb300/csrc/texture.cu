@@ -8,9 +8,11 @@
 // that depth pixel (0 when invisible, or when the RGB projection leaves the
 // RGB image); the UV is the RGB projection in pixels.  The headless stand-in
 // for the paper's OpenGL multitexture blend is the weighted mean of bilinear
-// RGB samples, stored as floor(c + 1/2).  Projections and the blend run in
-// float64 so that every discrete decision (pixel choice, visibility) matches
-// a float64 evaluation of the same formulas.
+// RGB samples, stored as floor(c + 1/2).  Every discrete decision (pixel
+// choice, z > 0, the depth test, the RGB bounds) must match a float64
+// evaluation of the same formulas: each camera is evaluated in float32 first
+// and redone in float64 when any decision quantity falls within a guard band
+// (2e-3 px, 1e-4 m) of its threshold, far wider than the float32 error.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -19,17 +21,92 @@
 namespace ftr {
 namespace {
 
-__device__ __forceinline__ void project(const double* K, const double* RT, const double X[3], double& u, double& v,
-                                        double& z) {
-    const double xc = RT[0] * X[0] + RT[1] * X[1] + RT[2] * X[2] + RT[3];
-    const double yc = RT[4] * X[0] + RT[5] * X[1] + RT[6] * X[2] + RT[7];
-    const double zc = RT[8] * X[0] + RT[9] * X[1] + RT[10] * X[2] + RT[11];
-    const double uu = K[0] * xc + K[1] * yc + K[2] * zc;
-    const double vv = K[3] * xc + K[4] * yc + K[5] * zc;
-    const double ww = K[6] * xc + K[7] * yc + K[8] * zc;
+template <class T>
+__device__ __forceinline__ void project(const T* K, const T* RT, const T X[3], T& u, T& v, T& z) {
+    const T xc = RT[0] * X[0] + RT[1] * X[1] + RT[2] * X[2] + RT[3];
+    const T yc = RT[4] * X[0] + RT[5] * X[1] + RT[6] * X[2] + RT[7];
+    const T zc = RT[8] * X[0] + RT[9] * X[1] + RT[10] * X[2] + RT[11];
+    const T uu = K[0] * xc + K[1] * yc + K[2] * zc;
+    const T vv = K[3] * xc + K[4] * yc + K[5] * zc;
+    const T ww = K[6] * xc + K[7] * yc + K[8] * zc;
     u = uu / ww;
     v = vv / ww;
     z = zc;
+}
+
+template <class T> struct Cams;
+template <> struct Cams<float> {
+    __device__ static const float* K(const ViewDev& v) { return v.Kf; }
+    __device__ static const float* RT(const ViewDev& v) { return v.RTf; }
+    __device__ static const float* Krgb(const ViewDev& v) { return v.Krgbf; }
+    __device__ static const float* RTrgb(const ViewDev& v) { return v.RTrgbf; }
+};
+template <> struct Cams<double> {
+    __device__ static const double* K(const ViewDev& v) { return v.K; }
+    __device__ static const double* RT(const ViewDev& v) { return v.RT; }
+    __device__ static const double* Krgb(const ViewDev& v) { return v.Krgb; }
+    __device__ static const double* RTrgb(const ViewDev& v) { return v.RTrgb; }
+};
+
+template <class T>
+__device__ __forceinline__ bool near_half_int(T u, T band) {
+    const T s = u + (T)0.5;
+    const T d = s - floor(s);
+    return d < band || d > (T)1 - band;
+}
+
+// One camera for one vertex in precision T.  With GUARD set, returns false
+// (and nothing else) when a decision lies inside the guard band.
+template <class T, bool GUARD>
+__device__ __forceinline__ bool eval_camera(const ViewDev& vw, const T X[3], T tau, T& wk, T& ur, T& vr, T rgb[3]) {
+    const T band_px = (T)2e-3, band_m = (T)1e-4;
+    T u, v, z;
+    project<T>(Cams<T>::K(vw), Cams<T>::RT(vw), X, u, v, z);
+    wk = 0;
+    ur = -1;
+    vr = -1;
+    if (GUARD && fabs(z) < band_m) return false;
+    if (z > (T)0) {
+        if (GUARD && (near_half_int(u, band_px) || near_half_int(v, band_px))) return false;
+        const T px = floor(u + (T)0.5), py = floor(v + (T)0.5);
+        if (px >= (T)0 && px < (T)vw.w && py >= (T)0 && py < (T)vw.h) {
+            const int64_t pi = (int64_t)py * vw.w + (int64_t)px;
+            const T D = (T)vw.depth[pi];
+            if (D > (T)0) {
+                const T dz = fabs(D - z);
+                if (GUARD && fabs(dz - tau) < band_m) return false;
+                if (dz <= tau) wk = (T)vw.conf[pi];
+            }
+        }
+    }
+    if (wk > (T)0) {
+        T zr;
+        project<T>(Cams<T>::Krgb(vw), Cams<T>::RTrgb(vw), X, ur, vr, zr);
+        const T xmax = (T)(vw.rgb_w - 1), ymax = (T)(vw.rgb_h - 1);
+        if (GUARD && (fabs(zr) < band_m || fabs(ur) < band_px || fabs(ur - xmax) < band_px ||
+                      fabs(vr) < band_px || fabs(vr - ymax) < band_px))
+            return false;
+        if (!(zr > (T)0 && ur >= (T)0 && ur <= xmax && vr >= (T)0 && vr <= ymax)) wk = 0;
+    }
+    if (wk > (T)0) {
+        const T fx0 = floor(ur), fy0 = floor(vr);
+        const T fx = ur - fx0, fy = vr - fy0;
+        const int x0 = (int)fx0, y0 = (int)fy0;
+        const int xa = min(max(x0, 0), vw.rgb_w - 1), xb = min(max(x0 + 1, 0), vw.rgb_w - 1);
+        const int ya = min(max(y0, 0), vw.rgb_h - 1), yb = min(max(y0 + 1, 0), vw.rgb_h - 1);
+        const uint8_t* p00 = vw.rgb + 3 * ((int64_t)ya * vw.rgb_w + xa);
+        const uint8_t* p10 = vw.rgb + 3 * ((int64_t)ya * vw.rgb_w + xb);
+        const uint8_t* p01 = vw.rgb + 3 * ((int64_t)yb * vw.rgb_w + xa);
+        const uint8_t* p11 = vw.rgb + 3 * ((int64_t)yb * vw.rgb_w + xb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            rgb[c] = ((T)1 - fx) * ((T)1 - fy) * (T)p00[c] + fx * ((T)1 - fy) * (T)p10[c] +
+                     ((T)1 - fx) * fy * (T)p01[c] + fx * fy * (T)p11[c];
+    } else {
+        ur = -1;
+        vr = -1;
+    }
+    return true;
 }
 
 __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __restrict__ verts, int64_t nv,
@@ -37,66 +114,43 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
                                                  uint8_t* __restrict__ rgbout, uint8_t* __restrict__ texout) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
-    const double X[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
-    double acc[3] = {0.0, 0.0, 0.0};
-    double wsum = 0.0;
+    const float Xf[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
+    float acc[3] = {0.f, 0.f, 0.f};
+    float wsum = 0.f;
     for (int k = 0; k < vs.k; ++k) {
         const ViewDev& vw = vs.v[k];
-        double u, v, z;
-        project(vw.K, vw.RT, X, u, v, z);
-        double wk = 0.0;
-        double ur = -1.0, vr = -1.0;
-        if (z > 0.0) {
-            const double px = floor(u + 0.5), py = floor(v + 0.5);
-            if (px >= 0.0 && px < (double)vw.w && py >= 0.0 && py < (double)vw.h) {
-                const int64_t pi = (int64_t)py * vw.w + (int64_t)px;
-                const double D = vw.depth[pi];
-                if (D > 0.0 && fabs(D - z) <= tau) wk = vw.conf[pi];
-            }
+        float wk, ur, vr, rgb[3];
+        if (!eval_camera<float, true>(vw, Xf, (float)tau, wk, ur, vr, rgb)) {
+            const double Xd[3] = {Xf[0], Xf[1], Xf[2]};
+            double wd, ud, vd, cd[3];
+            eval_camera<double, false>(vw, Xd, tau, wd, ud, vd, cd);
+            wk = (float)wd;
+            ur = (float)ud;
+            vr = (float)vd;
+            rgb[0] = (float)cd[0];
+            rgb[1] = (float)cd[1];
+            rgb[2] = (float)cd[2];
         }
-        if (wk > 0.0) {
-            double zr;
-            project(vw.Krgb, vw.RTrgb, X, ur, vr, zr);
-            if (!(zr > 0.0 && ur >= 0.0 && ur <= (double)(vw.rgb_w - 1) && vr >= 0.0 &&
-                  vr <= (double)(vw.rgb_h - 1)))
-                wk = 0.0;
-        }
-        if (wk > 0.0) {
-            const double fx0 = floor(ur), fy0 = floor(vr);
-            const double fx = ur - fx0, fy = vr - fy0;
-            const int x0 = (int)fx0, y0 = (int)fy0;
-            const int xa = min(max(x0, 0), vw.rgb_w - 1), xb = min(max(x0 + 1, 0), vw.rgb_w - 1);
-            const int ya = min(max(y0, 0), vw.rgb_h - 1), yb = min(max(y0 + 1, 0), vw.rgb_h - 1);
-            const uint8_t* p00 = vw.rgb + 3 * ((int64_t)ya * vw.rgb_w + xa);
-            const uint8_t* p10 = vw.rgb + 3 * ((int64_t)ya * vw.rgb_w + xb);
-            const uint8_t* p01 = vw.rgb + 3 * ((int64_t)yb * vw.rgb_w + xa);
-            const uint8_t* p11 = vw.rgb + 3 * ((int64_t)yb * vw.rgb_w + xb);
+        if (wk > 0.f) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double s = (1.0 - fx) * (1.0 - fy) * p00[c] + fx * (1.0 - fy) * p10[c] +
-                                 (1.0 - fx) * fy * p01[c] + fx * fy * p11[c];
-                acc[c] += wk * s;
-            }
+            for (int c = 0; c < 3; ++c) acc[c] += wk * rgb[c];
             wsum += wk;
-        } else {
-            ur = -1.0;
-            vr = -1.0;
         }
-        if (wout) wout[i * vs.k + k] = (float)wk;
+        if (wout) wout[i * vs.k + k] = wk;
         if (uvout) {
-            uvout[2 * (i * vs.k + k)] = (float)ur;
-            uvout[2 * (i * vs.k + k) + 1] = (float)vr;
+            uvout[2 * (i * vs.k + k)] = ur;
+            uvout[2 * (i * vs.k + k) + 1] = vr;
         }
     }
     if (rgbout) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double col = wsum > 0.0 ? floor(acc[c] / wsum + 0.5) : 0.0;
-            col = col < 0.0 ? 0.0 : (col > 255.0 ? 255.0 : col);
+            float col = wsum > 0.f ? floorf(acc[c] / wsum + 0.5f) : 0.f;
+            col = fminf(fmaxf(col, 0.f), 255.f);
             rgbout[3 * i + c] = (uint8_t)col;
         }
     }
-    if (texout) texout[i] = wsum > 0.0 ? 1 : 0;
+    if (texout) texout[i] = wsum > 0.f ? 1 : 0;
 }
 
 }  // namespace

@@ -162,3 +162,25 @@ def test_edge_cases(ftr):
     ftr.ftr_splat(ctx.h, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), None)   # n = 0 is fine
     assert ctx.solve() == 0.0
     ctx.close()
+
+
+def test_texture_matches_oracle_on_the_same_mesh(ftr):
+    """Sec. III-C per-vertex weights, UVs and blended colour on the GPU mesh."""
+    from oracle import texture as otex
+    name = "human96"
+    c = G.CASES[name]
+    P, N, W, views = G.case_inputs(name)
+    ctx, _ = _run(ftr, name)
+    m = ctx.mesh_numpy()
+    tol = float(np.float32(0.03))
+    tex = ctx.texture_numpy(views, tol, len(m["vertices"]))
+    ref = otex.texture(m["vertices"].astype(np.float64), views, tol)
+    assert np.array_equal(tex["weights"] > 0, ref["weights"] > 0)
+    assert np.array_equal(tex["weights"], ref["weights"].astype(np.float32))
+    vis = ref["weights"] > 0
+    assert vis.mean() > 0.3
+    assert np.max(np.abs(tex["uv"][vis] - ref["uv"][vis])) <= 1e-3
+    assert np.all(tex["uv"][~vis] == -1)
+    assert np.array_equal(tex["textured"], ref["textured"])
+    assert np.max(np.abs(tex["rgb"].astype(int) - ref["rgb"].astype(int))) <= 1
+    ctx.close()
