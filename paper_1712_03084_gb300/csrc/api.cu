@@ -178,7 +178,6 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_level);
     dfree(c->d_level_part);
     dfree(c->d_mc_blk);
-    dfree(c->d_mc_mask);
     dfree(c->d_mc_tile);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
@@ -246,6 +245,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     g.inv_s2sq = (float)(1.0 / (s2 * s2));
     g.mode = prm.splat_mode;
     g.v_scale = prm.splat_mode == FTR_SPLAT_WEIGHTED ? s2 / s1 : 1.0;
+    g.v_scale_f = (float)g.v_scale;
     c->M = (int64_t)grid_n[0] * grid_n[1] * grid_n[2];
     c->Mh = (int64_t)(grid_n[0] / 2 + 1) * grid_n[1] * grid_n[2];
     c->n_bricks = g.nb[0] * g.nb[1] * g.nb[2];
@@ -281,9 +281,8 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     c->level_blocks = 304;
     ALLOC(c->d_level, 2);
     ALLOC(c->d_level_part, 2 * c->level_blocks);
-    c->mc_blocks = (grid_n[1] / 8) * grid_n[2];
+    c->mc_blocks = grid_n[1] * grid_n[2];      // marching cubes counts per grid row
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
-    ALLOC(c->d_mc_mask, c->mc_blocks);
     ALLOC(c->d_mc_tile, (c->mc_blocks + 2047) / 2048 + 1);
     ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
 #undef ALLOC

@@ -45,6 +45,7 @@ struct GridDev {
     float hf[3];
     float inv_s1sq, inv_s2sq;  // 1/sigma1^2, 1/sigma2^2 (world units)
     double v_scale;            // sigma2/sigma1 (weighted) or 1 (simple)
+    float v_scale_f;           // the same in float32
     int mode;
 };
 
@@ -108,9 +109,8 @@ struct ftr_ctx {
     double level_host = 0.0;
 
     // marching cubes
-    int mc_blocks = 0;
-    int* d_mc_blk = nullptr;       // 3 x mc_blocks
-    int* d_mc_mask = nullptr;      // per chunk: rounds holding surface
+    int mc_blocks = 0;             // grid rows n_y n_z
+    int* d_mc_blk = nullptr;       // 3 x mc_blocks (per grid row: active nodes, vertices, triangles)
     int3* d_mc_tile = nullptr;     // tile sums / offsets of the chunk scan
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)

@@ -3,7 +3,8 @@
 // Every accepted point contributes the trilinear interpolation of A between
 // its 8 surrounding cell-centred nodes (floor(t) .. floor(t) + 1, weights from
 // t - floor(t)); accepted points are interior, so no clamping is needed.  The
-// sum runs in float64 with a fixed grid, a fixed per-thread order and a fixed
+// interpolation runs in float32 (A itself is float32); the sum over points
+// runs in float64 with a fixed grid, a fixed per-thread order and a fixed
 // reduction tree, so L is bit-reproducible run to run.
 #include <cuda_runtime.h>
 
@@ -38,15 +39,16 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
         const int4 b = pbase[i];
         if (!(b.w & 1)) continue;
         const float4 fr = pfrac[i];
-        const double fx = fr.x, fy = fr.y, fz = fr.z;
+        const float fx = fr.x, fy = fr.y, fz = fr.z;
         const float* a0 = A + b.x + (int64_t)nx * b.y + nxy * b.z;
-        const double c00 = (1.0 - fx) * a0[0] + fx * a0[1];
-        const double c10 = (1.0 - fx) * a0[nx] + fx * a0[nx + 1];
-        const double c01 = (1.0 - fx) * a0[nxy] + fx * a0[nxy + 1];
-        const double c11 = (1.0 - fx) * a0[nxy + nx] + fx * a0[nxy + nx + 1];
-        const double c0 = (1.0 - fy) * c00 + fy * c10;
-        const double c1 = (1.0 - fy) * c01 + fy * c11;
-        sum += (1.0 - fz) * c0 + fz * c1;
+        // trilinear interpolation in float32; the sum over points in float64
+        const float c00 = fmaf(fx, a0[1] - a0[0], a0[0]);
+        const float c10 = fmaf(fx, a0[nx + 1] - a0[nx], a0[nx]);
+        const float c01 = fmaf(fx, a0[nxy + 1] - a0[nxy], a0[nxy]);
+        const float c11 = fmaf(fx, a0[nxy + nx + 1] - a0[nxy + nx], a0[nxy + nx]);
+        const float c0 = fmaf(fy, c10 - c00, c00);
+        const float c1 = fmaf(fy, c11 - c01, c01);
+        sum += (double)fmaf(fz, c1 - c0, c0);
         cnt += 1.0;
     }
     const double s = block_sum(sum, sh);

@@ -2,20 +2,25 @@
 //
 // Corner bit = 1 iff A >= L with A promoted to float64.  Because A is float32,
 // that is the same as A >= Lf with Lf = L rounded up to float32, so the
-// kernels compare in float32 and still take the float64 decision.  A node owns the
-// grid edges toward +x, +y, +z; an edge carries a vertex when its two bits
+// kernels compare in float32 and still take the float64 decision.  A node owns
+// the grid edges toward +x, +y, +z; an edge carries a vertex when its two bits
 // differ.  Vertex ids are the rank of (node, axis) in linear node order and
 // triangles follow cell order then table order, so the mesh does not depend
-// on scheduling.  Launches:
-//   count  one CTA per chunk of 8 consecutive grid rows: active nodes (owning
-//          a vertex or lower corner of a cell with triangles), vertices,
-//          triangles, and a mask of the 256-node rounds that hold any
-//   scan   three coalesced launches: exclusive offsets of the chunk counts
-//   emit   same chunks again, skipping empty chunks and empty rounds:
-//          block-local scan, one 16-byte record per active
-//          node (node, edge bits | class << 8, first vertex, first triangle),
-//          vertex positions t = (L - A0)/(A1 - A0) in float64 and normals
-//          -grad A (central differences, one-sided at the border, lerped)
+// on scheduling.
+//
+// One warp walks one grid row (y, z) in 32-node segments.  Per segment it
+// loads the rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) once, turns them into
+// four 32-bit ballots, and reads every node's edge bits and cube class from
+// those masks (the +x neighbour is the next bit; lane 31 fetches the first
+// node of the next segment).  Launches:
+//   count  per row: active nodes (owning a vertex or lower corner of a cell
+//          with triangles), vertices, triangles
+//   scan   three coalesced launches: exclusive offsets of the row counts
+//   emit   rows with surface only: one 16-byte record per active node (node,
+//          edge bits | class << 8, first vertex, first triangle), vertex
+//          positions t = (L - A0)/(A1 - A0) in float64 and normals -grad A
+//          (central differences, one-sided at the border, lerped); in-row
+//          offsets come from ballot popcounts
 //   tris   one thread per active node: triangle corners from the case table;
 //          an edge owned by another node is found by binary search in the
 //          sorted node records.
@@ -58,21 +63,97 @@ __device__ __forceinline__ NodeInfo classify_node(const float* __restrict__ A, i
     return r;
 }
 
-// Chunk c covers rows y0 .. y0+7 of plane z (8 n_x consecutive nodes).
-struct Chunk {
-    int z, y0;
-    int64_t base;   // linear index of its first node
-    int nodes;
+constexpr int kRowsPerCta = kMcThreads / 32;
+
+// Bits of one 32-node segment of row (y, z) starting at x0.
+struct SegBits {
+    unsigned m00, m10, m01, m11;   // A >= L on rows (y,z), (y+1,z), (y,z+1), (y+1,z+1)
+    unsigned e;                    // bits 0..3: the same four rows at x0 + 32
 };
 
-__device__ __forceinline__ Chunk chunk_of(const GridDev& g, int c) {
-    const int rows8 = g.n[1] / 8;
-    Chunk k;
-    k.z = c / rows8;
-    k.y0 = (c - k.z * rows8) * 8;
-    k.base = (int64_t)g.n[0] * (k.y0 + (int64_t)g.n[1] * k.z);
-    k.nodes = 8 * g.n[0];
-    return k;
+__device__ __forceinline__ SegBits seg_bits(const float* __restrict__ A, int64_t rowbase, int x0, int nx,
+                                            int64_t sy, int64_t sz, bool hy, bool hz, float L) {
+    const int lane = threadIdx.x & 31;
+    const int x = x0 + lane;
+    const bool valid = x < nx;
+    const int64_t n = rowbase + x;
+    SegBits s;
+    s.m00 = __ballot_sync(0xffffffffu, valid && A[n] >= L);
+    s.m10 = __ballot_sync(0xffffffffu, valid && hy && A[n + sy] >= L);
+    s.m01 = __ballot_sync(0xffffffffu, valid && hz && A[n + sz] >= L);
+    s.m11 = __ballot_sync(0xffffffffu, valid && hy && hz && A[n + sy + sz] >= L);
+    unsigned e = 0;
+    if (lane == 31 && x + 1 < nx) {
+        e = (A[n + 1] >= L) | ((hy && A[n + 1 + sy] >= L) << 1) | ((hz && A[n + 1 + sz] >= L) << 2) |
+            ((hy && hz && A[n + 1 + sy + sz] >= L) << 3);
+    }
+    s.e = __shfl_sync(0xffffffffu, e, 31);
+    return s;
+}
+
+// Edge bits and cube class of this lane's node from the segment masks.
+__device__ __forceinline__ NodeInfo lane_node(const SegBits& s, int x, int nx, bool hy, bool hz) {
+    const int lane = threadIdx.x & 31;
+    const bool hx = x < nx - 1;
+    const int b0 = (s.m00 >> lane) & 1, by = (s.m10 >> lane) & 1;
+    const int bz = (s.m01 >> lane) & 1, byz = (s.m11 >> lane) & 1;
+    int bx, bxy, bxz, bxyz;
+    if (lane < 31) {
+        bx = (s.m00 >> (lane + 1)) & 1;
+        bxy = (s.m10 >> (lane + 1)) & 1;
+        bxz = (s.m01 >> (lane + 1)) & 1;
+        bxyz = (s.m11 >> (lane + 1)) & 1;
+    } else {
+        bx = s.e & 1;
+        bxy = (s.e >> 1) & 1;
+        bxz = (s.e >> 2) & 1;
+        bxyz = (s.e >> 3) & 1;
+    }
+    NodeInfo r;
+    r.flags = (hx && bx != b0) | ((hy && by != b0) << 1) | ((hz && bz != b0) << 2);
+    r.cls = (hx && hy && hz)
+                ? (b0 | (bx << 1) | (by << 2) | (bxy << 3) | (bz << 4) | (bxz << 5) | (byz << 6) | (bxyz << 7))
+                : 0;
+    return r;
+}
+
+__device__ __forceinline__ int ntri_of(int cls) { return (cls == 0 || cls == 255) ? 0 : c_ntri[cls]; }
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
+                                                         const double* __restrict__ level, int* __restrict__ cnt,
+                                                         int nrows) {
+    const float L = __double2float_ru(level[0]);
+    const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
+    if (row >= nrows) return;                    // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int y = row % ny, z = row / ny;
+    const bool hy = y < ny - 1, hz = z < nz - 1;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const int64_t rowbase = (int64_t)row * nx;
+    int na = 0, nv = 0, nt = 0;
+    for (int x0 = 0; x0 < nx; x0 += 32) {
+        const SegBits sb = seg_bits(A, rowbase, x0, nx, sy, sz, hy, hz, L);
+        const int x = x0 + lane;
+        if (x < nx) {
+            const NodeInfo ni = lane_node(sb, x, nx, hy, hz);
+            const int t = ntri_of(ni.cls);
+            na += (ni.flags != 0 || t > 0);
+            nv += __popc(ni.flags);
+            nt += t;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        na += __shfl_down_sync(0xffffffffu, na, o);
+        nv += __shfl_down_sync(0xffffffffu, nv, o);
+        nt += __shfl_down_sync(0xffffffffu, nt, o);
+    }
+    if (lane == 0) {
+        cnt[row] = na;
+        cnt[nrows + row] = nv;
+        cnt[2 * nrows + row] = nt;
+    }
 }
 
 // Block-wide exclusive scan of 3 ints (kMcThreads threads); returns totals.
@@ -114,42 +195,7 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
     return make_int3(before.x + inc.x - v.x, before.y + inc.y - v.y, before.z + inc.z - v.z);
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
-                                                         const double* __restrict__ level, int* __restrict__ blk,
-                                                         int* __restrict__ mask, int nblocks) {
-    __shared__ int3 sh[kMcThreads / 32];
-    const float L = __double2float_ru(level[0]);
-    const Chunk ch = chunk_of(g, blockIdx.x);
-    const int nx = g.n[0];
-    const int rounds = (ch.nodes + kMcThreads - 1) / kMcThreads;
-    int3 cnt = make_int3(0, 0, 0);
-    int m = 0;
-    for (int k = 0; k < rounds; ++k) {
-        const int l = k * kMcThreads + threadIdx.x;
-        int act = 0;
-        if (l < ch.nodes) {
-            const int r = l / nx;
-            const int x = l - r * nx;
-            const NodeInfo ni = classify_node(A, ch.base + l, x, ch.y0 + r, ch.z, g, L);
-            const int nt = c_ntri[ni.cls];
-            act = (ni.flags != 0 || nt > 0);
-            cnt.x += act;
-            cnt.y += __popc(ni.flags);
-            cnt.z += nt;
-        }
-        if (__syncthreads_or(act)) m |= 1 << k;
-    }
-    int3 tot;
-    block_scan3(cnt, tot, sh);
-    if (threadIdx.x == 0) {
-        blk[blockIdx.x] = tot.x;
-        blk[nblocks + blockIdx.x] = tot.y;
-        blk[2 * nblocks + blockIdx.x] = tot.z;
-        mask[blockIdx.x] = m;
-    }
-}
-
-// Exclusive scan of the three chunk-count arrays (length nb) in tiles of
+// Exclusive scan of the three row-count arrays (length nb) in tiles of
 // kScanTile: tile sums, one CTA over the tile sums, then each tile writes
 // off[a * (nb + 1) + i]; totals go to off[a * (nb + 1) + nb].
 constexpr int kScanTile = 2048;
@@ -222,66 +268,66 @@ __device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t 
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
                                                         const double* __restrict__ level,
-                                                        const int* __restrict__ blk, const int* __restrict__ mask,
-                                                        const int* __restrict__ off, int nblocks,
-                                                        int4* __restrict__ nodes, float* __restrict__ verts,
-                                                        float* __restrict__ vnrm) {
-    __shared__ int3 sh[kMcThreads / 32];
-    if (blk[blockIdx.x] == 0) return;           // no surface in this chunk (block-uniform)
-    const int m = mask[blockIdx.x];
+                                                        const int* __restrict__ cnt, const int* __restrict__ off,
+                                                        int nrows, int4* __restrict__ nodes,
+                                                        float* __restrict__ verts, float* __restrict__ vnrm) {
+    const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
+    if (row >= nrows || cnt[row] == 0) return;   // warp-uniform: no surface on this row
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const double Ld = level[0];
     const float L = __double2float_ru(Ld);
-    const Chunk ch = chunk_of(g, blockIdx.x);
-    int ia = off[blockIdx.x];
-    int iv = off[(nblocks + 1) + blockIdx.x];
-    int it = off[2 * (nblocks + 1) + blockIdx.x];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int y = row % ny, z = row / ny;
+    const bool hy = y < ny - 1, hz = z < nz - 1;
     const int64_t st[3] = {1, (int64_t)nx, (int64_t)nx * ny};
+    const int64_t rowbase = (int64_t)row * nx;
     const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
     const int nn[3] = {nx, ny, nz};
-    const int rounds = (ch.nodes + kMcThreads - 1) / kMcThreads;
-    for (int k = 0; k < rounds; ++k) {
-        if (!((m >> k) & 1)) continue;          // block-uniform
-        const int l = k * kMcThreads + threadIdx.x;
-        NodeInfo info;
-        info.flags = 0;
-        info.cls = 0;
-        int q[3] = {0, 0, 0};
-        const int64_t n = ch.base + l;
-        if (l < ch.nodes) {
-            const int r = l / nx;
-            q[0] = l - r * nx;
-            q[1] = ch.y0 + r;
-            q[2] = ch.z;
-            info = classify_node(A, n, q[0], q[1], q[2], g, L);
-        }
-        const int nt = c_ntri[info.cls];
-        const int act = (info.flags != 0 || nt > 0);
-        int3 tot;
-        const int3 ex = block_scan3(make_int3(act, __popc(info.flags), nt), tot, sh);
+    int ia = off[row];
+    int iv = off[(nrows + 1) + row];
+    int it = off[2 * (nrows + 1) + row];
+    for (int x0 = 0; x0 < nx; x0 += 32) {
+        const SegBits sb = seg_bits(A, rowbase, x0, nx, st[1], st[2], hy, hz, L);
+        const int x = x0 + lane;
+        NodeInfo ni;
+        ni.flags = 0;
+        ni.cls = 0;
+        if (x < nx) ni = lane_node(sb, x, nx, hy, hz);
+        const int t = ntri_of(ni.cls);
+        const int act = (ni.flags != 0 || t > 0);
+        const unsigned ma = __ballot_sync(0xffffffffu, act);
+        if (ma == 0u) continue;                  // warp-uniform
+        const int nvl = __popc(ni.flags);
+        const unsigned v0 = __ballot_sync(0xffffffffu, nvl & 1), v1 = __ballot_sync(0xffffffffu, nvl & 2);
+        const unsigned t0 = __ballot_sync(0xffffffffu, t & 1), t1 = __ballot_sync(0xffffffffu, t & 2);
+        const unsigned t2 = __ballot_sync(0xffffffffu, t & 4);
         if (act) {
-            int vi = iv + ex.y;
-            nodes[ia + ex.x] = make_int4((int)n, info.flags | (info.cls << 8), vi, it + ex.z);
-            if (info.flags) {
+            const int64_t n = rowbase + x;
+            const int q[3] = {x, y, z};
+            int vi = iv + __popc(v0 & lt) + 2 * __popc(v1 & lt);
+            const int ti = it + __popc(t0 & lt) + 2 * __popc(t1 & lt) + 4 * __popc(t2 & lt);
+            nodes[ia + __popc(ma & lt)] = make_int4((int)n, ni.flags | (ni.cls << 8), vi, ti);
+            if (ni.flags) {
                 float g0[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
                 for (int a = 0; a < 3; ++a) {
-                    if (!((info.flags >> a) & 1)) continue;
+                    if (!((ni.flags >> a) & 1)) continue;
                     const int64_t n1 = n + st[a];
                     const double a0 = A[n], a1 = A[n1];
-                    const double t = (Ld - a0) / (a1 - a0);
+                    const double tt = (Ld - a0) / (a1 - a0);
                     int q1[3] = {q[0], q[1], q[2]};
                     q1[a] += 1;
                     float g1[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
                     float p[3], nv[3];
-                    const float tf = (float)t;
+                    const float tf = (float)tt;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
-                        if (c == a) pc += t * g.h[c];
+                        if (c == a) pc += tt * g.h[c];
                         p[c] = (float)pc;
                         nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
                     }
@@ -297,9 +343,9 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
                 }
             }
         }
-        ia += tot.x;
-        iv += tot.y;
-        it += tot.z;
+        ia += __popc(ma);
+        iv += __popc(v0) + 2 * __popc(v1);
+        it += __popc(t0) + 2 * __popc(t1) + 4 * __popc(t2);
     }
 }
 
@@ -376,31 +422,33 @@ cudaError_t mc_init() {
 }
 
 cudaError_t launch_mc_count(ftr_ctx* c) {
-    const int nb = c->mc_blocks;
+    const int nr = c->mc_blocks;              // grid rows n_y n_z
+    const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
     prof_begin(c, ST_MC_COUNT);
-    k_mc_count<<<nb, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, c->d_mc_mask, nb);
+    k_mc_count<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, nr);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
     if (e != cudaSuccess) return e;
     prof_begin(c, ST_MC_SCAN);
-    const int ntiles = (nb + kScanTile - 1) / kScanTile;
-    k_mc_tile_sums<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nb, c->d_mc_tile);
-    k_mc_tile_scan<<<1, kMcThreads, 0, c->stream>>>(c->d_mc_tile, ntiles, nb, c->d_mc_off);
-    k_mc_tile_write<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nb, c->d_mc_tile, c->d_mc_off);
+    const int ntiles = (nr + kScanTile - 1) / kScanTile;
+    k_mc_tile_sums<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nr, c->d_mc_tile);
+    k_mc_tile_scan<<<1, kMcThreads, 0, c->stream>>>(c->d_mc_tile, ntiles, nr, c->d_mc_off);
+    k_mc_tile_write<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nr, c->d_mc_tile, c->d_mc_off);
     c->launches += 3;
     e = cudaGetLastError();
     prof_end(c, ST_MC_SCAN);
     if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(c->h_mc_tot, c->d_mc_off + 3 * (nb + 1), 3 * sizeof(int), cudaMemcpyDeviceToHost,
+    return cudaMemcpyAsync(c->h_mc_tot, c->d_mc_off + 3 * (nr + 1), 3 * sizeof(int), cudaMemcpyDeviceToHost,
                            c->stream);
 }
 
 cudaError_t launch_mc_emit(ftr_ctx* c) {
+    const int nr = c->mc_blocks;
+    const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
     prof_begin(c, ST_MC_EMIT);
-    k_mc_emit<<<c->mc_blocks, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, c->d_mc_mask,
-                                                         c->d_mc_off, c->mc_blocks, c->d_mc_nodes, c->d_verts,
-                                                         c->d_vnrm);
+    k_mc_emit<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, c->d_mc_off, nr,
+                                                  c->d_mc_nodes, c->d_verts, c->d_vnrm);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);

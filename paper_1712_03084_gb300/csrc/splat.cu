@@ -26,6 +26,22 @@ namespace ftr {
 
 namespace {
 
+// t = (X - b_min) / h - 1/2 per axis.  The float64 product with 1/h is exact
+// enough for the stencil offsets; wherever it could round to the other side
+// of a decision (the acceptance bounds, floor(t), floor(t + 1/2)) the
+// quotient is recomputed with a true division, so every decision equals that
+// of (X - b_min) / h in float64.
+__device__ __forceinline__ double node_t(double x, double bmin, double h, double inv_h, double n) {
+    double t = (x - bmin) * inv_h - 0.5;
+    const double band = 1e-9 * (1.0 + fabs(t));
+    const double fr = t - floor(t);
+    const double fh = (t + 0.5) - floor(t + 0.5);
+    if (fr < band || fr > 1.0 - band || fh < band || fh > 1.0 - band || fabs(t - 1.0) < band ||
+        fabs(t - (n - 2.0)) < band)
+        t = (x - bmin) / h - 0.5;
+    return t;
+}
+
 __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
                          float4* pfrac, float4* pnrm, unsigned long long* dropped) {
@@ -37,7 +53,7 @@ __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict_
     int up = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        double t = ((double)pts[3 * i + c] - g.bmin[c]) / g.h[c] - 0.5;
+        const double t = node_t((double)pts[3 * i + c], g.bmin[c], g.h[c], g.inv_h[c], (double)g.n[c]);
         bool in = (t >= 1.0) && (t < (double)g.n[c] - 2.0);   // false for NaN
         ok = ok && in;
         if (in) {
@@ -288,10 +304,11 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
         for (int li = tid; li < kBrickVox; li += kAccThreads) {
             const long long d = (long long)acc[3][li];
             if (d > 0) {
-                const double sc = g.v_scale / (double)d;
-                out[li] = (float)((double)(long long)acc[0][li] * sc);
-                out[kBrickVox + li] = (float)((double)(long long)acc[1][li] * sc);
-                out[2 * kBrickVox + li] = (float)((double)(long long)acc[2][li] * sc);
+                // exact integer sums, one float32 quotient per voxel
+                const float sc = g.v_scale_f / (float)d;
+                out[li] = (float)(long long)acc[0][li] * sc;
+                out[kBrickVox + li] = (float)(long long)acc[1][li] * sc;
+                out[2 * kBrickVox + li] = (float)(long long)acc[2][li] * sc;
             } else {
                 out[li] = 0.f;
                 out[kBrickVox + li] = 0.f;
