@@ -65,50 +65,59 @@ __device__ __forceinline__ NodeInfo classify_node(const float* __restrict__ A, i
 
 constexpr int kRowsPerCta = kMcThreads / 32;
 
-// Bits of one 32-node segment of row (y, z) starting at x0.
-struct SegBits {
-    unsigned m00, m10, m01, m11;   // A >= L on rows (y,z), (y+1,z), (y,z+1), (y+1,z+1)
-    unsigned e;                    // bits 0..3: the same four rows at x0 + 32
+// One 128-node segment of row (y, z) starting at x0: lane l holds nodes
+// x0 + 4l .. x0 + 4l + 3.  bits[r] packs, for the rows r = (y,z), (y+1,z),
+// (y,z+1), (y+1,z+1), bit j = (A >= L) at node j of the lane and bit 4 = the
+// same at the lane's +x neighbour of node 3.
+struct Seg4 {
+    int bits[4];
 };
 
-__device__ __forceinline__ SegBits seg_bits(const float* __restrict__ A, int64_t rowbase, int x0, int nx,
-                                            int64_t sy, int64_t sz, bool hy, bool hz, float L) {
+__device__ __forceinline__ int nib(float4 v, float L) {
+    return (v.x >= L) | ((v.y >= L) << 1) | ((v.z >= L) << 2) | ((v.w >= L) << 3);
+}
+
+__device__ __forceinline__ Seg4 seg_load(const float* __restrict__ A, int64_t rowbase, int x0, int nx,
+                                         int64_t sy, int64_t sz, bool hy, bool hz, float L) {
     const int lane = threadIdx.x & 31;
-    const int x = x0 + lane;
+    const int x = x0 + 4 * lane;
     const bool valid = x < nx;
-    const int64_t n = rowbase + x;
-    SegBits s;
-    s.m00 = __ballot_sync(0xffffffffu, valid && A[n] >= L);
-    s.m10 = __ballot_sync(0xffffffffu, valid && hy && A[n + sy] >= L);
-    s.m01 = __ballot_sync(0xffffffffu, valid && hz && A[n + sz] >= L);
-    s.m11 = __ballot_sync(0xffffffffu, valid && hy && hz && A[n + sy + sz] >= L);
-    unsigned e = 0;
-    if (lane == 31 && x + 1 < nx) {
-        e = (A[n + 1] >= L) | ((hy && A[n + 1 + sy] >= L) << 1) | ((hz && A[n + 1 + sz] >= L) << 2) |
-            ((hy && hz && A[n + 1 + sy + sz] >= L) << 3);
+    const float4* p = reinterpret_cast<const float4*>(A + rowbase + x);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 r00 = valid ? p[0] : z4;
+    const float4 r10 = (valid && hy) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy) : z4;
+    const float4 r01 = (valid && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sz) : z4;
+    const float4 r11 = (valid && hy && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy + sz) : z4;
+    Seg4 s;
+    s.bits[0] = valid ? nib(r00, L) : 0;
+    s.bits[1] = (valid && hy) ? nib(r10, L) : 0;
+    s.bits[2] = (valid && hz) ? nib(r01, L) : 0;
+    s.bits[3] = (valid && hy && hz) ? nib(r11, L) : 0;
+    // +x neighbour of node 3: the next lane's node 0, or the next segment's
+    // first node for lane 31
+    int nb[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) nb[r] = __shfl_down_sync(0xffffffffu, s.bits[r], 1) & 1;
+    if (lane == 31) {
+        const int64_t n = rowbase + x + 4;
+        const bool more = x + 4 < nx;
+        nb[0] = more && A[n] >= L;
+        nb[1] = more && hy && A[n + sy] >= L;
+        nb[2] = more && hz && A[n + sz] >= L;
+        nb[3] = more && hy && hz && A[n + sy + sz] >= L;
     }
-    s.e = __shfl_sync(0xffffffffu, e, 31);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s.bits[r] |= nb[r] << 4;
     return s;
 }
 
-// Edge bits and cube class of this lane's node from the segment masks.
-__device__ __forceinline__ NodeInfo lane_node(const SegBits& s, int x, int nx, bool hy, bool hz) {
-    const int lane = threadIdx.x & 31;
+// Edge bits and cube class of node j (0..3) of this lane.
+__device__ __forceinline__ NodeInfo seg_node(const Seg4& s, int j, int x, int nx, bool hy, bool hz) {
     const bool hx = x < nx - 1;
-    const int b0 = (s.m00 >> lane) & 1, by = (s.m10 >> lane) & 1;
-    const int bz = (s.m01 >> lane) & 1, byz = (s.m11 >> lane) & 1;
-    int bx, bxy, bxz, bxyz;
-    if (lane < 31) {
-        bx = (s.m00 >> (lane + 1)) & 1;
-        bxy = (s.m10 >> (lane + 1)) & 1;
-        bxz = (s.m01 >> (lane + 1)) & 1;
-        bxyz = (s.m11 >> (lane + 1)) & 1;
-    } else {
-        bx = s.e & 1;
-        bxy = (s.e >> 1) & 1;
-        bxz = (s.e >> 2) & 1;
-        bxyz = (s.e >> 3) & 1;
-    }
+    const int b0 = (s.bits[0] >> j) & 1, bx = (s.bits[0] >> (j + 1)) & 1;
+    const int by = (s.bits[1] >> j) & 1, bxy = (s.bits[1] >> (j + 1)) & 1;
+    const int bz = (s.bits[2] >> j) & 1, bxz = (s.bits[2] >> (j + 1)) & 1;
+    const int byz = (s.bits[3] >> j) & 1, bxyz = (s.bits[3] >> (j + 1)) & 1;
     NodeInfo r;
     r.flags = (hx && bx != b0) | ((hy && by != b0) << 1) | ((hz && bz != b0) << 2);
     r.cls = (hx && hy && hz)
@@ -132,15 +141,21 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float*
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     const int64_t rowbase = (int64_t)row * nx;
     int na = 0, nv = 0, nt = 0;
-    for (int x0 = 0; x0 < nx; x0 += 32) {
-        const SegBits sb = seg_bits(A, rowbase, x0, nx, sy, sz, hy, hz, L);
-        const int x = x0 + lane;
-        if (x < nx) {
-            const NodeInfo ni = lane_node(sb, x, nx, hy, hz);
-            const int t = ntri_of(ni.cls);
-            na += (ni.flags != 0 || t > 0);
-            nv += __popc(ni.flags);
-            nt += t;
+    for (int x0 = 0; x0 < nx; x0 += 128) {
+        const Seg4 sb = seg_load(A, rowbase, x0, nx, sy, sz, hy, hz, L);
+        const int xl = x0 + 4 * lane;
+        // all four rows agree on all five bits: no edge or cell changes here
+        const int all = sb.bits[0] & sb.bits[1] & sb.bits[2] & sb.bits[3];
+        const int any = sb.bits[0] | sb.bits[1] | sb.bits[2] | sb.bits[3];
+        if (xl < nx && !(all == 0x1f || any == 0)) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const NodeInfo ni = seg_node(sb, j, xl + j, nx, hy, hz);
+                const int t = ntri_of(ni.cls);
+                na += (ni.flags != 0 || t > 0);
+                nv += __popc(ni.flags);
+                nt += t;
+            }
         }
     }
 #pragma unroll
@@ -266,6 +281,46 @@ __device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t 
     return (A[n + stride] - A[n - stride]) * (0.5f * inv_h);
 }
 
+__device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __restrict__ A, double Ld,
+                                              int64_t n, const int q[3], int flags, int vi,
+                                              float* __restrict__ verts, float* __restrict__ vnrm) {
+    const int nn[3] = {g.n[0], g.n[1], g.n[2]};
+    const int64_t st[3] = {1, (int64_t)g.n[0], (int64_t)g.n[0] * g.n[1]};
+    const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
+    float g0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
+    for (int a = 0; a < 3; ++a) {
+        if (!((flags >> a) & 1)) continue;
+        const int64_t n1 = n + st[a];
+        const double a0 = A[n], a1 = A[n1];
+        const double tt = (Ld - a0) / (a1 - a0);
+        int q1[3] = {q[0], q[1], q[2]};
+        q1[a] += 1;
+        float g1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
+        float p[3], nv[3];
+        const float tf = (float)tt;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
+            if (c == a) pc += tt * g.h[c];
+            p[c] = (float)pc;
+            nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
+        }
+        const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+        const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
+        verts[3 * (int64_t)vi + 0] = p[0];
+        verts[3 * (int64_t)vi + 1] = p[1];
+        verts[3 * (int64_t)vi + 2] = p[2];
+        vnrm[3 * (int64_t)vi + 0] = nv[0] * inv;
+        vnrm[3 * (int64_t)vi + 1] = nv[1] * inv;
+        vnrm[3 * (int64_t)vi + 2] = nv[2] * inv;
+        ++vi;
+    }
+}
+
 __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
                                                         const double* __restrict__ level,
                                                         const int* __restrict__ cnt, const int* __restrict__ off,
@@ -274,78 +329,66 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows || cnt[row] == 0) return;   // warp-uniform: no surface on this row
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const double Ld = level[0];
     const float L = __double2float_ru(Ld);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int y = row % ny, z = row / ny;
     const bool hy = y < ny - 1, hz = z < nz - 1;
-    const int64_t st[3] = {1, (int64_t)nx, (int64_t)nx * ny};
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
     const int64_t rowbase = (int64_t)row * nx;
-    const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
-    const int nn[3] = {nx, ny, nz};
     int ia = off[row];
     int iv = off[(nrows + 1) + row];
     int it = off[2 * (nrows + 1) + row];
-    for (int x0 = 0; x0 < nx; x0 += 32) {
-        const SegBits sb = seg_bits(A, rowbase, x0, nx, st[1], st[2], hy, hz, L);
-        const int x = x0 + lane;
-        NodeInfo ni;
-        ni.flags = 0;
-        ni.cls = 0;
-        if (x < nx) ni = lane_node(sb, x, nx, hy, hz);
-        const int t = ntri_of(ni.cls);
-        const int act = (ni.flags != 0 || t > 0);
-        const unsigned ma = __ballot_sync(0xffffffffu, act);
-        if (ma == 0u) continue;                  // warp-uniform
-        const int nvl = __popc(ni.flags);
-        const unsigned v0 = __ballot_sync(0xffffffffu, nvl & 1), v1 = __ballot_sync(0xffffffffu, nvl & 2);
-        const unsigned t0 = __ballot_sync(0xffffffffu, t & 1), t1 = __ballot_sync(0xffffffffu, t & 2);
-        const unsigned t2 = __ballot_sync(0xffffffffu, t & 4);
-        if (act) {
-            const int64_t n = rowbase + x;
-            const int q[3] = {x, y, z};
-            int vi = iv + __popc(v0 & lt) + 2 * __popc(v1 & lt);
-            const int ti = it + __popc(t0 & lt) + 2 * __popc(t1 & lt) + 4 * __popc(t2 & lt);
-            nodes[ia + __popc(ma & lt)] = make_int4((int)n, ni.flags | (ni.cls << 8), vi, ti);
-            if (ni.flags) {
-                float g0[3];
+    for (int x0 = 0; x0 < nx; x0 += 128) {
+        const Seg4 sb = seg_load(A, rowbase, x0, nx, sy, sz, hy, hz, L);
+        const int xl = x0 + 4 * lane;
+        NodeInfo ni[4];
+        int ca = 0, cv = 0, ct = 0;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
-                for (int a = 0; a < 3; ++a) {
-                    if (!((ni.flags >> a) & 1)) continue;
-                    const int64_t n1 = n + st[a];
-                    const double a0 = A[n], a1 = A[n1];
-                    const double tt = (Ld - a0) / (a1 - a0);
-                    int q1[3] = {q[0], q[1], q[2]};
-                    q1[a] += 1;
-                    float g1[3];
+        for (int j = 0; j < 4; ++j) {
+            ni[j].flags = 0;
+            ni[j].cls = 0;
+            if (xl < nx) ni[j] = seg_node(sb, j, xl + j, nx, hy, hz);
+            const int t = ntri_of(ni[j].cls);
+            ca += (ni[j].flags != 0 || t > 0);
+            cv += __popc(ni[j].flags);
+            ct += t;
+        }
+        // exclusive prefix over lanes (x order), then in-lane order j
+        int pa = ca, pv = cv, pt = ct;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
-                    float p[3], nv[3];
-                    const float tf = (float)tt;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
-                        if (c == a) pc += tt * g.h[c];
-                        p[c] = (float)pc;
-                        nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
-                    }
-                    const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
-                    const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
-                    verts[3 * (int64_t)vi + 0] = p[0];
-                    verts[3 * (int64_t)vi + 1] = p[1];
-                    verts[3 * (int64_t)vi + 2] = p[2];
-                    vnrm[3 * (int64_t)vi + 0] = nv[0] * inv;
-                    vnrm[3 * (int64_t)vi + 1] = nv[1] * inv;
-                    vnrm[3 * (int64_t)vi + 2] = nv[2] * inv;
-                    ++vi;
-                }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, pa, o);
+            const int b = __shfl_up_sync(0xffffffffu, pv, o);
+            const int c = __shfl_up_sync(0xffffffffu, pt, o);
+            if (lane >= o) {
+                pa += a;
+                pv += b;
+                pt += c;
             }
         }
-        ia += __popc(ma);
-        iv += __popc(v0) + 2 * __popc(v1);
-        it += __popc(t0) + 2 * __popc(t1) + 4 * __popc(t2);
+        const int ta = __shfl_sync(0xffffffffu, pa, 31);
+        const int tv = __shfl_sync(0xffffffffu, pv, 31);
+        const int tt = __shfl_sync(0xffffffffu, pt, 31);
+        int ja = ia + pa - ca, jv = iv + pv - cv, jt = it + pt - ct;
+        if (ca > 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = ntri_of(ni[j].cls);
+                if (ni[j].flags == 0 && t == 0) continue;
+                const int64_t n = rowbase + xl + j;
+                nodes[ja++] = make_int4((int)n, ni[j].flags | (ni[j].cls << 8), jv, jt);
+                if (ni[j].flags) {
+                    const int q[3] = {xl + j, y, z};
+                    emit_vertices(g, A, Ld, n, q, ni[j].flags, jv, verts, vnrm);
+                }
+                jv += __popc(ni[j].flags);
+                jt += t;
+            }
+        }
+        ia += ta;
+        iv += tv;
+        it += tt;
     }
 }
 
