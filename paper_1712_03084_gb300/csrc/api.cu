@@ -176,6 +176,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_A);
     for (int a = 0; a < 3; ++a) dfree(c->d_tw[a]);
     dfree(c->d_level);
+    dfree(c->d_levelf);
     dfree(c->d_level_part);
     dfree(c->d_mc_blk);
     dfree(c->d_mc_tile);
@@ -237,6 +238,8 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         g.h[a] = ((double)bbox[3 + a] - (double)bbox[a]) / grid_n[a];
         g.inv_h[a] = 1.0 / g.h[a];
         g.hf[a] = (float)g.h[a];
+        g.inv_hf[a] = (float)g.inv_h[a];
+        g.bminf[a] = bbox[a];
         diag2 += g.h[a] * g.h[a];
     }
     const double s1 = (double)prm.sigma1_scale * 0.5 * sqrt(diag2);
@@ -280,6 +283,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     for (int a = 0; a < 3; ++a) ALLOC(c->d_tw[a], grid_n[a]);
     c->level_blocks = 304;
     ALLOC(c->d_level, 2);
+    ALLOC(c->d_levelf, 2);
     ALLOC(c->d_level_part, 2 * c->level_blocks);
     c->mc_blocks = grid_n[1] * grid_n[2];      // marching cubes counts per grid row
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
@@ -310,7 +314,9 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     }
     cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
     double zero2[2] = {0.0, 0.0};
+    float zerof[2] = {0.f, 0.f};
     cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_levelf, zerof, sizeof(zerof), cudaMemcpyHostToDevice, c->stream);
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
         free_all(c);
         delete c;
@@ -654,7 +660,12 @@ int ftr_set_indicator(ftr_ctx* c, const float* A, double level) {
     if (!c || !A) return FTR_EINVAL;
     cudaError_t e = cudaMemcpyAsync(c->d_A, A, sizeof(float) * c->M, cudaMemcpyDefault, c->stream);
     double lv[2] = {level, 1.0};
+    // float thresholds: rounded up (same decision as the float64 compare) and to nearest
+    float up = (float)level;
+    if ((double)up < level) up = nextafterf(up, INFINITY);
+    float lvf[2] = {up, (float)level};
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_level, lv, sizeof(lv), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_levelf, lvf, sizeof(lvf), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_set_indicator");
     c->solved = true;

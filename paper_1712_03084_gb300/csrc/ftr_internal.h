@@ -43,6 +43,8 @@ struct GridDev {
     double h[3];
     double inv_h[3];
     float hf[3];
+    float inv_hf[3];
+    float bminf[3];
     float inv_s1sq, inv_s2sq;  // 1/sigma1^2, 1/sigma2^2 (world units)
     double v_scale;            // sigma2/sigma1 (weighted) or 1 (simple)
     float v_scale_f;           // the same in float32
@@ -102,6 +104,7 @@ struct ftr_ctx {
 
     // level
     double* d_level = nullptr;     // [0] L, [1] accepted count
+    float* d_levelf = nullptr;     // [0] L rounded up to float32, [1] L rounded to nearest
     double* d_level_part = nullptr;
     int level_blocks = 0;
     bool solved = false;

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
 
 // One warp: lane l sums partials l, l + 32, ... in order, then a fixed
 // shuffle tree combines the lanes.
-__global__ void k_level_final(const double* __restrict__ part, int nblocks, double* level) {
+__global__ void k_level_final(const double* __restrict__ part, int nblocks, double* level, float* levelf) {
     const int lane = threadIdx.x;
     double s = 0.0, c = 0.0;
     for (int b = lane; b < nblocks; b += 32) {
@@ -74,8 +74,11 @@ __global__ void k_level_final(const double* __restrict__ part, int nblocks, doub
         c += __shfl_down_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-        level[0] = c > 0.0 ? s / c : 0.0;
+        const double L = c > 0.0 ? s / c : 0.0;
+        level[0] = L;
         level[1] = c;
+        levelf[0] = __double2float_ru(L);   // A >= L (float64) <=> A >= levelf[0] for float32 A
+        levelf[1] = __double2float_rn(L);
     }
 }
 
@@ -87,7 +90,7 @@ cudaError_t launch_level(ftr_ctx* c) {
     c->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_level_final<<<1, 32, 0, c->stream>>>(c->d_level_part, c->level_blocks, c->d_level);
+    k_level_final<<<1, 32, 0, c->stream>>>(c->d_level_part, c->level_blocks, c->d_level, c->d_levelf);
     c->launches++;
     return cudaGetLastError();
 }

@@ -129,9 +129,9 @@ __device__ __forceinline__ NodeInfo seg_node(const Seg4& s, int j, int x, int nx
 __device__ __forceinline__ int ntri_of(int cls) { return (cls == 0 || cls == 255) ? 0 : c_ntri[cls]; }
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
-                                                         const double* __restrict__ level, int* __restrict__ cnt,
+                                                         const float* __restrict__ levelf, int* __restrict__ cnt,
                                                          int nrows) {
-    const float L = __double2float_ru(level[0]);
+    const float L = levelf[0];
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows) return;                    // warp-uniform
     const int lane = threadIdx.x & 31;
@@ -281,33 +281,33 @@ __device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t 
     return (A[n + stride] - A[n - stride]) * (0.5f * inv_h);
 }
 
-__device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __restrict__ A, double Ld,
+// Vertices on the crossing edges of node n: t = (L - A0) / (A1 - A0) and the
+// position p(q) + t h_a e_a, in float32 (no decision depends on them; the
+// error is a few float32 ulps of the coordinates), normal = -grad A lerped.
+__device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __restrict__ A, float Ln,
                                               int64_t n, const int q[3], int flags, int vi,
                                               float* __restrict__ verts, float* __restrict__ vnrm) {
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
     const int64_t st[3] = {1, (int64_t)g.n[0], (int64_t)g.n[0] * g.n[1]};
-    const float inv_h[3] = {(float)g.inv_h[0], (float)g.inv_h[1], (float)g.inv_h[2]};
     float g0[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], inv_h[c]);
+    for (int c = 0; c < 3; ++c) g0[c] = grad_axis(A, n, q[c], nn[c], st[c], g.inv_hf[c]);
     for (int a = 0; a < 3; ++a) {
         if (!((flags >> a) & 1)) continue;
         const int64_t n1 = n + st[a];
-        const double a0 = A[n], a1 = A[n1];
-        const double tt = (Ld - a0) / (a1 - a0);
+        const float a0 = A[n], a1 = A[n1];
+        const float tt = (Ln - a0) / (a1 - a0);
         int q1[3] = {q[0], q[1], q[2]};
         q1[a] += 1;
         float g1[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], inv_h[c]);
+        for (int c = 0; c < 3; ++c) g1[c] = grad_axis(A, n1, q1[c], nn[c], st[c], g.inv_hf[c]);
         float p[3], nv[3];
-        const float tf = (float)tt;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double pc = g.bmin[c] + ((double)q[c] + 0.5) * g.h[c];
-            if (c == a) pc += tt * g.h[c];
-            p[c] = (float)pc;
-            nv[c] = -((1.0f - tf) * g0[c] + tf * g1[c]);
+            const float qc = (float)q[c] + 0.5f + (c == a ? tt : 0.0f);
+            p[c] = fmaf(qc, g.hf[c], g.bminf[c]);
+            nv[c] = -((1.0f - tt) * g0[c] + tt * g1[c]);
         }
         const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
         const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
@@ -322,15 +322,15 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
 }
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
-                                                        const double* __restrict__ level,
+                                                        const float* __restrict__ levelf,
                                                         const int* __restrict__ cnt, const int* __restrict__ off,
                                                         int nrows, int4* __restrict__ nodes,
                                                         float* __restrict__ verts, float* __restrict__ vnrm) {
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows || cnt[row] == 0) return;   // warp-uniform: no surface on this row
     const int lane = threadIdx.x & 31;
-    const double Ld = level[0];
-    const float L = __double2float_ru(Ld);
+    const float L = levelf[0];
+    const float Ln = levelf[1];
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const int y = row % ny, z = row / ny;
     const bool hy = y < ny - 1, hz = z < nz - 1;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
                 nodes[ja++] = make_int4((int)n, ni[j].flags | (ni[j].cls << 8), jv, jt);
                 if (ni[j].flags) {
                     const int q[3] = {xl + j, y, z};
-                    emit_vertices(g, A, Ld, n, q, ni[j].flags, jv, verts, vnrm);
+                    emit_vertices(g, A, Ln, n, q, ni[j].flags, jv, verts, vnrm);
                 }
                 jv += __popc(ni[j].flags);
                 jt += t;
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restri
     }
 }
 
-__global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const double* __restrict__ level,
+__global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const float* __restrict__ levelf,
                              uint8_t* out) {
     const int cx = g.n[0] - 1, cy = g.n[1] - 1, cz = g.n[2] - 1;
     const int64_t ncell = (int64_t)cx * cy * cz;
@@ -446,7 +446,7 @@ __global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const doubl
     const int y = rem / cx;
     const int x = rem - y * cx;
     const int64_t n = x + (int64_t)g.n[0] * (y + (int64_t)g.n[1] * z);
-    out[i] = (uint8_t)classify_node(A, n, x, y, z, g, __double2float_ru(level[0])).cls;
+    out[i] = (uint8_t)classify_node(A, n, x, y, z, g, levelf[0]).cls;
 }
 
 }  // namespace
@@ -468,7 +468,7 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
     const int nr = c->mc_blocks;              // grid rows n_y n_z
     const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
     prof_begin(c, ST_MC_COUNT);
-    k_mc_count<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, nr);
+    k_mc_count<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
@@ -490,7 +490,7 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int nr = c->mc_blocks;
     const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
     prof_begin(c, ST_MC_EMIT);
-    k_mc_emit<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_level, c->d_mc_blk, c->d_mc_off, nr,
+    k_mc_emit<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, c->d_mc_off, nr,
                                                   c->d_mc_nodes, c->d_verts, c->d_vnrm);
     c->launches++;
     cudaError_t e = cudaGetLastError();
@@ -509,7 +509,7 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
 
 cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev) {
     const int64_t ncell = (int64_t)(c->g.n[0] - 1) * (c->g.n[1] - 1) * (c->g.n[2] - 1);
-    k_mc_classes<<<(unsigned)((ncell + 255) / 256), 256, 0, c->stream>>>(c->g, c->d_A, c->d_level, out_dev);
+    k_mc_classes<<<(unsigned)((ncell + 255) / 256), 256, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, out_dev);
     c->launches++;
     return cudaGetLastError();
 }

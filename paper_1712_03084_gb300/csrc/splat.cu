@@ -227,7 +227,24 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restri
 }
 
 constexpr int kAccThreads = 256;
-constexpr float kFix = 1099511627776.0f;    // 2^40
+
+// round(v * 2^40) as int64 without a 64-bit conversion (those run on the slow
+// double-precision pipe): v 2^40 = hi 2^32 + r 2^32 with hi = floor(v 2^8) and
+// r in [0, 1) exact, and r 2^32 rounded to the nearest integer (ties to even,
+// like the direct conversion, since hi 2^32 is even).
+__device__ __forceinline__ long long fix40(float v) {
+    const float x = v * 256.0f;
+    const float hf = floorf(x);
+    const unsigned lo = __float2uint_rn((x - hf) * 4294967296.0f);
+    return (long long)(((unsigned long long)(long long)(int)hf << 32) + lo);
+}
+
+// int64 -> float32 through its two 32-bit halves (same reason as above)
+__device__ __forceinline__ float fix_to_float(long long v) {
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
 
 constexpr int kStage = 128;   // point records staged in shared memory per batch
 
@@ -281,10 +298,10 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                     const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
                     const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
                     const int li = lx + kBrick * (ly + kBrick * lz);
-                    atomicAdd(&acc[0][li], (unsigned long long)__float2ll_rn(e1v * nr.x * kFix));
-                    atomicAdd(&acc[1][li], (unsigned long long)__float2ll_rn(e1v * nr.y * kFix));
-                    atomicAdd(&acc[2][li], (unsigned long long)__float2ll_rn(e1v * nr.z * kFix));
-                    atomicAdd(&acc[3][li], (unsigned long long)__float2ll_rn(e2v * kFix));
+                    atomicAdd(&acc[0][li], (unsigned long long)fix40(e1v * nr.x));
+                    atomicAdd(&acc[1][li], (unsigned long long)fix40(e1v * nr.y));
+                    atomicAdd(&acc[2][li], (unsigned long long)fix40(e1v * nr.z));
+                    atomicAdd(&acc[3][li], (unsigned long long)fix40(e2v));
                 }
             } else if (tid < nbatch) {
                 const int4 pb = s_base[tid];
@@ -293,9 +310,9 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                 const int lz = pb.z + ((pb.w >> 3) & 1) - orgz;
                 const float4 nr = s_nrm[tid];
                 const int li = lx + kBrick * (ly + kBrick * lz);
-                atomicAdd(&acc[0][li], (unsigned long long)__float2ll_rn(nr.x * kFix));
-                atomicAdd(&acc[1][li], (unsigned long long)__float2ll_rn(nr.y * kFix));
-                atomicAdd(&acc[2][li], (unsigned long long)__float2ll_rn(nr.z * kFix));
+                atomicAdd(&acc[0][li], (unsigned long long)fix40(nr.x));
+                atomicAdd(&acc[1][li], (unsigned long long)fix40(nr.y));
+                atomicAdd(&acc[2][li], (unsigned long long)fix40(nr.z));
                 atomicAdd(&acc[3][li], (unsigned long long)(1ll << 40));
             }
         }
@@ -305,10 +322,10 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
             const long long d = (long long)acc[3][li];
             if (d > 0) {
                 // exact integer sums, one float32 quotient per voxel
-                const float sc = g.v_scale_f / (float)d;
-                out[li] = (float)(long long)acc[0][li] * sc;
-                out[kBrickVox + li] = (float)(long long)acc[1][li] * sc;
-                out[2 * kBrickVox + li] = (float)(long long)acc[2][li] * sc;
+                const float sc = g.v_scale_f / fix_to_float(d);
+                out[li] = fix_to_float((long long)acc[0][li]) * sc;
+                out[kBrickVox + li] = fix_to_float((long long)acc[1][li]) * sc;
+                out[2 * kBrickVox + li] = fix_to_float((long long)acc[2][li]) * sc;
             } else {
                 out[li] = 0.f;
                 out[kBrickVox + li] = 0.f;
@@ -356,7 +373,8 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n) {
     if (n == 0) return cudaSuccess;
-    k_ingest<<<blocks_for(n, 256), 256, 0, c->stream>>>(pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
+    // small CTAs spread the few float64 operations per point over every SM
+    k_ingest<<<blocks_for(n, 32), 32, 0, c->stream>>>(pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
                                                        c->pts.nrm, c->d_dropped);
     c->launches++;
     return cudaGetLastError();
