@@ -229,21 +229,24 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restri
 constexpr int kAccThreads = 256;
 
 // round(v * 2^40) as int64 without a 64-bit conversion (those run on the slow
-// double-precision pipe): v 2^40 = hi 2^32 + r 2^32 with hi = floor(v 2^8) and
-// r in [0, 1) exact, and r 2^32 rounded to the nearest integer (ties to even,
-// like the direct conversion, since hi 2^32 is even).
+// double-precision pipe): with x = v 2^9, hi = trunc(x) and r = x - hi (exact:
+// Sterbenz, or r = x when |x| < 1), v 2^40 = hi 2^31 + r 2^31 where r 2^31 is
+// an exact float in (-2^31, 2^31) rounded to the nearest integer (ties to
+// even, like the direct conversion, since hi 2^31 is even).
 __device__ __forceinline__ long long fix40(float v) {
-    const float x = v * 256.0f;
-    const float hf = floorf(x);
-    const unsigned lo = __float2uint_rn((x - hf) * 4294967296.0f);
-    return (long long)(((unsigned long long)(long long)(int)hf << 32) + lo);
+    const float x = v * 512.0f;
+    const float hf = truncf(x);
+    const int lo = __float2int_rn((x - hf) * 2147483648.0f);
+    return (long long)(int)hf * 2147483648ll + (long long)lo;
 }
 
-// int64 -> float32 through its two 32-bit halves (same reason as above)
+// int64 -> float32 of its magnitude's two 32-bit halves, sign restored after
+// (no cancellation for small negative values; no 64-bit conversion)
 __device__ __forceinline__ float fix_to_float(long long v) {
-    const int hi = (int)(v >> 32);
-    const unsigned lo = (unsigned)(v & 0xffffffffll);
-    return fmaf((float)hi, 4294967296.0f, (float)lo);
+    const bool neg = v < 0;
+    const unsigned long long m = neg ? (unsigned long long)(-v) : (unsigned long long)v;
+    const float f = fmaf((float)(unsigned)(m >> 32), 4294967296.0f, (float)(unsigned)(m & 0xffffffffull));
+    return neg ? -f : f;
 }
 
 constexpr int kStage = 128;   // point records staged in shared memory per batch
