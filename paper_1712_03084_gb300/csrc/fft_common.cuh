@@ -160,6 +160,14 @@ template <> struct Plan<384> { static constexpr int N1 = 24, N2 = 16; };
 template <> struct Plan<512> { static constexpr int N1 = 32, N2 = 16; };
 
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Minimum resident CTAs per SM requested from the register allocator for the
+// 16-line passes: three (24 warps) while the transform still fits in 80
+// registers without spilling (n <= 256), one above.
+template <int N>
+struct MinCtas {
+    static constexpr int value = N <= 256 ? 3 : 1;
+};
 __host__ __device__ constexpr int make_odd(int v) { return (v & 1) ? v : v + 1; }
 
 // Shared-memory exchange layout for F lines of length N: element (f, j, k1)

@@ -28,7 +28,7 @@ __device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r
 }
 
 template <int N>
-__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
+__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT, MinCtas<N>::value)
     k_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
          const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta) {
     using X = Xchg<N, kLines>;

@@ -32,7 +32,7 @@ __device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r
 }
 
 template <int N>
-__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
+__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT, MinCtas<N>::value)
     k_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
          float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta) {
     using X = Xchg<N, kLines>;
@@ -48,8 +48,14 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     // forward z transforms of W (field 0) and of the x/y-transformed V_z (field 1)
     if (r < X::N2) load_step1<N>(s1 + line, r, f, zl, zh, smem, tw);
     __syncthreads();
+    // the transformed W waits in shared memory (the same thread reads it back)
+    float2* stash = smem + X::SIZE;
     float2 xw[X::N2];
-    if (r < X::N1) fft_step2<N, kLines, -1>(xw, f, r, smem);
+    if (r < X::N1) {
+        fft_step2<N, kLines, -1>(xw, f, r, smem);
+#pragma unroll
+        for (int k2 = 0; k2 < X::N2; ++k2) stash[f + (kLines + 1) * (r + X::N1 * k2)] = xw[k2];
+    }
     __syncthreads();
     if (r < X::N2) load_step1<N>(s1 + Mh + line, r, f, zl, zh, smem, tw);
     __syncthreads();
@@ -69,7 +75,8 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
             const float den = base + wzd * wzd;
             const float s = den > 0.f ? inv_m / den : 0.f;
             // S = W^ + j w_z V^_z
-            const float2 sv = make_float2(xw[k2].x - wzn * xh[k2].y, xw[k2].y + wzn * xh[k2].x);
+            const float2 w = stash[f + (kLines + 1) * kz];
+            const float2 sv = make_float2(w.x - wzn * xh[k2].y, w.y + wzn * xh[k2].x);
             xw[k2] = make_float2(sv.x * s, sv.y * s);
         }
         (void)nx;
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
 template <int N>
 cudaError_t run_fz(ftr_ctx* c) {
     using X = Xchg<N, kLines>;
-    const size_t smem = sizeof(float2) * X::SIZE;
+    const size_t smem = sizeof(float2) * (X::SIZE + (kLines + 1) * N);
     static bool attr_done[64] = {};
     if (!attr_done[c->device & 63]) {
         cudaError_t e = cudaFuncSetAttribute(k_fz<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -10,11 +10,11 @@
 //   count   per point, +1 on every brick its stencil overlaps
 //   scan    one CTA: brick offsets, dense slot per touched brick
 //   fill    per point, append its index to each overlapped brick's list
-//   accum   one CTA per touched brick: 64 lanes per point evaluate the stencil
-//           nodes inside the brick and add the contributions to shared-memory
-//           int64 fixed-point accumulators (value * 2^40, exact and
-//           order-independent, so the result is bit-reproducible); then
-//           V = (sigma2 / sigma1) U / d is written to the brick's slot.
+//   accum   one CTA per touched brick: every thread gathers, for its two
+//           voxels, the contributions of the brick's points into int64
+//           fixed-point registers (value * 2^40, exact and order-independent,
+//           so the result is bit-reproducible); then V = (sigma2 / sigma1) U / d
+//           is written to the brick's slot.
 // The simple variant (nearest node floor(t + 1/2), V = mean N) uses the same
 // bricks with one node per point and d counting points.
 #include <cuda_runtime.h>
@@ -249,8 +249,13 @@ __device__ __forceinline__ float fix_to_float(long long v) {
     return neg ? -f : f;
 }
 
-constexpr int kStage = 128;   // point records staged in shared memory per batch
+constexpr int kStage = 256;   // point records staged in shared memory per batch
 
+// One CTA per touched brick (persistent over the list).  Each thread owns two
+// voxels of the brick, (lx, ly, lz) and (lx, ly, lz + 4), and gathers from
+// the staged points the contributions whose 4^3 stencil contains them, into
+// int64 fixed-point registers: no atomics, and the exact integer sums do not
+// depend on the (scheduling-dependent) order of the brick's point list.
 __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const int* __restrict__ active,
                                                              const int* __restrict__ meta,
                                                              const int* __restrict__ off,
@@ -259,83 +264,90 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const float4* __restrict__ pfrac,
                                                              const float4* __restrict__ pnrm,
                                                              float* __restrict__ vpool) {
-    __shared__ unsigned long long acc[4][kBrickVox];
-    __shared__ int4 s_base[kStage];
+    __shared__ int4 s_rel[kStage];     // stencil base relative to the brick origin, flags
     __shared__ float4 s_frac[kStage];
     __shared__ float4 s_nrm[kStage];
     const int nact = meta[0];
     const int tid = threadIdx.x;
-    const int o = tid & 63;
-    const int ox = o & 3, oy = (o >> 2) & 3, oz = o >> 4;
-    const int pl = tid >> 6;
+    const int lx = tid & 7, ly = (tid >> 3) & 7, lz = tid >> 6;   // second voxel at lz + 4
     for (int s = blockIdx.x; s < nact; s += gridDim.x) {
         const int b = active[s];
         const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
         const int orgx = bx * kBrick, orgy = by * kBrick, orgz = bz * kBrick;
-        for (int k = tid; k < 4 * kBrickVox; k += kAccThreads) (&acc[0][0])[k] = 0ull;
+        long long u0[4] = {0, 0, 0, 0}, u1[4] = {0, 0, 0, 0};
         const int e0 = off[b], e1 = off[b + 1];
         for (int eb = e0; eb < e1; eb += kStage) {
             const int nbatch = min(kStage, e1 - eb);
             __syncthreads();
             if (tid < nbatch) {
                 const int i = entries[eb + tid];
-                s_base[tid] = pbase[i];
+                const int4 pb = pbase[i];
+                s_rel[tid] = make_int4(pb.x - orgx, pb.y - orgy, pb.z - orgz, pb.w);
                 s_frac[tid] = pfrac[i];
                 s_nrm[tid] = pnrm[i];
             }
             __syncthreads();
             if (g.mode == FTR_SPLAT_WEIGHTED) {
-                for (int p = pl; p < nbatch; p += kAccThreads / 64) {
-                    const int4 pb = s_base[p];
-                    const int lx = pb.x - 1 + ox - orgx;
-                    const int ly = pb.y - 1 + oy - orgy;
-                    const int lz = pb.z - 1 + oz - orgz;
-                    if ((unsigned)lx >= kBrick || (unsigned)ly >= kBrick || (unsigned)lz >= kBrick) continue;
+                for (int p = 0; p < nbatch; ++p) {
+                    const int4 rb = s_rel[p];
+                    // stencil offset of this voxel: node = base - 1 + o, o in 0..3
+                    const unsigned ox = (unsigned)(lx - rb.x + 1), oy = (unsigned)(ly - rb.y + 1);
+                    if (ox > 3u || oy > 3u) continue;
+                    const int oz0 = lz - rb.z + 1;
+                    const bool in0 = (unsigned)oz0 <= 3u, in1 = (unsigned)(oz0 + 4) <= 3u;
+                    if (!in0 && !in1) continue;
                     const float4 fr = s_frac[p];
                     const float4 nr = s_nrm[p];
                     // X - p(q) = (t - q) h with t - q = frac + 1 - offset
                     const float dx = (fr.x + 1.0f - (float)ox) * g.hf[0];
                     const float dy = (fr.y + 1.0f - (float)oy) * g.hf[1];
-                    const float dz = (fr.z + 1.0f - (float)oz) * g.hf[2];
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
-                    const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
-                    const int li = lx + kBrick * (ly + kBrick * lz);
-                    atomicAdd(&acc[0][li], (unsigned long long)fix40(e1v * nr.x));
-                    atomicAdd(&acc[1][li], (unsigned long long)fix40(e1v * nr.y));
-                    atomicAdd(&acc[2][li], (unsigned long long)fix40(e1v * nr.z));
-                    atomicAdd(&acc[3][li], (unsigned long long)fix40(e2v));
+                    const float dxy = dx * dx + dy * dy;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        if (!(k ? in1 : in0)) continue;
+                        const float dz = (fr.z + 1.0f - (float)(oz0 + 4 * k)) * g.hf[2];
+                        const float r2 = dxy + dz * dz;
+                        const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
+                        const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
+                        long long* u = k ? u1 : u0;
+                        u[0] += fix40(e1v * nr.x);
+                        u[1] += fix40(e1v * nr.y);
+                        u[2] += fix40(e1v * nr.z);
+                        u[3] += fix40(e2v);
+                    }
                 }
-            } else if (tid < nbatch) {
-                const int4 pb = s_base[tid];
-                const int lx = pb.x + ((pb.w >> 1) & 1) - orgx;
-                const int ly = pb.y + ((pb.w >> 2) & 1) - orgy;
-                const int lz = pb.z + ((pb.w >> 3) & 1) - orgz;
-                const float4 nr = s_nrm[tid];
-                const int li = lx + kBrick * (ly + kBrick * lz);
-                atomicAdd(&acc[0][li], (unsigned long long)fix40(nr.x));
-                atomicAdd(&acc[1][li], (unsigned long long)fix40(nr.y));
-                atomicAdd(&acc[2][li], (unsigned long long)fix40(nr.z));
-                atomicAdd(&acc[3][li], (unsigned long long)(1ll << 40));
+            } else {
+                for (int p = 0; p < nbatch; ++p) {
+                    const int4 rb = s_rel[p];
+                    const int nx_ = rb.x + ((rb.w >> 1) & 1), ny_ = rb.y + ((rb.w >> 2) & 1);
+                    const int nz_ = rb.z + ((rb.w >> 3) & 1);
+                    if (nx_ != lx || ny_ != ly || (nz_ != lz && nz_ != lz + 4)) continue;
+                    const float4 nr = s_nrm[p];
+                    long long* u = (nz_ == lz) ? u0 : u1;
+                    u[0] += fix40(nr.x);
+                    u[1] += fix40(nr.y);
+                    u[2] += fix40(nr.z);
+                    u[3] += 1ll << 40;
+                }
             }
         }
-        __syncthreads();
         float* out = vpool + (size_t)s * 3 * kBrickVox;
-        for (int li = tid; li < kBrickVox; li += kAccThreads) {
-            const long long d = (long long)acc[3][li];
-            if (d > 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const long long* u = k ? u1 : u0;
+            const int li = lx + kBrick * (ly + kBrick * (lz + 4 * k));
+            if (u[3] > 0) {
                 // exact integer sums, one float32 quotient per voxel
-                const float sc = g.v_scale_f / fix_to_float(d);
-                out[li] = fix_to_float((long long)acc[0][li]) * sc;
-                out[kBrickVox + li] = fix_to_float((long long)acc[1][li]) * sc;
-                out[2 * kBrickVox + li] = fix_to_float((long long)acc[2][li]) * sc;
+                const float sc = g.v_scale_f / fix_to_float(u[3]);
+                out[li] = fix_to_float(u[0]) * sc;
+                out[kBrickVox + li] = fix_to_float(u[1]) * sc;
+                out[2 * kBrickVox + li] = fix_to_float(u[2]) * sc;
             } else {
                 out[li] = 0.f;
                 out[kBrickVox + li] = 0.f;
                 out[2 * kBrickVox + li] = 0.f;
             }
         }
-        __syncthreads();
     }
 }
 
