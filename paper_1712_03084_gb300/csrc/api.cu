@@ -161,6 +161,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->pts.frac);
     dfree(c->pts.nrm);
     dfree(c->d_dropped);
+    dfree(c->d_wild);
     if (c->d_stage) cudaFree(c->d_stage);
     dfree(c->d_brick_cnt);
     dfree(c->d_brick_off);
@@ -269,6 +270,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         return FTR_ENOMEM;                                  \
     }
     ALLOC(c->d_dropped, 1);
+    ALLOC(c->d_wild, 1);
     ALLOC(c->d_brick_cnt, c->n_bricks);
     ALLOC(c->d_brick_off, c->n_bricks + 1);
     ALLOC(c->d_brick_cursor, c->n_bricks);
@@ -313,6 +315,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         cudaEventCreate(&c->ev_stop[s]);
     }
     cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
     double zero2[2] = {0.0, 0.0};
     float zerof[2] = {0.f, 0.f};
     cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
@@ -342,6 +345,7 @@ int ftr_reset(ftr_ctx* c) {
     c->meshed = false;
     c->n_verts = c->n_tris = 0;
     cudaError_t e = cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_reset");
     return FTR_OK;
 }

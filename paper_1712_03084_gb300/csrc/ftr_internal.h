@@ -80,6 +80,7 @@ struct ftr_ctx {
     int64_t n_pts = 0;
     int64_t points_in = 0;
     unsigned long long* d_dropped = nullptr;
+    int* d_wild = nullptr;     // set when some accepted weight lies outside [0, 1]
     void* d_stage = nullptr;   // staging for host inputs
     size_t stage_cap = 0;
 

@@ -128,6 +128,57 @@ __device__ __forceinline__ NodeInfo seg_node(const Seg4& s, int j, int x, int nx
 
 __device__ __forceinline__ int ntri_of(int cls) { return (cls == 0 || cls == 255) ? 0 : c_ntri[cls]; }
 
+// Loads of one segment (issued before any of them is used).
+struct SegLoads {
+    float4 r00, r10, r01, r11;
+    float e[4];
+};
+
+__device__ __forceinline__ SegLoads seg_issue(const float* __restrict__ A, int64_t rowbase, int x0, int nx,
+                                              int64_t sy, int64_t sz, bool hy, bool hz) {
+    const int lane = threadIdx.x & 31;
+    const int x = x0 + 4 * lane;
+    const bool valid = x < nx;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    SegLoads l;
+    l.r00 = valid ? *reinterpret_cast<const float4*>(A + rowbase + x) : z4;
+    l.r10 = (valid && hy) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy) : z4;
+    l.r01 = (valid && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sz) : z4;
+    l.r11 = (valid && hy && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy + sz) : z4;
+    const bool more = lane == 31 && x + 4 < nx;
+    const int64_t n = rowbase + x + 4;
+    l.e[0] = more ? A[n] : 0.f;
+    l.e[1] = (more && hy) ? A[n + sy] : 0.f;
+    l.e[2] = (more && hz) ? A[n + sz] : 0.f;
+    l.e[3] = (more && hy && hz) ? A[n + sy + sz] : 0.f;
+    return l;
+}
+
+__device__ __forceinline__ Seg4 seg_bits_of(const SegLoads& l, int x0, int nx, bool hy, bool hz, float L) {
+    const int lane = threadIdx.x & 31;
+    const int x = x0 + 4 * lane;
+    const bool valid = x < nx;
+    Seg4 s;
+    s.bits[0] = valid ? nib(l.r00, L) : 0;
+    s.bits[1] = (valid && hy) ? nib(l.r10, L) : 0;
+    s.bits[2] = (valid && hz) ? nib(l.r01, L) : 0;
+    s.bits[3] = (valid && hy && hz) ? nib(l.r11, L) : 0;
+    int nb[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) nb[r] = __shfl_down_sync(0xffffffffu, s.bits[r], 1) & 1;
+    if (lane == 31) {
+        const bool more = x + 4 < nx;
+        nb[0] = more && l.e[0] >= L;
+        nb[1] = more && hy && l.e[1] >= L;
+        nb[2] = more && hz && l.e[2] >= L;
+        nb[3] = more && hy && hz && l.e[3] >= L;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s.bits[r] |= nb[r] << 4;
+    return s;
+}
+
+template <int SEGS>
 __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
                                                          const float* __restrict__ levelf, int* __restrict__ cnt,
                                                          int nrows) {
@@ -140,9 +191,14 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float*
     const bool hy = y < ny - 1, hz = z < nz - 1;
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     const int64_t rowbase = (int64_t)row * nx;
+    SegLoads ld[SEGS];
+#pragma unroll
+    for (int k = 0; k < SEGS; ++k) ld[k] = seg_issue(A, rowbase, 128 * k, nx, sy, sz, hy, hz);
     int na = 0, nv = 0, nt = 0;
-    for (int x0 = 0; x0 < nx; x0 += 128) {
-        const Seg4 sb = seg_load(A, rowbase, x0, nx, sy, sz, hy, hz, L);
+#pragma unroll
+    for (int k = 0; k < SEGS; ++k) {
+        const int x0 = 128 * k;
+        const Seg4 sb = seg_bits_of(ld[k], x0, nx, hy, hz, L);
         const int xl = x0 + 4 * lane;
         // all four rows agree on all five bits: no edge or cell changes here
         const int all = sb.bits[0] & sb.bits[1] & sb.bits[2] & sb.bits[3];
@@ -392,42 +448,38 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
     }
 }
 
+// The owner of a triangle corner is this node or a node of the same row
+// (+x), of the next row (+y) or of the next plane (+z): its record is found
+// by a short scan of that row's records, whose range comes from the row
+// offsets of the scan (off_rows[row] .. off_rows[row + 1]).
 __global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restrict__ nodes, int n_nodes,
-                                                 int32_t* __restrict__ tris) {
+                                                 const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_nodes) return;
     const int4 rec = nodes[r];
     const int cls = rec.y >> 8;
-    const int nt = c_ntri[cls];
+    const int nt = ntri_of(cls);
     if (nt == 0) return;
-    const int nx = g.n[0];
-    const int64_t sxy = (int64_t)nx * g.n[1];
+    const int nx = g.n[0], ny = g.n[1];
+    const int row = rec.x / nx;
+    const int x = rec.x - row * nx;
     for (int t = 0; t < nt; ++t) {
         for (int j = 0; j < 3; ++j) {
             const int e = c_tri[cls][t][j];
             const int axis = e >> 2;
             const int cu = e & 1, cv = (e >> 1) & 1;
             // owner offset: the edge's fixed coordinates on the two other axes
-            int o[3] = {0, 0, 0};
-            if (axis == 0) {
-                o[1] = cu;
-                o[2] = cv;
-            } else if (axis == 1) {
-                o[0] = cu;
-                o[2] = cv;
-            } else {
-                o[0] = cu;
-                o[1] = cv;
-            }
-            const int64_t owner = (int64_t)rec.x + o[0] + (int64_t)nx * o[1] + sxy * o[2];
+            const int ox = axis == 0 ? 0 : cu;
+            const int oy = axis == 1 ? 0 : (axis == 0 ? cu : cv);
+            const int oz = axis == 2 ? 0 : cv;
             int4 orec = rec;
-            if (owner != rec.x) {
-                int lo = r + 1, hi = n_nodes - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if ((int64_t)nodes[mid].x < owner) lo = mid + 1; else hi = mid;
-                }
-                orec = nodes[lo];
+            if (ox | oy | oz) {
+                const int orow = row + oy + ny * oz;
+                const int ox_node = x + ox;
+                int k = off_rows[orow];
+                const int kend = off_rows[orow + 1];
+                while (k < kend - 1 && nodes[k].x - orow * nx < ox_node) ++k;
+                orec = nodes[k];
             }
             const int below = (orec.y & 7) & ((1 << axis) - 1);
             tris[3 * (int64_t)(rec.w + t) + j] = orec.z + __popc(below);
@@ -468,7 +520,12 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
     const int nr = c->mc_blocks;              // grid rows n_y n_z
     const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
     prof_begin(c, ST_MC_COUNT);
-    k_mc_count<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr);
+    switch ((c->g.n[0] + 127) / 128) {
+        case 1: k_mc_count<1><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
+        case 2: k_mc_count<2><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
+        case 3: k_mc_count<3><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
+        default: k_mc_count<4><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
+    }
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
@@ -499,7 +556,8 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int n_nodes = c->h_mc_tot[0];
     if (n_nodes > 0 && c->n_tris > 0) {
         prof_begin(c, ST_MC_TRIS);
-        k_mc_tris<<<(n_nodes + 255) / 256, 256, 0, c->stream>>>(c->g, c->d_mc_nodes, n_nodes, c->d_tris);
+        k_mc_tris<<<(n_nodes + 255) / 256, 256, 0, c->stream>>>(c->g, c->d_mc_nodes, n_nodes, c->d_mc_off,
+                                                                c->d_tris);
         c->launches++;
         e = cudaGetLastError();
         prof_end(c, ST_MC_TRIS);

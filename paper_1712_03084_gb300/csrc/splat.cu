@@ -10,11 +10,11 @@
 //   count   per point, +1 on every brick its stencil overlaps
 //   scan    one CTA: brick offsets, dense slot per touched brick
 //   fill    per point, append its index to each overlapped brick's list
-//   accum   one CTA per touched brick: every thread gathers, for its two
-//           voxels, the contributions of the brick's points into int64
-//           fixed-point registers (value * 2^40, exact and order-independent,
-//           so the result is bit-reproducible); then V = (sigma2 / sigma1) U / d
-//           is written to the brick's slot.
+//   accum   one CTA per touched brick: 64 lanes per point evaluate the stencil
+//           nodes inside the brick and add the contributions to shared-memory
+//           fixed-point accumulators (value * 2^40 as 32-bit hi/lo halves,
+//           exact and order-independent, so the result is bit-reproducible);
+//           then V = (sigma2 / sigma1) U / d is written to the brick's slot.
 // The simple variant (nearest node floor(t + 1/2), V = mean N) uses the same
 // bricks with one node per point and d counting points.
 #include <cuda_runtime.h>
@@ -44,7 +44,7 @@ __device__ __forceinline__ double node_t(double x, double bmin, double h, double
 
 __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
-                         float4* pfrac, float4* pnrm, unsigned long long* dropped) {
+                         float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     bool ok = true;
@@ -68,7 +68,9 @@ __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict_
         fl[0] = fl[1] = fl[2] = 0;
     }
     pbase[base + i] = make_int4(fl[0], fl[1], fl[2], ok ? (1 | (up << 1)) : 0);
-    pfrac[base + i] = make_float4(fr[0], fr[1], fr[2], w ? w[i] : 1.0f);
+    const float wi = w ? w[i] : 1.0f;
+    if (ok && !(wi >= 0.f && wi <= 1.f)) atomicOr(wild_weights, 1);   // outside the fast path's range
+    pfrac[base + i] = make_float4(fr[0], fr[1], fr[2], wi);
     pnrm[base + i] = make_float4(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], 0.f);
 }
 
@@ -249,13 +251,34 @@ __device__ __forceinline__ float fix_to_float(long long v) {
     return neg ? -f : f;
 }
 
-constexpr int kStage = 256;   // point records staged in shared memory per batch
+constexpr int kStage = 128;       // point records staged in shared memory per batch
+constexpr int kFastEntries = 2047; // the split accumulators stay exact up to this many points per brick
 
-// One CTA per touched brick (persistent over the list).  Each thread owns two
-// voxels of the brick, (lx, ly, lz) and (lx, ly, lz + 4), and gathers from
-// the staged points the contributions whose 4^3 stencil contains them, into
-// int64 fixed-point registers: no atomics, and the exact integer sums do not
-// depend on the (scheduling-dependent) order of the brick's point list.
+// Fixed-point contribution round(v * 2^40) = hi 2^20 + lo with lo in [0, 2^20)
+// (float ops only: x = v 2^20, trunc and the exact remainder as in fix40).
+__device__ __forceinline__ void fix40_split(float v, int& hi, unsigned& lo) {
+    const float x = v * 1048576.0f;
+    const float hf = truncf(x);
+    int h = (int)hf;
+    int l = __float2int_rn((x - hf) * 1048576.0f);   // in [-2^20, 2^20]
+    if (l < 0) {
+        l += 1 << 20;
+        h -= 1;
+    } else if (l >= (1 << 20)) {
+        l -= 1 << 20;
+        h += 1;
+    }
+    hi = h;
+    lo = (unsigned)l;
+}
+
+// One CTA per touched brick (persistent over the list).  64 lanes per point
+// evaluate the stencil nodes that fall inside the brick and add the
+// fixed-point contributions to shared-memory accumulators.  Integer sums are
+// exact and order-independent, so V is bit-reproducible.  Fast path: 32-bit
+// atomics on (hi, lo) halves, exact while a voxel receives fewer than 2^11
+// contributions of magnitude <= 1 (at most kFastEntries points per brick,
+// weights in [0, 1]); otherwise the brick takes the 64-bit atomic path.
 __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const int* __restrict__ active,
                                                              const int* __restrict__ meta,
                                                              const int* __restrict__ off,
@@ -263,79 +286,105 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const int4* __restrict__ pbase,
                                                              const float4* __restrict__ pfrac,
                                                              const float4* __restrict__ pnrm,
+                                                             const int* __restrict__ wild_weights,
                                                              float* __restrict__ vpool) {
-    __shared__ int4 s_rel[kStage];     // stencil base relative to the brick origin, flags
+    __shared__ __align__(16) unsigned acc[8][kBrickVox];   // fast: [c] hi, [4 + c] lo; slow: 4 x int64
+    __shared__ int4 s_base[kStage];
     __shared__ float4 s_frac[kStage];
     __shared__ float4 s_nrm[kStage];
+    unsigned long long* acc64 = reinterpret_cast<unsigned long long*>(&acc[0][0]);
     const int nact = meta[0];
     const int tid = threadIdx.x;
-    const int lx = tid & 7, ly = (tid >> 3) & 7, lz = tid >> 6;   // second voxel at lz + 4
+    const int o = tid & 63;
+    const int ox = o & 3, oy = (o >> 2) & 3, oz = o >> 4;
+    const int pl = tid >> 6;
+    const bool weights_ok = wild_weights[0] == 0;
     for (int s = blockIdx.x; s < nact; s += gridDim.x) {
         const int b = active[s];
         const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
         const int orgx = bx * kBrick, orgy = by * kBrick, orgz = bz * kBrick;
-        long long u0[4] = {0, 0, 0, 0}, u1[4] = {0, 0, 0, 0};
         const int e0 = off[b], e1 = off[b + 1];
+        const bool fast = weights_ok && (e1 - e0) <= kFastEntries;     // block-uniform
+        for (int k = tid; k < 8 * kBrickVox; k += kAccThreads) (&acc[0][0])[k] = 0u;
         for (int eb = e0; eb < e1; eb += kStage) {
             const int nbatch = min(kStage, e1 - eb);
             __syncthreads();
             if (tid < nbatch) {
                 const int i = entries[eb + tid];
-                const int4 pb = pbase[i];
-                s_rel[tid] = make_int4(pb.x - orgx, pb.y - orgy, pb.z - orgz, pb.w);
+                s_base[tid] = pbase[i];
                 s_frac[tid] = pfrac[i];
                 s_nrm[tid] = pnrm[i];
             }
             __syncthreads();
             if (g.mode == FTR_SPLAT_WEIGHTED) {
-                for (int p = 0; p < nbatch; ++p) {
-                    const int4 rb = s_rel[p];
-                    // stencil offset of this voxel: node = base - 1 + o, o in 0..3
-                    const unsigned ox = (unsigned)(lx - rb.x + 1), oy = (unsigned)(ly - rb.y + 1);
-                    if (ox > 3u || oy > 3u) continue;
-                    const int oz0 = lz - rb.z + 1;
-                    const bool in0 = (unsigned)oz0 <= 3u, in1 = (unsigned)(oz0 + 4) <= 3u;
-                    if (!in0 && !in1) continue;
+                for (int p = pl; p < nbatch; p += kAccThreads / 64) {
+                    const int4 pb = s_base[p];
+                    const int lx = pb.x - 1 + ox - orgx;
+                    const int ly = pb.y - 1 + oy - orgy;
+                    const int lz = pb.z - 1 + oz - orgz;
+                    if ((unsigned)lx >= kBrick || (unsigned)ly >= kBrick || (unsigned)lz >= kBrick) continue;
                     const float4 fr = s_frac[p];
                     const float4 nr = s_nrm[p];
                     // X - p(q) = (t - q) h with t - q = frac + 1 - offset
                     const float dx = (fr.x + 1.0f - (float)ox) * g.hf[0];
                     const float dy = (fr.y + 1.0f - (float)oy) * g.hf[1];
-                    const float dxy = dx * dx + dy * dy;
+                    const float dz = (fr.z + 1.0f - (float)oz) * g.hf[2];
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
+                    const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
+                    const int li = lx + kBrick * (ly + kBrick * lz);
+                    const float val[4] = {e1v * nr.x, e1v * nr.y, e1v * nr.z, e2v};
+                    if (fast) {
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        if (!(k ? in1 : in0)) continue;
-                        const float dz = (fr.z + 1.0f - (float)(oz0 + 4 * k)) * g.hf[2];
-                        const float r2 = dxy + dz * dz;
-                        const float e1v = expf(-r2 * g.inv_s1sq) * fr.w;   // sigma1 * g1 * W
-                        const float e2v = expf(-r2 * g.inv_s2sq) * fr.w;   // sigma2 * g2 * W
-                        long long* u = k ? u1 : u0;
-                        u[0] += fix40(e1v * nr.x);
-                        u[1] += fix40(e1v * nr.y);
-                        u[2] += fix40(e1v * nr.z);
-                        u[3] += fix40(e2v);
+                        for (int c = 0; c < 4; ++c) {
+                            int hi;
+                            unsigned lo;
+                            fix40_split(val[c], hi, lo);
+                            atomicAdd(reinterpret_cast<int*>(&acc[c][li]), hi);
+                            atomicAdd(&acc[4 + c][li], lo);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            atomicAdd(&acc64[c * kBrickVox + li], (unsigned long long)fix40(val[c]));
                     }
                 }
             } else {
-                for (int p = 0; p < nbatch; ++p) {
-                    const int4 rb = s_rel[p];
-                    const int nx_ = rb.x + ((rb.w >> 1) & 1), ny_ = rb.y + ((rb.w >> 2) & 1);
-                    const int nz_ = rb.z + ((rb.w >> 3) & 1);
-                    if (nx_ != lx || ny_ != ly || (nz_ != lz && nz_ != lz + 4)) continue;
+                for (int p = tid; p < nbatch; p += kAccThreads) {
+                    const int4 pb = s_base[p];
+                    const int lx = pb.x + ((pb.w >> 1) & 1) - orgx;
+                    const int ly = pb.y + ((pb.w >> 2) & 1) - orgy;
+                    const int lz = pb.z + ((pb.w >> 3) & 1) - orgz;
                     const float4 nr = s_nrm[p];
-                    long long* u = (nz_ == lz) ? u0 : u1;
-                    u[0] += fix40(nr.x);
-                    u[1] += fix40(nr.y);
-                    u[2] += fix40(nr.z);
-                    u[3] += 1ll << 40;
+                    const int li = lx + kBrick * (ly + kBrick * lz);
+                    const float val[3] = {nr.x, nr.y, nr.z};
+                    if (fast) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            int hi;
+                            unsigned lo;
+                            fix40_split(val[c], hi, lo);
+                            atomicAdd(reinterpret_cast<int*>(&acc[c][li]), hi);
+                            atomicAdd(&acc[4 + c][li], lo);
+                        }
+                        atomicAdd(reinterpret_cast<int*>(&acc[3][li]), 1 << 20);   // count: 2^40 = 2^20 * 2^20
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            atomicAdd(&acc64[c * kBrickVox + li], (unsigned long long)fix40(val[c]));
+                        atomicAdd(&acc64[3 * kBrickVox + li], 1ull << 40);
+                    }
                 }
             }
         }
+        __syncthreads();
         float* out = vpool + (size_t)s * 3 * kBrickVox;
+        for (int li = tid; li < kBrickVox; li += kAccThreads) {
+            long long u[4];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const long long* u = k ? u1 : u0;
-            const int li = lx + kBrick * (ly + kBrick * (lz + 4 * k));
+            for (int c = 0; c < 4; ++c)
+                u[c] = fast ? (long long)(int)acc[c][li] * (1ll << 20) + (long long)acc[4 + c][li]
+                            : (long long)acc64[c * kBrickVox + li];
             if (u[3] > 0) {
                 // exact integer sums, one float32 quotient per voxel
                 const float sc = g.v_scale_f / fix_to_float(u[3]);
@@ -348,6 +397,7 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                 out[2 * kBrickVox + li] = 0.f;
             }
         }
+        __syncthreads();
     }
 }
 
@@ -390,7 +440,7 @@ cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const 
     if (n == 0) return cudaSuccess;
     // small CTAs spread the few float64 operations per point over every SM
     k_ingest<<<blocks_for(n, 32), 32, 0, c->stream>>>(pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
-                                                       c->pts.nrm, c->d_dropped);
+                                                       c->pts.nrm, c->d_dropped, c->d_wild);
     c->launches++;
     return cudaGetLastError();
 }
@@ -425,7 +475,7 @@ cudaError_t launch_splat(ftr_ctx* c) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     const int grid = (sms > 0 ? sms : 152) * 8;
     k_splat_accum<<<grid, kAccThreads, 0, c->stream>>>(c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
-                                                       c->pts.base, c->pts.frac, c->pts.nrm, c->d_vpool);
+                                                       c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool);
     c->launches++;
     prof_end(c, ST_SPLAT_ACC);
     return cudaGetLastError();

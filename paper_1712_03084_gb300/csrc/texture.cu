@@ -109,17 +109,20 @@ __device__ __forceinline__ bool eval_camera(const ViewDev& vw, const T X[3], T t
     return true;
 }
 
+// One thread per (vertex, camera): G = next power of two >= k lanes per
+// vertex, the blend sums combined across the group with shuffles.
+template <int G>
 __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __restrict__ verts, int64_t nv,
                                                  double tau, float* __restrict__ wout, float* __restrict__ uvout,
                                                  uint8_t* __restrict__ rgbout, uint8_t* __restrict__ texout) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv) return;
-    const float Xf[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
-    float acc[3] = {0.f, 0.f, 0.f};
-    float wsum = 0.f;
-    for (int k = 0; k < vs.k; ++k) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / G;
+    const int k = (int)(t % G);
+    const bool live = i < nv && k < vs.k;
+    float wk = 0.f, ur = -1.f, vr = -1.f, rgb[3] = {0.f, 0.f, 0.f};
+    if (live) {
         const ViewDev& vw = vs.v[k];
-        float wk, ur, vr, rgb[3];
+        const float Xf[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
         if (!eval_camera<float, true>(vw, Xf, (float)tau, wk, ur, vr, rgb)) {
             const double Xd[3] = {Xf[0], Xf[1], Xf[2]};
             double wd, ud, vd, cd[3];
@@ -131,26 +134,32 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
             rgb[1] = (float)cd[1];
             rgb[2] = (float)cd[2];
         }
-        if (wk > 0.f) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc[c] += wk * rgb[c];
-            wsum += wk;
-        }
         if (wout) wout[i * vs.k + k] = wk;
         if (uvout) {
             uvout[2 * (i * vs.k + k)] = ur;
             uvout[2 * (i * vs.k + k) + 1] = vr;
         }
     }
-    if (rgbout) {
+    float acc[3], wsum = wk > 0.f ? wk : 0.f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float col = wsum > 0.f ? floorf(acc[c] / wsum + 0.5f) : 0.f;
-            col = fminf(fmaxf(col, 0.f), 255.f);
-            rgbout[3 * i + c] = (uint8_t)col;
-        }
+    for (int c = 0; c < 3; ++c) acc[c] = wk > 0.f ? wk * rgb[c] : 0.f;
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o, G);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
     }
-    if (texout) texout[i] = wsum > 0.f ? 1 : 0;
+    if (k == 0 && i < nv) {
+        if (rgbout) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float col = wsum > 0.f ? floorf(acc[c] / wsum + 0.5f) : 0.f;
+                col = fminf(fmaxf(col, 0.f), 255.f);
+                rgbout[3 * i + c] = (uint8_t)col;
+            }
+        }
+        if (texout) texout[i] = wsum > 0.f ? 1 : 0;
+    }
 }
 
 }  // namespace
@@ -159,8 +168,14 @@ cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float
                            uint8_t* textured) {
     if (c->n_verts == 0) return cudaSuccess;
     prof_begin(c, ST_TEXTURE);
-    k_texture<<<(unsigned)((c->n_verts + 255) / 256), 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts,
-                                                                           (double)depth_tol, w, uv, rgb, textured);
+    const int G = vs.k <= 1 ? 1 : (vs.k <= 2 ? 2 : (vs.k <= 4 ? 4 : 8));
+    const unsigned blocks = (unsigned)((c->n_verts * G + 255) / 256);
+    switch (G) {
+        case 1: k_texture<1><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
+        case 2: k_texture<2><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
+        case 4: k_texture<4><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
+        default: k_texture<8><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
+    }
     c->launches++;
     prof_end(c, ST_TEXTURE);
     return cudaGetLastError();
