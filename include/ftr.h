@@ -195,6 +195,34 @@ const char* ftr_stage_name(int stage);
 /* Number of kernels this context has launched so far. */
 int64_t ftr_launch_count(const ftr_ctx* ctx);
 
+/* ---- allocation-free variant ------------------------------------------------ */
+
+/*
+ * Iso-level L = mean over the accepted points of trilinear A (the same value
+ * ftr_solve computes), without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory where they need the level -- a per-frame loop with a hard
+ * latency budget (cudaMalloc/cudaFree may synchronise the device), or a host
+ * framework that owns every allocation and gives the library none.
+ *
+ * A: n_z x n_y x n_x float32 indicator (device); grid_n, bbox as in
+ * ftr_create; points: n x 3 float32 (device); level_out: one double, host or
+ * device (a host pointer makes the call wait for the stream); stream: the
+ * cudaStream_t to use, NULL = the default stream.  Needs no context.
+ *
+ * Scratch: a static 64 KB device array inside the library (one per device
+ * that loads it, kept until the process exits), so n is limited to
+ * 4,194,304 points; larger n returns FTR_EINVAL before any work.  The first
+ * call on each device looks up that array's device address; make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.  Every scratch slot a call reads
+ * is written by that call first, so nothing needs clearing between calls.
+ * Returns FTR_EINVAL for bad arguments, FTR_ECUDA if a CUDA call fails.
+ */
+int ftr_iso_level_noalloc(const float* A, const int grid_n[3], const float bbox[6], const float* points,
+                          int64_t n, double* level_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

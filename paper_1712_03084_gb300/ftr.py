@@ -80,6 +80,9 @@ _SIGNATURES = [
     ("ftr_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("ftr_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("ftr_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("ftr_iso_level_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 EXPORTED = [s[0] for s in _SIGNATURES]
@@ -272,6 +275,18 @@ def ftr_stage_name(s):
 
 def ftr_launch_count(ctx):
     return int(load().ftr_launch_count(ctx))
+
+
+def ftr_iso_level_noalloc(A, grid_n, bbox, points, n=None, level_out=None, stream=None):
+    """Level without device allocation (see include/ftr.h); returns L when level_out is None."""
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid_n])
+    b = (ctypes.c_float * 6)(*[float(v) for v in bbox])
+    n = int(points.shape[0]) if n is None else int(n)
+    out = np.zeros(1, np.float64) if level_out is None else level_out
+    code = load().ftr_iso_level_noalloc(_ptr(A, np.float32), g, b, _ptr(points, np.float32), n, _ptr(out), stream)
+    if code != FTR_OK:
+        raise FtrError(code, "ftr_iso_level_noalloc failed")
+    return float(out[0]) if level_out is None else None
 
 
 # ---------------------------------------------------------------- convenience
