@@ -179,6 +179,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_level);
     dfree(c->d_levelf);
     dfree(c->d_level_part);
+    dfree(c->d_ticket);
     dfree(c->d_mc_blk);
     dfree(c->d_mc_tile);
     dfree(c->d_mc_off);
@@ -287,6 +288,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_level, 2);
     ALLOC(c->d_levelf, 2);
     ALLOC(c->d_level_part, 2 * c->level_blocks);
+    ALLOC(c->d_ticket, 1);
     c->mc_blocks = grid_n[1] * grid_n[2];      // marching cubes counts per grid row
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
     ALLOC(c->d_mc_tile, (c->mc_blocks + 2047) / 2048 + 1);
@@ -316,6 +318,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     }
     cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
     double zero2[2] = {0.0, 0.0};
     float zerof[2] = {0.f, 0.f};
     cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
@@ -441,36 +444,61 @@ int ftr_solve(ftr_ctx* c, double* iso_level_out) {
     return FTR_OK;
 }
 
+namespace {
+
+// Grow the mesh buffers to hold at least (na, nv, nt) with 50 % headroom.
+cudaError_t grow_mesh(ftr_ctx* c, int64_t na, int64_t nv, int64_t nt) {
+    cudaError_t e = cudaSuccess;
+    if (na > c->cap_mc_nodes) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c->d_mc_nodes);
+        const int64_t cap = na + na / 2 + 1024;
+        if ((e = dalloc(&c->d_mc_nodes, cap)) != cudaSuccess) return e;
+        c->cap_mc_nodes = cap;
+    }
+    if (nv > c->cap_verts) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c->d_verts);
+        dfree(c->d_vnrm);
+        const int64_t cap = nv + nv / 2 + 1024;
+        if ((e = dalloc(&c->d_verts, 3 * cap)) != cudaSuccess) return e;
+        if ((e = dalloc(&c->d_vnrm, 3 * cap)) != cudaSuccess) return e;
+        c->cap_verts = cap;
+    }
+    if (nt > c->cap_tris) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c->d_tris);
+        const int64_t cap = nt + nt / 2 + 1024;
+        if ((e = dalloc(&c->d_tris, 3 * cap)) != cudaSuccess) return e;
+        c->cap_tris = cap;
+    }
+    return e;
+}
+
+}  // namespace
+
 int ftr_extract_mesh(ftr_ctx* c, ftr_mesh* out) {
     if (!c || !out) return FTR_EINVAL;
     if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_extract_mesh: nothing solved");
     cudaError_t e;
+    // first use: room for a surface of M / 256 vertices (grows on demand)
+    if (c->cap_verts == 0) {
+        const int64_t guess = c->M / 256 + 4096;
+        if ((e = grow_mesh(c, guess, guess, 2 * guess)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
+    }
+    // counts, offsets and the emission run back to back; the host waits once
     if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: count");
+    if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
     const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
-    if (na > c->cap_mc_nodes) {
-        dfree(c->d_mc_nodes);
-        int64_t cap = na + na / 2 + 1024;
-        if ((e = dalloc(&c->d_mc_nodes, cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: nodes");
-        c->cap_mc_nodes = cap;
-    }
-    if (nv > c->cap_verts) {
-        dfree(c->d_verts);
-        dfree(c->d_vnrm);
-        int64_t cap = nv + nv / 2 + 1024;
-        if ((e = dalloc(&c->d_verts, 3 * cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: vertices");
-        if ((e = dalloc(&c->d_vnrm, 3 * cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: normals");
-        c->cap_verts = cap;
-    }
-    if (nt > c->cap_tris) {
-        dfree(c->d_tris);
-        int64_t cap = nt + nt / 2 + 1024;
-        if ((e = dalloc(&c->d_tris, 3 * cap)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: tris");
-        c->cap_tris = cap;
+    if (na > c->cap_mc_nodes || nv > c->cap_verts || nt > c->cap_tris) {
+        // the buffers were too small: the kernels skipped the writes past them
+        if ((e = grow_mesh(c, na, nv, nt)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: grow");
+        if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
     }
     c->n_verts = nv;
     c->n_tris = nt;
-    if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
     c->meshed = true;
     out->vertices = c->d_verts;
     out->normals = c->d_vnrm;

@@ -107,6 +107,7 @@ struct ftr_ctx {
     double* d_level = nullptr;     // [0] L, [1] accepted count
     float* d_levelf = nullptr;     // [0] L rounded up to float32, [1] L rounded to nearest
     double* d_level_part = nullptr;
+    unsigned* d_ticket = nullptr;   // last-CTA ticket of the level reduction (0 between launches)
     int level_blocks = 0;
     bool solved = false;
     bool v_external = false;   // V was set with ftr_set_field_V: solve skips the splat

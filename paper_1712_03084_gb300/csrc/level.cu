@@ -28,10 +28,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;
 }
 
+// Per-CTA partial sums; the last CTA to finish (ticket counter) sums the
+// partials in block order and writes L (fixed order: bit-reproducible).
 __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int4* __restrict__ pbase,
                                                             const float4* __restrict__ pfrac, int64_t n,
-                                                            const float* __restrict__ A, double* part) {
+                                                            const float* __restrict__ A, double* part,
+                                                            unsigned* ticket, double* level, float* levelf) {
     __shared__ double sh[kThreads / 32];
+    __shared__ bool last;
     const int nx = g.n[0];
     const int64_t nxy = (int64_t)nx * g.n[1];
     double sum = 0.0, cnt = 0.0;
@@ -56,29 +60,30 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = s;
         part[2 * blockIdx.x + 1] = c;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
-}
-
-// One warp: lane l sums partials l, l + 32, ... in order, then a fixed
-// shuffle tree combines the lanes.
-__global__ void k_level_final(const double* __restrict__ part, int nblocks, double* level, float* levelf) {
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
     const int lane = threadIdx.x;
-    double s = 0.0, c = 0.0;
-    for (int b = lane; b < nblocks; b += 32) {
-        s += part[2 * b];
-        c += part[2 * b + 1];
+    double ts = 0.0, tc = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+        ts += __ldcg(&part[2 * b]);
+        tc += __ldcg(&part[2 * b + 1]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_down_sync(0xffffffffu, s, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
+        ts += __shfl_down_sync(0xffffffffu, ts, o);
+        tc += __shfl_down_sync(0xffffffffu, tc, o);
     }
     if (lane == 0) {
-        const double L = c > 0.0 ? s / c : 0.0;
+        const double L = tc > 0.0 ? ts / tc : 0.0;
         level[0] = L;
-        level[1] = c;
+        level[1] = tc;
         levelf[0] = __double2float_ru(L);   // A >= L (float64) <=> A >= levelf[0] for float32 A
         levelf[1] = __double2float_rn(L);
+        *ticket = 0u;                        // ready for the next launch
     }
 }
 
@@ -86,11 +91,8 @@ __global__ void k_level_final(const double* __restrict__ part, int nblocks, doub
 
 cudaError_t launch_level(ftr_ctx* c) {
     k_level_partial<<<c->level_blocks, kThreads, 0, c->stream>>>(c->g, c->pts.base, c->pts.frac, c->n_pts, c->d_A,
-                                                                 c->d_level_part);
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_level_final<<<1, 32, 0, c->stream>>>(c->d_level_part, c->level_blocks, c->d_level, c->d_levelf);
+                                                                 c->d_level_part, c->d_ticket, c->d_level,
+                                                                 c->d_levelf);
     c->launches++;
     return cudaGetLastError();
 }

@@ -341,7 +341,7 @@ __device__ __forceinline__ float grad_axis(const float* __restrict__ A, int64_t 
 // position p(q) + t h_a e_a, in float32 (no decision depends on them; the
 // error is a few float32 ulps of the coordinates), normal = -grad A lerped.
 __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __restrict__ A, float Ln,
-                                              int64_t n, const int q[3], int flags, int vi,
+                                              int64_t n, const int q[3], int flags, int vi, int cap_v,
                                               float* __restrict__ verts, float* __restrict__ vnrm) {
     const int nn[3] = {g.n[0], g.n[1], g.n[2]};
     const int64_t st[3] = {1, (int64_t)g.n[0], (int64_t)g.n[0] * g.n[1]};
@@ -367,6 +367,7 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
         }
         const float len2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
         const float inv = len2 > 0.f ? rsqrtf(len2) : 0.f;
+        if (vi >= cap_v) return;   // buffers too small: the host grows them and runs again
         verts[3 * (int64_t)vi + 0] = p[0];
         verts[3 * (int64_t)vi + 1] = p[1];
         verts[3 * (int64_t)vi + 2] = p[2];
@@ -380,8 +381,9 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
 __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
                                                         const float* __restrict__ levelf,
                                                         const int* __restrict__ cnt, const int* __restrict__ off,
-                                                        int nrows, int4* __restrict__ nodes,
-                                                        float* __restrict__ verts, float* __restrict__ vnrm) {
+                                                        int nrows, int4* __restrict__ nodes, int cap_nodes,
+                                                        float* __restrict__ verts, float* __restrict__ vnrm,
+                                                        int cap_v) {
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows || cnt[row] == 0) return;   // warp-uniform: no surface on this row
     const int lane = threadIdx.x & 31;
@@ -433,10 +435,11 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
                 const int t = ntri_of(ni[j].cls);
                 if (ni[j].flags == 0 && t == 0) continue;
                 const int64_t n = rowbase + xl + j;
-                nodes[ja++] = make_int4((int)n, ni[j].flags | (ni[j].cls << 8), jv, jt);
+                if (ja < cap_nodes) nodes[ja] = make_int4((int)n, ni[j].flags | (ni[j].cls << 8), jv, jt);
+                ++ja;
                 if (ni[j].flags) {
                     const int q[3] = {xl + j, y, z};
-                    emit_vertices(g, A, Ln, n, q, ni[j].flags, jv, verts, vnrm);
+                    emit_vertices(g, A, Ln, n, q, ni[j].flags, jv, cap_v, verts, vnrm);
                 }
                 jv += __popc(ni[j].flags);
                 jt += t;
@@ -452,10 +455,8 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* 
 // (+x), of the next row (+y) or of the next plane (+z): its record is found
 // by a short scan of that row's records, whose range comes from the row
 // offsets of the scan (off_rows[row] .. off_rows[row + 1]).
-__global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restrict__ nodes, int n_nodes,
-                                                 const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_nodes) return;
+__device__ __forceinline__ void tris_of_node(const GridDev& g, const int4* __restrict__ nodes, int r,
+                                                  const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
     const int4 rec = nodes[r];
     const int cls = rec.y >> 8;
     const int nt = ntri_of(cls);
@@ -485,6 +486,15 @@ __global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restri
             tris[3 * (int64_t)(rec.w + t) + j] = orec.z + __popc(below);
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restrict__ nodes,
+                                                 const int* __restrict__ totals, int cap_nodes, int cap_tris,
+                                                 const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
+    const int n_nodes = totals[0];
+    if (n_nodes > cap_nodes || totals[2] > cap_tris) return;   // the host grows the buffers and runs again
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_nodes; r += gridDim.x * blockDim.x)
+        tris_of_node(g, nodes, r, off_rows, tris);
 }
 
 __global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const float* __restrict__ levelf,
@@ -548,20 +558,21 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
     prof_begin(c, ST_MC_EMIT);
     k_mc_emit<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, c->d_mc_off, nr,
-                                                  c->d_mc_nodes, c->d_verts, c->d_vnrm);
+                                                  c->d_mc_nodes, (int)c->cap_mc_nodes, c->d_verts, c->d_vnrm,
+                                                  (int)c->cap_verts);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);
     if (e != cudaSuccess) return e;
-    const int n_nodes = c->h_mc_tot[0];
-    if (n_nodes > 0 && c->n_tris > 0) {
-        prof_begin(c, ST_MC_TRIS);
-        k_mc_tris<<<(n_nodes + 255) / 256, 256, 0, c->stream>>>(c->g, c->d_mc_nodes, n_nodes, c->d_mc_off,
-                                                                c->d_tris);
-        c->launches++;
-        e = cudaGetLastError();
-        prof_end(c, ST_MC_TRIS);
-    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    prof_begin(c, ST_MC_TRIS);
+    k_mc_tris<<<(sms > 0 ? sms : 152) * 4, 256, 0, c->stream>>>(c->g, c->d_mc_nodes, c->d_mc_off + 3 * (nr + 1),
+                                                                 (int)c->cap_mc_nodes, (int)c->cap_tris,
+                                                                 c->d_mc_off, c->d_tris);
+    c->launches++;
+    e = cudaGetLastError();
+    prof_end(c, ST_MC_TRIS);
     return e;
 }
 
