@@ -21,6 +21,7 @@ shard), launched with torch.distributed.run; the max over ranks is taken.
 """
 
 import argparse
+import gc
 import glob
 import hashlib
 import json
@@ -338,6 +339,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     clocks.start()
+    gc.disable()          # no collector pauses inside the timed steps
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.fill_(float(i))
@@ -345,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
             m = step()
             evs[i][1].record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     barrier()
     clk = clocks.stop()
     launches = ctx.launch_count() - l0
@@ -457,6 +460,7 @@ def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
         times = []
         if world > 1:
             torch.distributed.barrier()
+        gc.disable()
         for i in range(args.steps):
             flush.fill_(float(i))
             torch.cuda.synchronize()
@@ -464,6 +468,7 @@ def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
             step()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
+        gc.enable()
     total = float(sum(times))
     if world > 1:
         t = torch.tensor([total], device=dev)
