@@ -53,7 +53,8 @@ typedef enum {
     FTR_ENOMEM = -2,    /* device allocation failed                             */
     FTR_ECUDA = -3,     /* a CUDA call failed; the context may be unusable      */
     FTR_ETIMEOUT = -4,  /* reserved for bounded device waits                    */
-    FTR_ESTATE = -5     /* call out of order (e.g. extract before solve)        */
+    FTR_ESTATE = -5,    /* call out of order (e.g. extract before solve)        */
+    FTR_ECAPACITY = -6  /* caller buffers too small for the result (see ftr_frame_finish) */
 } ftr_status;
 
 enum { FTR_SPLAT_WEIGHTED = 0, FTR_SPLAT_SIMPLE = 1 };
@@ -153,6 +154,34 @@ typedef struct {
  * and the blend are evaluated in float64; the colour is floor(c + 1/2).
  */
 int ftr_texture(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out);
+
+/* ---- frames without a host wait in the middle --------------------------------
+ *
+ * ftr_extract_mesh and ftr_texture return counts or host data, so the host
+ * waits for the GPU between them.  The three calls below enqueue the same
+ * work with no wait until ftr_frame_finish, so a whole frame (splat, solve,
+ * mesh, texture) is queued at once:
+ *
+ *   ftr_extract_mesh_async  marching cubes into the context's mesh buffers
+ *                           sized by ftr_mesh_capacity() (grown from earlier
+ *                           frames); nothing is written past them.
+ *   ftr_texture_async       per-vertex texture data (as ftr_texture) for that
+ *                           mesh; views' images and all outputs must be device
+ *                           memory with room for out_capacity vertices, and
+ *                           must stay valid until ftr_frame_finish.
+ *   ftr_frame_finish        waits; if the mesh outgrew the buffers, grows them
+ *                           and redoes the marching cubes (and the texture, if
+ *                           out_capacity suffices); fills *out.  Returns
+ *                           FTR_ECAPACITY, with *out valid, when the mesh has
+ *                           more vertices than out_capacity (call ftr_texture
+ *                           with larger outputs).
+ */
+int ftr_extract_mesh_async(ftr_ctx* ctx);
+int ftr_texture_async(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out,
+                      int64_t out_capacity);
+int ftr_frame_finish(ftr_ctx* ctx, ftr_mesh* out);
+/* Vertex capacity of the context's mesh buffers (0 before the first mesh). */
+int64_t ftr_mesh_capacity(const ftr_ctx* ctx);
 
 /* Points added since the last reset, and how many of them were dropped. */
 int ftr_stats(const ftr_ctx* ctx, int64_t* points_in, int64_t* points_dropped);

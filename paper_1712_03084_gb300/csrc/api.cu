@@ -620,6 +620,108 @@ int ftr_texture(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_t
     return FTR_OK;
 }
 
+int ftr_extract_mesh_async(ftr_ctx* c) {
+    if (!c) return FTR_EINVAL;
+    if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_extract_mesh_async: nothing solved");
+    cudaError_t e;
+    if (c->cap_verts == 0) {
+        const int64_t guess = c->M / 256 + 4096;
+        if ((e = grow_mesh(c, guess, guess, 2 * guess)) != cudaSuccess) return cuda_fail(c, e, "extract_async");
+    }
+    if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: count");
+    if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: emit");
+    c->meshed = false;
+    c->mesh_pending = true;
+    c->tex_pending = false;
+    return FTR_OK;
+}
+
+int64_t ftr_mesh_capacity(const ftr_ctx* c) { return c ? c->cap_verts : 0; }
+
+int ftr_texture_async(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_tex* out,
+                      int64_t out_capacity) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_texture_async: no pending mesh");
+    if (k < 0 || k > kMaxViews || (k > 0 && !views)) return set_err(c, FTR_EINVAL, "ftr_texture_async: 0 <= k <= 8");
+    if (!(depth_tol >= 0.f) || out_capacity < 0) return set_err(c, FTR_EINVAL, "ftr_texture_async: bad argument");
+    ViewSet vs;
+    memset(&vs, 0, sizeof(vs));
+    vs.k = k;
+    for (int i = 0; i < k; ++i) {
+        const ftr_view& v = views[i];
+        if (v.w <= 0 || v.h <= 0 || v.rgb_w <= 0 || v.rgb_h <= 0 || !is_device_ptr(v.depth) ||
+            !is_device_ptr(v.conf) || !is_device_ptr(v.rgb))
+            return set_err(c, FTR_EINVAL, "ftr_texture_async: view %d needs device images", i);
+        ViewDev& d = vs.v[i];
+        d.w = v.w;
+        d.h = v.h;
+        d.rgb_w = v.rgb_w;
+        d.rgb_h = v.rgb_h;
+        for (int j = 0; j < 9; ++j) {
+            d.K[j] = d.Kf[j] = v.K[j];
+            d.Krgb[j] = d.Krgbf[j] = v.K_rgb[j];
+        }
+        for (int j = 0; j < 12; ++j) {
+            d.RT[j] = d.RTf[j] = v.world_to_cam[j];
+            d.RTrgb[j] = d.RTrgbf[j] = v.world_to_rgb[j];
+        }
+        d.depth = v.depth;
+        d.conf = v.conf;
+        d.rgb = v.rgb;
+    }
+    const void* outs[4] = {out->weights, out->uv, out->rgb, out->textured};
+    for (int i = 0; i < 4; ++i)
+        if (outs[i] && !is_device_ptr(outs[i]))
+            return set_err(c, FTR_EINVAL, "ftr_texture_async: outputs must be device memory");
+    const int nr = c->mc_blocks;
+    const int64_t limit = out_capacity < c->cap_verts ? out_capacity : c->cap_verts;
+    cudaError_t e = launch_texture_bounded(c, vs, depth_tol, limit, c->d_mc_off + 3 * (nr + 1) + 1, out->weights,
+                                           out->uv, out->rgb, out->textured);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_texture_async");
+    c->tex_pending = true;
+    c->tex_vs = vs;
+    c->tex_tol = depth_tol;
+    c->tex_capacity = out_capacity;
+    c->tex_w = out->weights;
+    c->tex_uv = out->uv;
+    c->tex_rgb = out->rgb;
+    c->tex_flag = out->textured;
+    return FTR_OK;
+}
+
+int ftr_frame_finish(ftr_ctx* c, ftr_mesh* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_frame_finish: nothing pending");
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish");
+    const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
+    if (na > c->cap_mc_nodes || nv > c->cap_verts || nt > c->cap_tris) {
+        if ((e = grow_mesh(c, na, nv, nt)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish: grow");
+        if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish: emit");
+        if (c->tex_pending && nv <= c->tex_capacity) {
+            e = launch_texture_bounded(c, c->tex_vs, c->tex_tol, nv, nullptr, c->tex_w, c->tex_uv, c->tex_rgb,
+                                       c->tex_flag);
+            if (e != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish: texture");
+        }
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish");
+    }
+    c->n_verts = nv;
+    c->n_tris = nt;
+    c->meshed = true;
+    c->mesh_pending = false;
+    out->vertices = c->d_verts;
+    out->normals = c->d_vnrm;
+    out->tris = c->d_tris;
+    out->n_vertices = nv;
+    out->n_tris = nt;
+    const bool tex_short = c->tex_pending && nv > c->tex_capacity;
+    c->tex_pending = false;
+    if (tex_short)
+        return set_err(c, FTR_ECAPACITY, "ftr_frame_finish: %lld vertices exceed the texture outputs (%lld)",
+                       (long long)nv, (long long)c->tex_capacity);
+    return FTR_OK;
+}
+
 int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
     if (!c) return FTR_EINVAL;
     if (points_in) *points_in = c->points_in;

@@ -63,6 +63,18 @@ struct PointStore {
     int64_t cap = 0;
 };
 
+struct ViewDev {
+    int w, h, rgb_w, rgb_h;
+    double K[9], RT[12], Krgb[9], RTrgb[12];
+    float Kf[9], RTf[12], Krgbf[9], RTrgbf[12];
+    const float* depth;
+    const float* conf;
+    const uint8_t* rgb;
+};
+struct ViewSet {
+    int k;
+    ViewDev v[kMaxViews];
+};
 }  // namespace ftr
 
 struct ftr_ctx {
@@ -127,6 +139,15 @@ struct ftr_ctx {
     int64_t cap_verts = 0, cap_tris = 0;
     int64_t n_verts = 0, n_tris = 0;
     bool meshed = false;
+    bool mesh_pending = false;     // ftr_extract_mesh_async enqueued, ftr_frame_finish not yet called
+    bool tex_pending = false;      // ftr_texture_async enqueued for the pending mesh
+    ftr::ViewSet tex_vs{};
+    int64_t tex_capacity = 0;
+    float tex_tol = 0.f;
+    float* tex_w = nullptr;
+    float* tex_uv = nullptr;
+    uint8_t* tex_rgb = nullptr;
+    uint8_t* tex_flag = nullptr;
 
     // texture staging (host views / outputs)
     void* d_tex_stage = nullptr;
@@ -173,20 +194,11 @@ cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);
 cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev);
 cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);
 
-struct ViewDev {
-    int w, h, rgb_w, rgb_h;
-    double K[9], RT[12], Krgb[9], RTrgb[12];
-    float Kf[9], RTf[12], Krgbf[9], RTrgbf[12];
-    const float* depth;
-    const float* conf;
-    const uint8_t* rgb;
-};
-struct ViewSet {
-    int k;
-    ViewDev v[kMaxViews];
-};
 cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv,
                            uint8_t* rgb, uint8_t* textured);
+// Same, for min(limit, *nv_dev) vertices with the count read on the device.
+cudaError_t launch_texture_bounded(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t limit,
+                                   const int* nv_dev, float* w, float* uv, uint8_t* rgb, uint8_t* textured);
 
 // marching-cubes table (mc_table.cpp), generated from the face rule
 void mc_generate_table(int32_t ntri[256], int32_t tris[256 * kMaxTrisPerCase * 3]);

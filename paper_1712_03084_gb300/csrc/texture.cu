@@ -111,10 +111,13 @@ __device__ __forceinline__ bool eval_camera(const ViewDev& vw, const T X[3], T t
 
 // One thread per (vertex, camera): G = next power of two >= k lanes per
 // vertex, the blend sums combined across the group with shuffles.
+// nv_dev (optional): the vertex count on the device; nv then bounds it.
 template <int G>
 __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __restrict__ verts, int64_t nv,
-                                                 double tau, float* __restrict__ wout, float* __restrict__ uvout,
+                                                 const int* __restrict__ nv_dev, double tau,
+                                                 float* __restrict__ wout, float* __restrict__ uvout,
                                                  uint8_t* __restrict__ rgbout, uint8_t* __restrict__ texout) {
+    if (nv_dev) nv = min(nv, (int64_t)nv_dev[0]);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / G;
     const int k = (int)(t % G);
@@ -164,21 +167,36 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
 
 }  // namespace
 
-cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv, uint8_t* rgb,
-                           uint8_t* textured) {
-    if (c->n_verts == 0) return cudaSuccess;
+namespace {
+
+cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t nv, const int* nv_dev, float* w,
+                        float* uv, uint8_t* rgb, uint8_t* textured) {
+    if (nv <= 0) return cudaSuccess;
     prof_begin(c, ST_TEXTURE);
     const int G = vs.k <= 1 ? 1 : (vs.k <= 2 ? 2 : (vs.k <= 4 ? 4 : 8));
-    const unsigned blocks = (unsigned)((c->n_verts * G + 255) / 256);
+    const unsigned blocks = (unsigned)((nv * G + 255) / 256);
+    const double tau = (double)depth_tol;
     switch (G) {
-        case 1: k_texture<1><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
-        case 2: k_texture<2><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
-        case 4: k_texture<4><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
-        default: k_texture<8><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, c->n_verts, (double)depth_tol, w, uv, rgb, textured); break;
+        case 1: k_texture<1><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 2: k_texture<2><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 4: k_texture<4><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        default: k_texture<8><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
     }
     c->launches++;
     prof_end(c, ST_TEXTURE);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv, uint8_t* rgb,
+                           uint8_t* textured) {
+    return run_texture(c, vs, depth_tol, c->n_verts, nullptr, w, uv, rgb, textured);
+}
+
+cudaError_t launch_texture_bounded(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t limit, const int* nv_dev,
+                                   float* w, float* uv, uint8_t* rgb, uint8_t* textured) {
+    return run_texture(c, vs, depth_tol, limit, nv_dev, w, uv, rgb, textured);
 }
 
 }  // namespace ftr

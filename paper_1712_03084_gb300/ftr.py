@@ -66,6 +66,11 @@ _SIGNATURES = [
     ("ftr_mesh_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_texture", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
                                    ctypes.POINTER(ftr_tex)]),
+    ("ftr_extract_mesh_async", ctypes.c_int, [ctypes.c_void_p]),
+    ("ftr_texture_async", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
+                                         ctypes.POINTER(ftr_tex), ctypes.c_int64]),
+    ("ftr_frame_finish", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_mesh)]),
+    ("ftr_mesh_capacity", ctypes.c_int64, [ctypes.c_void_p]),
     ("ftr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ftr_frame_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -204,6 +209,27 @@ def ftr_texture(ctx, views, depth_tol, weights=None, uv=None, rgb=None, textured
     arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
     t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
     _check(load().ftr_texture(ctx, arr, len(views), float(depth_tol), ctypes.byref(t)), ctx)
+
+
+def ftr_extract_mesh_async(ctx):
+    _check(load().ftr_extract_mesh_async(ctx), ctx)
+
+
+def ftr_texture_async(ctx, views, depth_tol, weights, uv, rgb, textured, out_capacity):
+    arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
+    t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
+    _check(load().ftr_texture_async(ctx, arr, len(views), float(depth_tol), ctypes.byref(t), int(out_capacity)), ctx)
+
+
+def ftr_frame_finish(ctx):
+    """Wait for the queued frame; returns the mesh (raises FtrError on FTR_ECAPACITY too)."""
+    m = ftr_mesh()
+    _check(load().ftr_frame_finish(ctx, ctypes.byref(m)), ctx)
+    return m
+
+
+def ftr_mesh_capacity(ctx):
+    return int(load().ftr_mesh_capacity(ctx))
 
 
 def ftr_stats(ctx):

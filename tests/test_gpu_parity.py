@@ -184,3 +184,66 @@ def test_texture_matches_oracle_on_the_same_mesh(ftr):
     assert np.array_equal(tex["textured"], ref["textured"])
     assert np.max(np.abs(tex["rgb"].astype(int) - ref["rgb"].astype(int))) <= 1
     ctx.close()
+
+
+def test_async_frame_equals_sync_frame(ftr):
+    """Queued frame (extract/texture async, one wait) = the waiting calls."""
+    import torch
+    name = "human96"
+    c = G.CASES[name]
+    P, N, W, views = G.case_inputs(name)
+    tol = float(np.float32(0.03))
+    ctx, _ = _run(ftr, name)
+    m_sync = ctx.mesh_numpy()
+    t_sync = ctx.texture_numpy(views, tol, len(m_sync["vertices"]))
+    dviews = []
+    for v in views:
+        d = dict(v)
+        for key in ("depth", "conf", "rgb"):
+            d[key] = torch.from_numpy(v[key]).cuda()
+        dviews.append(d)
+    cap = ftr.ftr_mesh_capacity(ctx.h)
+    K = len(views)
+    w = torch.zeros((cap, K), dtype=torch.float32, device="cuda")
+    uv = torch.zeros((cap, K, 2), dtype=torch.float32, device="cuda")
+    rgb = torch.zeros((cap, 3), dtype=torch.uint8, device="cuda")
+    tx = torch.zeros((cap,), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        ctx.reset()
+        ctx.splat(P, N, W)
+        ctx.solve(want_level=False)
+        ftr.ftr_extract_mesh_async(ctx.h)
+        ftr.ftr_texture_async(ctx.h, dviews, tol, w, uv, rgb, tx, cap)
+        m = ftr.ftr_frame_finish(ctx.h)
+        nv = m.n_vertices
+        assert nv == len(m_sync["vertices"]) and m.n_tris == len(m_sync["tris"])
+        v = np.zeros((nv, 3), np.float32)
+        t = np.zeros((m.n_tris, 3), np.int32)
+        ftr.ftr_mesh_copy(ctx.h, v, None, t)
+        assert np.array_equal(v, m_sync["vertices"]) and np.array_equal(t, m_sync["tris"])
+        assert np.array_equal(w[:nv].cpu().numpy(), t_sync["weights"])
+        assert np.array_equal(rgb[:nv].cpu().numpy(), t_sync["rgb"])
+        assert np.array_equal(tx[:nv].cpu().numpy(), t_sync["textured"])
+    ctx.close()
+
+
+def test_async_mesh_grows_past_its_first_capacity(ftr):
+    """A field with far more surface than the first buffers: finish grows and redoes the mesh."""
+    grid = (64, 64, 64)
+    box = (0.0, 0.0, 0.0, 1.0, 1.0, 1.0)
+    A = np.random.default_rng(8).standard_normal((64, 64, 64)).astype(np.float32)
+    ref_ctx = ftr.Context(grid, box)
+    ref_ctx.set_indicator(A, 0.0)
+    ref = ref_ctx.mesh_numpy()
+    ref_ctx.close()
+    ctx = ftr.Context(grid, box)
+    ctx.set_indicator(A, 0.0)
+    ftr.ftr_extract_mesh_async(ctx.h)
+    assert ftr.ftr_mesh_capacity(ctx.h) < len(ref["vertices"])
+    m = ftr.ftr_frame_finish(ctx.h)
+    assert m.n_vertices == len(ref["vertices"]) and m.n_tris == len(ref["tris"])
+    v = np.zeros((m.n_vertices, 3), np.float32)
+    t = np.zeros((m.n_tris, 3), np.int32)
+    ftr.ftr_mesh_copy(ctx.h, v, None, t)
+    assert np.array_equal(v, ref["vertices"]) and np.array_equal(t, ref["tris"])
+    ctx.close()
