@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=SEED)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (quick runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi clocks")
     return ap.parse_args()
 
 
@@ -321,6 +322,17 @@ def run_ours(args, rank, world, local_rank):
     def finish():
         return ftr.ftr_frame_finish(ctx.h)
 
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    # the sampler starts before the warm-up: its start-up (driver queries) must
+    # not fall inside the timed steps
+    clocks = ClockSampler(uuid)
+    if not args.no_clocks:
+        clocks.start()
+        time.sleep(1.0)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             step()
@@ -331,18 +343,11 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
 
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        uuid = None
-    clocks = ClockSampler(uuid)
     ctx.profile_enable(True)
     l0 = ctx.launch_count()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
     gc.disable()          # no collector pauses inside the timed steps
     with torch.cuda.stream(stream):
         for i in range(args.steps):
@@ -354,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     gc.enable()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop() if not args.no_clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
     launches = ctx.launch_count() - l0
     prof = ctx.profile_read()
     ctx.profile_enable(False)
