@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restri
     }
 }
 
-constexpr int kAccThreads = 256;
+constexpr int kAccThreads = 512;
 
 // round(v * 2^40) as int64 without a 64-bit conversion (those run on the slow
 // double-precision pipe): with x = v 2^9, hi = trunc(x) and r = x - hi (exact:
@@ -473,7 +473,7 @@ cudaError_t launch_splat(ftr_ctx* c) {
     prof_begin(c, ST_SPLAT_ACC);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const int grid = (sms > 0 ? sms : 152) * 8;
+    const int grid = (sms > 0 ? sms : 152) * 4;
     k_splat_accum<<<grid, kAccThreads, 0, c->stream>>>(c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
                                                        c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool);
     c->launches++;
