@@ -180,6 +180,17 @@ int ftr_extract_mesh_async(ftr_ctx* ctx);
 int ftr_texture_async(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out,
                       int64_t out_capacity);
 int ftr_frame_finish(ftr_ctx* ctx, ftr_mesh* out);
+/*
+ * ftr_solve + ftr_extract_mesh_async + ftr_texture_async (k = 0: no texture)
+ * as one CUDA graph replay on the context stream, for the points added since
+ * ftr_reset; complete it with ftr_frame_finish.  The graph is captured on the
+ * first call and again whenever the views, depth_tol, the outputs, the output
+ * capacity or a context buffer changed (a buffer grows when a frame has more
+ * points or a larger mesh than any before).  Same results as the separate
+ * calls; does not return L (see ftr_frame_info / ftr_solve).
+ */
+int ftr_frame_launch(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out,
+                     int64_t out_capacity);
 /* Vertex capacity of the context's mesh buffers (0 before the first mesh). */
 int64_t ftr_mesh_capacity(const ftr_ctx* ctx);
 

@@ -121,6 +121,7 @@ cudaError_t ensure_stage(ftr_ctx* c, void** buf, size_t* cap, size_t bytes) {
 
 cudaError_t grow_points(ftr_ctx* c, int64_t need) {
     if (need <= c->pts.cap) return cudaSuccess;
+    c->graph_valid = false;
     int64_t cap = c->pts.cap ? c->pts.cap : 1 << 16;
     while (cap < need) cap *= 2;
     int4* b;
@@ -147,6 +148,7 @@ cudaError_t grow_points(ftr_ctx* c, int64_t need) {
 
 cudaError_t grow_entries(ftr_ctx* c, int64_t need) {
     if (need <= c->cap_entries) return cudaSuccess;
+    c->graph_valid = false;
     int64_t cap = c->cap_entries ? c->cap_entries : 1 << 18;
     while (cap < need) cap *= 2;
     cudaStreamSynchronize(c->stream);
@@ -161,6 +163,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->pts.frac);
     dfree(c->pts.nrm);
     dfree(c->d_dropped);
+    dfree(c->d_npts);
     dfree(c->d_wild);
     if (c->d_stage) cudaFree(c->d_stage);
     dfree(c->d_brick_cnt);
@@ -193,6 +196,7 @@ void free_all(ftr_ctx* c) {
         if (c->ev_start[s]) cudaEventDestroy(c->ev_start[s]);
         if (c->ev_stop[s]) cudaEventDestroy(c->ev_stop[s]);
     }
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -271,6 +275,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         return FTR_ENOMEM;                                  \
     }
     ALLOC(c->d_dropped, 1);
+    ALLOC(c->d_npts, 1);
     ALLOC(c->d_wild, 1);
     ALLOC(c->d_brick_cnt, c->n_bricks);
     ALLOC(c->d_brick_off, c->n_bricks + 1);
@@ -319,6 +324,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
     cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
+    cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
     double zero2[2] = {0.0, 0.0};
     float zerof[2] = {0.f, 0.f};
     cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
@@ -349,6 +355,7 @@ int ftr_reset(ftr_ctx* c) {
     c->n_verts = c->n_tris = 0;
     cudaError_t e = cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_reset");
     return FTR_OK;
 }
@@ -449,6 +456,7 @@ namespace {
 // Grow the mesh buffers to hold at least (na, nv, nt) with 50 % headroom.
 cudaError_t grow_mesh(ftr_ctx* c, int64_t na, int64_t nv, int64_t nt) {
     cudaError_t e = cudaSuccess;
+    if (na > c->cap_mc_nodes || nv > c->cap_verts || nt > c->cap_tris) c->graph_valid = false;
     if (na > c->cap_mc_nodes) {
         cudaStreamSynchronize(c->stream);
         dfree(c->d_mc_nodes);
@@ -620,6 +628,126 @@ int ftr_texture(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_t
     return FTR_OK;
 }
 
+namespace {
+
+// Device-only view set for the queued paths (images must already be on the device).
+int device_viewset(ftr_ctx* c, const ftr_view* views, int k, ViewSet& vs, const char* who) {
+    memset(&vs, 0, sizeof(vs));
+    vs.k = k;
+    for (int i = 0; i < k; ++i) {
+        const ftr_view& v = views[i];
+        if (v.w <= 0 || v.h <= 0 || v.rgb_w <= 0 || v.rgb_h <= 0 || !is_device_ptr(v.depth) ||
+            !is_device_ptr(v.conf) || !is_device_ptr(v.rgb))
+            return set_err(c, FTR_EINVAL, "%s: view %d needs device images", who, i);
+        ViewDev& d = vs.v[i];
+        d.w = v.w;
+        d.h = v.h;
+        d.rgb_w = v.rgb_w;
+        d.rgb_h = v.rgb_h;
+        for (int j = 0; j < 9; ++j) {
+            d.K[j] = d.Kf[j] = v.K[j];
+            d.Krgb[j] = d.Krgbf[j] = v.K_rgb[j];
+        }
+        for (int j = 0; j < 12; ++j) {
+            d.RT[j] = d.RTf[j] = v.world_to_cam[j];
+            d.RTrgb[j] = d.RTrgbf[j] = v.world_to_rgb[j];
+        }
+        d.depth = v.depth;
+        d.conf = v.conf;
+        d.rgb = v.rgb;
+    }
+    return FTR_OK;
+}
+
+// Enqueue solve + marching cubes + texture exactly as the separate calls do.
+cudaError_t enqueue_frame(ftr_ctx* c, const ViewSet& vs, float tol, const ftr_tex& out, int64_t out_capacity) {
+    cudaError_t e;
+    if ((e = launch_splat(c)) != cudaSuccess) return e;
+    if ((e = launch_fx(c)) != cudaSuccess) return e;
+    if ((e = launch_fy(c)) != cudaSuccess) return e;
+    if ((e = launch_fz(c)) != cudaSuccess) return e;
+    if ((e = launch_iy(c)) != cudaSuccess) return e;
+    if ((e = launch_ix(c)) != cudaSuccess) return e;
+    if ((e = launch_level(c)) != cudaSuccess) return e;
+    if ((e = launch_mc_count(c)) != cudaSuccess) return e;
+    if ((e = launch_mc_emit(c)) != cudaSuccess) return e;
+    if (vs.k > 0) {
+        const int64_t limit = out_capacity < c->cap_verts ? out_capacity : c->cap_verts;
+        e = launch_texture_bounded(c, vs, tol, limit, c->d_mc_off + 3 * (c->mc_blocks + 1) + 1, out.weights, out.uv,
+                                   out.rgb, out.textured);
+    }
+    return e;
+}
+
+}  // namespace
+
+int ftr_frame_launch(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_tex* out, int64_t out_capacity) {
+    if (!c || !out) return FTR_EINVAL;
+    if (c->v_external) return set_err(c, FTR_ESTATE, "ftr_frame_launch: works on splatted points only");
+    if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_frame_launch: finish the previous frame first");
+    if (k < 0 || k > kMaxViews || (k > 0 && !views)) return set_err(c, FTR_EINVAL, "ftr_frame_launch: 0 <= k <= 8");
+    if (!(depth_tol >= 0.f) || out_capacity < 0) return set_err(c, FTR_EINVAL, "ftr_frame_launch: bad argument");
+    ViewSet vs;
+    int st = device_viewset(c, views, k, vs, "ftr_frame_launch");
+    if (st != FTR_OK) return st;
+    const void* outs[4] = {out->weights, out->uv, out->rgb, out->textured};
+    for (int i = 0; i < 4; ++i)
+        if (outs[i] && !is_device_ptr(outs[i]))
+            return set_err(c, FTR_EINVAL, "ftr_frame_launch: outputs must be device memory");
+    cudaError_t e;
+    // every buffer the graph captures is sized here, outside the capture
+    if ((e = grow_entries(c, 8 * c->n_pts + 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
+    if (c->cap_verts == 0) {
+        const int64_t guess = c->M / 256 + 4096;
+        if ((e = grow_mesh(c, guess, guess, 2 * guess)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
+        c->graph_valid = false;
+    }
+    const bool same = c->graph_valid && c->graph_tol == depth_tol && c->graph_cap == out_capacity &&
+                      memcmp(&c->graph_vs, &vs, sizeof(vs)) == 0 &&
+                      memcmp(c->graph_outs, outs, sizeof(outs)) == 0;
+    if (!same) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        const bool prof = c->prof;
+        c->prof = false;                 // no event records inside the capture
+        const int64_t l0 = c->launches;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_frame(c, vs, depth_tol, *out, out_capacity);
+            e = cudaStreamEndCapture(c->stream, &graph);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        c->prof = prof;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch: graph capture");
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
+        c->graph_valid = true;
+        c->graph_vs = vs;
+        c->graph_tol = depth_tol;
+        c->graph_cap = out_capacity;
+        memcpy(c->graph_outs, outs, sizeof(outs));
+    }
+    if ((e = cudaGraphLaunch(c->graph_exec, c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
+    c->launches += c->graph_launches;
+    c->solved = true;
+    c->meshed = false;
+    c->mesh_pending = true;
+    c->tex_pending = k > 0;
+    c->tex_vs = vs;
+    c->tex_tol = depth_tol;
+    c->tex_capacity = out_capacity;
+    c->tex_w = out->weights;
+    c->tex_uv = out->uv;
+    c->tex_rgb = out->rgb;
+    c->tex_flag = out->textured;
+    return FTR_OK;
+}
+
 int ftr_extract_mesh_async(ftr_ctx* c) {
     if (!c) return FTR_EINVAL;
     if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_extract_mesh_async: nothing solved");
@@ -786,6 +914,7 @@ int ftr_set_field_V(ftr_ctx* c, const float* V) {
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_set_field_V");
     c->n_pts = 0;
+    cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
     c->v_external = true;
     return FTR_OK;
 }

@@ -90,6 +90,7 @@ struct ftr_ctx {
     // points of the current frame
     ftr::PointStore pts;
     int64_t n_pts = 0;
+    int64_t* d_npts = nullptr;         // the same count on the device (written by the ingest)
     int64_t points_in = 0;
     unsigned long long* d_dropped = nullptr;
     int* d_wild = nullptr;     // set when some accepted weight lies outside [0, 1]
@@ -152,6 +153,15 @@ struct ftr_ctx {
     // texture staging (host views / outputs)
     void* d_tex_stage = nullptr;
     size_t tex_stage_cap = 0;
+
+    // whole-frame CUDA graph (ftr_frame_launch)
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;       // kernels per replay
+    bool graph_valid = false;
+    ftr::ViewSet graph_vs{};
+    float graph_tol = 0.f;
+    int64_t graph_cap = -1;
+    void* graph_outs[4] = {nullptr, nullptr, nullptr, nullptr};
 
     // profiling
     bool prof = false;

@@ -31,7 +31,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // Per-CTA partial sums; the last CTA to finish (ticket counter) sums the
 // partials in block order and writes L (fixed order: bit-reproducible).
 __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int4* __restrict__ pbase,
-                                                            const float4* __restrict__ pfrac, int64_t n,
+                                                            const float4* __restrict__ pfrac,
+                                                            const int64_t* __restrict__ npts,
                                                             const float* __restrict__ A, double* part,
                                                             unsigned* ticket, double* level, float* levelf) {
     __shared__ double sh[kThreads / 32];
@@ -39,6 +40,7 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
     const int nx = g.n[0];
     const int64_t nxy = (int64_t)nx * g.n[1];
     double sum = 0.0, cnt = 0.0;
+    const int64_t n = *npts;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const int4 b = pbase[i];
         if (!(b.w & 1)) continue;
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
 }  // namespace
 
 cudaError_t launch_level(ftr_ctx* c) {
-    k_level_partial<<<c->level_blocks, kThreads, 0, c->stream>>>(c->g, c->pts.base, c->pts.frac, c->n_pts, c->d_A,
+    k_level_partial<<<c->level_blocks, kThreads, 0, c->stream>>>(c->g, c->pts.base, c->pts.frac, c->d_npts, c->d_A,
                                                                  c->d_level_part, c->d_ticket, c->d_level,
                                                                  c->d_levelf);
     c->launches++;

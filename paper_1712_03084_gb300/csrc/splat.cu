@@ -44,8 +44,10 @@ __device__ __forceinline__ double node_t(double x, double bmin, double h, double
 
 __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
-                         float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights) {
+                         float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
+                         int64_t* npts_dev) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *npts_dev = base + n;   // points stored so far: later kernels read the count here
     if (i >= n) return;
     bool ok = true;
     int fl[3] = {0, 0, 0};
@@ -91,27 +93,33 @@ __device__ __forceinline__ bool stencil_bricks(const int4 b, int mode, int lo[3]
     return true;
 }
 
-__global__ void k_brick_count(const int4* __restrict__ pbase, int64_t n, GridDev g, int* cnt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int lo[3], hi[3];
-    if (!stencil_bricks(pbase[i], g.mode, lo, hi)) return;
-    for (int bz = lo[2]; bz <= hi[2]; ++bz)
-        for (int by = lo[1]; by <= hi[1]; ++by)
-            for (int bx = lo[0]; bx <= hi[0]; ++bx) atomicAdd(&cnt[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
+// Grid-stride over the stored points; the count is read on the device, so the
+// launch does not depend on it.
+__global__ void k_brick_count(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
+                              int* cnt) {
+    const int64_t n = *npts;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo[3], hi[3];
+        if (!stencil_bricks(pbase[i], g.mode, lo, hi)) continue;
+        for (int bz = lo[2]; bz <= hi[2]; ++bz)
+            for (int by = lo[1]; by <= hi[1]; ++by)
+                for (int bx = lo[0]; bx <= hi[0]; ++bx) atomicAdd(&cnt[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
+    }
 }
 
-__global__ void k_brick_fill(const int4* __restrict__ pbase, int64_t n, GridDev g, int* cursor, int* entries) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int lo[3], hi[3];
-    if (!stencil_bricks(pbase[i], g.mode, lo, hi)) return;
-    for (int bz = lo[2]; bz <= hi[2]; ++bz)
-        for (int by = lo[1]; by <= hi[1]; ++by)
-            for (int bx = lo[0]; bx <= hi[0]; ++bx) {
-                int pos = atomicAdd(&cursor[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
-                entries[pos] = (int)i;
-            }
+__global__ void k_brick_fill(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
+                             int* cursor, int* entries) {
+    const int64_t n = *npts;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo[3], hi[3];
+        if (!stencil_bricks(pbase[i], g.mode, lo, hi)) continue;
+        for (int bz = lo[2]; bz <= hi[2]; ++bz)
+            for (int by = lo[1]; by <= hi[1]; ++by)
+                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                    int pos = atomicAdd(&cursor[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
+                    entries[pos] = (int)i;
+                }
+    }
 }
 
 // Exclusive scan of the brick counts in three coalesced launches over tiles
@@ -254,31 +262,24 @@ __device__ __forceinline__ float fix_to_float(long long v) {
 constexpr int kStage = 128;       // point records staged in shared memory per batch
 constexpr int kFastEntries = 2047; // the split accumulators stay exact up to this many points per brick
 
-// Fixed-point contribution round(v * 2^40) = hi 2^20 + lo with lo in [0, 2^20)
-// (float ops only: x = v 2^20, trunc and the exact remainder as in fix40).
-__device__ __forceinline__ void fix40_split(float v, int& hi, unsigned& lo) {
-    const float x = v * 1048576.0f;
-    const float hf = truncf(x);
-    int h = (int)hf;
-    int l = __float2int_rn((x - hf) * 1048576.0f);   // in [-2^20, 2^20]
-    if (l < 0) {
-        l += 1 << 20;
-        h -= 1;
-    } else if (l >= (1 << 20)) {
-        l -= 1 << 20;
-        h += 1;
-    }
-    hi = h;
-    lo = (unsigned)l;
+// Fixed-point contribution round(v * 2^40) = hi 2^20 + lo with two float to
+// int conversions: hi = round(v 2^20); r = v - hi 2^-20 is exact (Sterbenz,
+// or r = v when hi = 0) with |r| <= 2^-21, and lo = round(r 2^40) in
+// [-2^19, 2^19].  Ties go to even as in a direct conversion (hi 2^20 is even).
+__device__ __forceinline__ void fix40_split(float v, int& hi, int& lo) {
+    const float hf = rintf(v * 1048576.0f);
+    hi = (int)hf;
+    lo = __float2int_rn(fmaf(hf, -9.5367431640625e-07f, v) * 1099511627776.0f);
 }
 
 // One CTA per touched brick (persistent over the list).  64 lanes per point
 // evaluate the stencil nodes that fall inside the brick and add the
 // fixed-point contributions to shared-memory accumulators.  Integer sums are
 // exact and order-independent, so V is bit-reproducible.  Fast path: 32-bit
-// atomics on (hi, lo) halves, exact while a voxel receives fewer than 2^11
+// atomics on the (hi, lo) parts, exact while a voxel receives fewer than 2^11
 // contributions of magnitude <= 1 (at most kFastEntries points per brick,
-// weights in [0, 1]); otherwise the brick takes the 64-bit atomic path.
+// weights in [0, 1]: |sum hi| < 2^31, |sum lo| < 2^30); otherwise the brick
+// takes the 64-bit atomic path.
 __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const int* __restrict__ active,
                                                              const int* __restrict__ meta,
                                                              const int* __restrict__ off,
@@ -337,11 +338,10 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                     if (fast) {
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            int hi;
-                            unsigned lo;
+                            int hi, lo;
                             fix40_split(val[c], hi, lo);
                             atomicAdd(reinterpret_cast<int*>(&acc[c][li]), hi);
-                            atomicAdd(&acc[4 + c][li], lo);
+                            atomicAdd(reinterpret_cast<int*>(&acc[4 + c][li]), lo);
                         }
                     } else {
 #pragma unroll
@@ -361,11 +361,10 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                     if (fast) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            int hi;
-                            unsigned lo;
+                            int hi, lo;
                             fix40_split(val[c], hi, lo);
                             atomicAdd(reinterpret_cast<int*>(&acc[c][li]), hi);
-                            atomicAdd(&acc[4 + c][li], lo);
+                            atomicAdd(reinterpret_cast<int*>(&acc[4 + c][li]), lo);
                         }
                         atomicAdd(reinterpret_cast<int*>(&acc[3][li]), 1 << 20);   // count: 2^40 = 2^20 * 2^20
                     } else {
@@ -383,7 +382,7 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
             long long u[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                u[c] = fast ? (long long)(int)acc[c][li] * (1ll << 20) + (long long)acc[4 + c][li]
+                u[c] = fast ? (long long)(int)acc[c][li] * (1ll << 20) + (long long)(int)acc[4 + c][li]
                             : (long long)acc64[c * kBrickVox + li];
             if (u[3] > 0) {
                 // exact integer sums, one float32 quotient per voxel
@@ -440,21 +439,21 @@ cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const 
     if (n == 0) return cudaSuccess;
     // small CTAs spread the few float64 operations per point over every SM
     k_ingest<<<blocks_for(n, 32), 32, 0, c->stream>>>(pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
-                                                       c->pts.nrm, c->d_dropped, c->d_wild);
+                                                       c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts);
     c->launches++;
     return cudaGetLastError();
 }
 
 cudaError_t launch_splat(ftr_ctx* c) {
     cudaError_t e;
-    const int64_t n = c->n_pts;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (sms <= 0) sms = 152;
     prof_begin(c, ST_SPLAT_BIN);
     if ((e = cudaMemsetAsync(c->d_brick_cnt, 0, sizeof(int) * c->n_bricks, c->stream)) != cudaSuccess) return e;
-    if (n > 0) {
-        k_brick_count<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->pts.base, n, c->g, c->d_brick_cnt);
-        c->launches++;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    k_brick_count<<<sms * 2, 256, 0, c->stream>>>(c->pts.base, c->d_npts, c->g, c->d_brick_cnt);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ntiles = (c->n_bricks + kTile - 1) / kTile;
     k_brick_tile_sums<<<ntiles, kScanT, 0, c->stream>>>(c->d_brick_cnt, c->n_bricks, c->d_tile);
     k_brick_tile_scan<<<1, kScanT, 0, c->stream>>>(c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta);
@@ -463,17 +462,12 @@ cudaError_t launch_splat(ftr_ctx* c) {
                                                         c->d_brick_slot, c->d_active, c->d_meta);
     c->launches += 3;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n > 0) {
-        k_brick_fill<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->pts.base, n, c->g, c->d_brick_cursor,
-                                                               c->d_entries);
-        c->launches++;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    k_brick_fill<<<sms * 2, 256, 0, c->stream>>>(c->pts.base, c->d_npts, c->g, c->d_brick_cursor, c->d_entries);
+    c->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     prof_end(c, ST_SPLAT_BIN);
     prof_begin(c, ST_SPLAT_ACC);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const int grid = (sms > 0 ? sms : 152) * 4;
+    const int grid = sms * 4;
     k_splat_accum<<<grid, kAccThreads, 0, c->stream>>>(c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
                                                        c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool);
     c->launches++;

@@ -70,6 +70,8 @@ _SIGNATURES = [
     ("ftr_texture_async", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
                                          ctypes.POINTER(ftr_tex), ctypes.c_int64]),
     ("ftr_frame_finish", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_mesh)]),
+    ("ftr_frame_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
+                                        ctypes.POINTER(ftr_tex), ctypes.c_int64]),
     ("ftr_mesh_capacity", ctypes.c_int64, [ctypes.c_void_p]),
     ("ftr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
@@ -219,6 +221,12 @@ def ftr_texture_async(ctx, views, depth_tol, weights, uv, rgb, textured, out_cap
     arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
     t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
     _check(load().ftr_texture_async(ctx, arr, len(views), float(depth_tol), ctypes.byref(t), int(out_capacity)), ctx)
+
+
+def ftr_frame_launch(ctx, views, depth_tol, weights=None, uv=None, rgb=None, textured=None, out_capacity=0):
+    arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
+    t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
+    _check(load().ftr_frame_launch(ctx, arr, len(views), float(depth_tol), ctypes.byref(t), int(out_capacity)), ctx)
 
 
 def ftr_frame_finish(ctx):

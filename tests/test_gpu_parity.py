@@ -247,3 +247,46 @@ def test_async_mesh_grows_past_its_first_capacity(ftr):
     ftr.ftr_mesh_copy(ctx.h, v, None, t)
     assert np.array_equal(v, ref["vertices"]) and np.array_equal(t, ref["tris"])
     ctx.close()
+
+
+def test_graph_frame_equals_separate_calls(ftr):
+    """ftr_frame_launch (one CUDA graph per frame) = solve + async extract + async texture,
+    also when the point count changes between replays."""
+    import torch
+    name = "human96"
+    c = G.CASES[name]
+    P, N, W, views = G.case_inputs(name)
+    tol = float(np.float32(0.03))
+    dviews = []
+    for v in views:
+        d = dict(v)
+        for key in ("depth", "conf", "rgb"):
+            d[key] = torch.from_numpy(v[key]).cuda()
+        dviews.append(d)
+    K = len(views)
+    cap = 200000
+    outs = [torch.zeros((cap, K), dtype=torch.float32, device="cuda"),
+            torch.zeros((cap, K, 2), dtype=torch.float32, device="cuda"),
+            torch.zeros((cap, 3), dtype=torch.uint8, device="cuda"),
+            torch.zeros((cap,), dtype=torch.uint8, device="cuda")]
+    g = ftr.Context(c["grid"], c["bbox"])
+    for sub in (len(P), len(P) // 2, len(P)):
+        ref = ftr.Context(c["grid"], c["bbox"])
+        ref.splat(P[:sub].copy(), N[:sub].copy(), W[:sub].copy())
+        L = ref.solve()
+        m_ref = ref.mesh_numpy()
+        t_ref = ref.texture_numpy(views, tol, len(m_ref["vertices"]))
+        ref.close()
+        g.reset()
+        g.splat(P[:sub].copy(), N[:sub].copy(), W[:sub].copy())
+        ftr.ftr_frame_launch(g.h, dviews, tol, *outs, out_capacity=cap)
+        m = ftr.ftr_frame_finish(g.h)
+        nv = m.n_vertices
+        assert nv == len(m_ref["vertices"]) and m.n_tris == len(m_ref["tris"])
+        v = np.zeros((nv, 3), np.float32)
+        t = np.zeros((m.n_tris, 3), np.int32)
+        ftr.ftr_mesh_copy(g.h, v, None, t)
+        assert np.array_equal(v, m_ref["vertices"]) and np.array_equal(t, m_ref["tris"])
+        assert np.array_equal(outs[0][:nv].cpu().numpy(), t_ref["weights"])
+        assert np.array_equal(outs[2][:nv].cpu().numpy(), t_ref["rgb"])
+    g.close()
