@@ -244,8 +244,13 @@ def _ray_ellipsoid(o, d, el):
     return np.where((disc >= 0) & (t > 1e-6), t, np.inf)
 
 
-def raycast(prims, origin, dirs):
-    """Nearest hit distance along unit rays from one origin (inf on a miss)."""
+def raycast(prims, origin, dirs, device=None):
+    """Nearest hit distance along unit rays from one origin (inf on a miss).
+
+    ``device`` (e.g. "cuda") evaluates the same intersections with torch."""
+    if device is not None:
+        from .torch_raycast import raycast_torch
+        return raycast_torch(prims, origin, dirs, device)
     o = np.asarray(origin, dtype=np.float64)
     best = np.full(len(dirs), np.inf)
     for p in prims:
@@ -259,10 +264,10 @@ def raycast(prims, origin, dirs):
 
 # --------------------------------------------------------------------------- depth views
 
-def depth_view(cam, prims, rng, noise_coef=0.0012):
+def depth_view(cam, prims, rng, noise_coef=0.0012, device=None):
     """Noisy depth map (0 = background) of the body seen by ``cam``."""
     dw, cosax = pixel_rays(cam)
-    t = raycast(prims, cam.pos, dw.reshape(-1, 3)).reshape(cam.h, cam.w)
+    t = raycast(prims, cam.pos, dw.reshape(-1, 3), device).reshape(cam.h, cam.w)
     fg = np.isfinite(t)
     z = np.where(fg, t * cosax, 0.0)
     sig = noise_coef * z * z
@@ -345,13 +350,15 @@ def procedural_colour(X, params):
     return 128.0 + 100.0 * np.sin(arg)
 
 
-def rgb_view(rgb_cam, prims, params, chunk=1 << 19):
+def rgb_view(rgb_cam, prims, params, chunk=1 << 19, device=None):
     dw, _ = pixel_rays(rgb_cam)
     d = dw.reshape(-1, 3)
     img = np.zeros((len(d), 3))
+    if device is not None:
+        chunk = len(d)
     for s in range(0, len(d), chunk):
         dd = d[s:s + chunk]
-        t = raycast(prims, rgb_cam.pos, dd)
+        t = raycast(prims, rgb_cam.pos, dd, device)
         hit = np.isfinite(t)
         X = rgb_cam.pos + t[hit, None] * dd[hit]
         col = np.zeros((len(dd), 3))
@@ -375,7 +382,7 @@ def frame_config(name):
 
 def human_frame(seed=0, K=4, ring=2.5, height=1.2, depth_wh=(512, 424), fxy=365.0,
                 rgb_wh=(1920, 1080), rgb_f=1060.0, angle_range=40.0, with_rgb=True,
-                noise_coef=0.0012, pixel_stride=1):
+                noise_coef=0.0012, pixel_stride=1, device=None, yaw_deg=None):
     """One synthetic multi-camera frame of the capsule human.
 
     Returns dict(points [P,3] f32, normals [P,3] f32, weights [P] f32,
@@ -383,14 +390,14 @@ def human_frame(seed=0, K=4, ring=2.5, height=1.2, depth_wh=(512, 424), fxy=365.
     K_rgb, world_to_rgb)], prims, cams).
     """
     rng = np.random.default_rng(seed)
-    prims = human_primitives(seed, angle_range)
+    prims = human_primitives(seed, angle_range, yaw_deg)
     cams = ring_cameras(K, ring, height, (0.0, 0.95, 0.0), depth_wh[0], depth_wh[1], fxy, fxy,
                         phase_deg=float(rng.uniform(0, 360.0 / K)))
     params = texture_params(seed)
     pts, nrms, ws, per_cam, views = [], [], [], [], []
     start = 0
     for cam in cams:
-        z = depth_view(cam, prims, rng, noise_coef)
+        z = depth_view(cam, prims, rng, noise_coef, device)
         xc, xw = backproject(cam, z)
         nc, valid = organised_normals(xc, z, noise_coef)
         if pixel_stride > 1:
@@ -412,7 +419,7 @@ def human_frame(seed=0, K=4, ring=2.5, height=1.2, depth_wh=(512, 424), fxy=365.
                 "K": cam.K.astype(np.float32), "world_to_cam": cam.world_to_cam.astype(np.float32)}
         if with_rgb:
             rc = rgb_companion(cam, rgb_wh[0], rgb_wh[1], rgb_f, rgb_f)
-            view["rgb"] = rgb_view(rc, prims, params)
+            view["rgb"] = rgb_view(rc, prims, params, device=device)
             view["K_rgb"] = rc.K.astype(np.float32)
             view["world_to_rgb"] = rc.world_to_cam.astype(np.float32)
         views.append(view)

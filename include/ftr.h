@@ -204,6 +204,10 @@ int ftr_stats(const ftr_ctx* ctx, int64_t* points_in, int64_t* points_dropped);
  * the last mesh.  Writes min(n, 8) values. */
 int ftr_frame_info(ftr_ctx* ctx, int64_t* info, int n);
 
+/* Device memory the context holds right now, in bytes (grids, FFT workspaces,
+ * brick tables, point store, mesh buffers and staging). */
+int64_t ftr_device_bytes(const ftr_ctx* ctx);
+
 /* Message of the last error on this context (never NULL). */
 const char* ftr_last_error(const ftr_ctx* ctx);
 

@@ -863,6 +863,24 @@ int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
     return FTR_OK;
 }
 
+int64_t ftr_device_bytes(const ftr_ctx* c) {
+    if (!c) return 0;
+    const int64_t nb = c->n_bricks;
+    int64_t b = 0;
+    b += c->pts.cap * (int64_t)(sizeof(int4) + 2 * sizeof(float4));
+    b += (int64_t)c->stage_cap + (int64_t)c->tex_stage_cap;
+    b += nb * (int64_t)sizeof(int) * 5 + (nb / 2048 + 1) * (int64_t)sizeof(int2) + 64;
+    b += c->cap_entries * (int64_t)sizeof(int);
+    b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
+    b += 5 * c->Mh * (int64_t)sizeof(float2) + c->M * (int64_t)sizeof(float);
+    b += (int64_t)(c->g.n[0] + c->g.n[1] + c->g.n[2]) * (int64_t)sizeof(float2);
+    b += (2 * c->level_blocks + 8) * (int64_t)sizeof(double);
+    b += (6 * (int64_t)c->mc_blocks + 16) * (int64_t)sizeof(int);
+    b += c->cap_mc_nodes * (int64_t)sizeof(int4) + c->cap_verts * 6 * (int64_t)sizeof(float) +
+         c->cap_tris * 3 * (int64_t)sizeof(int32_t);
+    return b;
+}
+
 const char* ftr_last_error(const ftr_ctx* c) {
     if (!c) return "null context";
     return c->err.c_str();

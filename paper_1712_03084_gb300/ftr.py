@@ -76,6 +76,7 @@ _SIGNATURES = [
     ("ftr_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ftr_frame_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("ftr_device_bytes", ctypes.c_int64, [ctypes.c_void_p]),
     ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_field_A", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -253,6 +254,10 @@ def ftr_frame_info(ctx):
     out = np.zeros(8, np.int64)
     _check(load().ftr_frame_info(ctx, out.ctypes.data, 8), ctx)
     return dict(zip(FRAME_INFO_KEYS, (int(v) for v in out)))
+
+
+def ftr_device_bytes(ctx):
+    return int(load().ftr_device_bytes(ctx))
 
 
 def ftr_last_error(ctx):

@@ -1,0 +1,274 @@
+"""Many frames on one GPU: batched frames and a continuously batched serving loop.
+
+Every frame slot owns one reconstruction context (its grids, FFT workspaces,
+brick tables and mesh stay resident in HBM), one CUDA stream, device staging
+buffers for the frame's points and RGB-D views, and device texture outputs.
+A submitted frame is copied in from pinned host memory and queued on the
+slot's stream as per-camera point ingests followed by one CUDA-graph replay
+of the whole reconstruction (``ftr_frame_launch``); frames on different slots
+run concurrently on the device.  Nothing here does reconstruction arithmetic:
+it only moves buffers and orders calls into the C ABI.
+
+* ``run_batch``: B frames of mixed grid sizes, one slot each, all submitted at
+  once; throughput against the same frames one after another.
+* ``Server``: live sessions (each a camera rig with a grid size) are admitted
+  while their device memory fits an HBM budget; frames arrive per session as
+  a Poisson process; a frame is dispatched as soon as its session's slot is
+  free, so frames that arrive while others are on the GPU join the work in
+  flight (continuous batching); per-frame latency = completion - arrival.
+"""
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ftr
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the serving runtime needs a CUDA device")
+    return torch
+
+
+@dataclass
+class FrameInput:
+    """One frame in pinned host memory."""
+    points: object
+    normals: object
+    weights: object
+    per_camera: list
+    views: list          # dicts: depth, conf, rgb (pinned tensors), K, world_to_cam, K_rgb, world_to_rgb
+    n_points: int = 0
+
+    @classmethod
+    def from_frame(cls, fr):
+        torch = _torch()
+
+        def pin(a):
+            return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        views = []
+        for v in fr["views"]:
+            d = {k: v[k] for k in ("K", "world_to_cam", "K_rgb", "world_to_rgb")}
+            d["depth"], d["conf"], d["rgb"] = pin(v["depth"]), pin(v["conf"]), pin(v["rgb"])
+            views.append(d)
+        return cls(pin(fr["points"]), pin(fr["normals"]), pin(fr["weights"]), list(fr["per_camera"]), views,
+                   int(len(fr["points"])))
+
+    def h2d_bytes(self):
+        b = 4 * (self.points.numel() + self.normals.numel() + self.weights.numel())
+        for v in self.views:
+            b += 4 * v["depth"].numel() + 4 * v["conf"].numel() + v["rgb"].numel()
+        return b
+
+
+class Slot:
+    """A resident context with its stream, staging buffers and texture outputs."""
+
+    def __init__(self, grid_n, bbox, template, point_cap, mesh_cap=None, device=0):
+        torch = _torch()
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.grid_n = tuple(grid_n)
+        self.bbox = tuple(bbox)
+        self.stream = torch.cuda.Stream(device=self.dev)
+        self.ctx = ftr.Context(grid_n, bbox, stream=self.stream.cuda_stream)
+        self.point_cap = int(point_cap)
+        z = dict(dtype=torch.float32, device=self.dev)
+        self.P = torch.empty((self.point_cap, 3), **z)
+        self.N = torch.empty((self.point_cap, 3), **z)
+        self.W = torch.empty((self.point_cap,), **z)
+        self.views = []
+        for v in template.views:
+            d = {k: v[k] for k in ("K", "world_to_cam", "K_rgb", "world_to_rgb")}
+            d["depth"] = torch.empty_like(v["depth"], device=self.dev)
+            d["conf"] = torch.empty_like(v["conf"], device=self.dev)
+            d["rgb"] = torch.empty_like(v["rgb"], device=self.dev)
+            self.views.append(d)
+        K = len(self.views)
+        nx, ny, nz = self.grid_n
+        self.cap = int(mesh_cap or max(1 << 16, (nx * ny * nz) // 64))
+        self.out_w = torch.empty((self.cap, K), **z)
+        self.out_uv = torch.empty((self.cap, K, 2), **z)
+        self.out_rgb = torch.empty((self.cap, 3), dtype=torch.uint8, device=self.dev)
+        self.out_tex = torch.empty((self.cap,), dtype=torch.uint8, device=self.dev)
+        self.done = torch.cuda.Event()
+        self.busy = False
+        self.tag = None
+        tol_h = max((bbox[3 + a] - bbox[a]) / grid_n[a] for a in range(3))
+        self.tol = float(np.float32(max(3.0 * tol_h, 0.02)))
+
+    def device_bytes(self):
+        t = self.torch
+        staged = sum(x.numel() * x.element_size() for x in (self.P, self.N, self.W, self.out_w, self.out_uv,
+                                                               self.out_rgb, self.out_tex))
+        for v in self.views:
+            staged += sum(v[k].numel() * v[k].element_size() for k in ("depth", "conf", "rgb"))
+        del t
+        return ftr.ftr_device_bytes(self.ctx.h) + staged
+
+    def submit(self, fin, tag=None):
+        """Queue one frame (copies in, ingests, graph replay); returns immediately."""
+        if fin.n_points > self.point_cap:
+            raise ValueError("frame has more points than the slot holds")
+        torch = self.torch
+        n = fin.n_points
+        with torch.cuda.stream(self.stream):
+            self.P[:n].copy_(fin.points, non_blocking=True)
+            self.N[:n].copy_(fin.normals, non_blocking=True)
+            self.W[:n].copy_(fin.weights, non_blocking=True)
+            for d, v in zip(self.views, fin.views):
+                d["depth"].copy_(v["depth"], non_blocking=True)
+                d["conf"].copy_(v["conf"], non_blocking=True)
+                d["rgb"].copy_(v["rgb"], non_blocking=True)
+            self.ctx.reset()
+            for (s, c) in fin.per_camera:
+                ftr.ftr_splat(self.ctx.h, self.P[s:s + c], self.N[s:s + c], self.W[s:s + c])
+            ftr.ftr_frame_launch(self.ctx.h, self.views, self.tol, self.out_w, self.out_uv, self.out_rgb,
+                                 self.out_tex, self.cap)
+            self.done.record(self.stream)
+        self.busy = True
+        self.tag = tag
+
+    def ready(self):
+        return self.done.query()
+
+    def finish(self):
+        """Complete the frame; returns (n_vertices, n_tris)."""
+        m = ftr.ftr_frame_finish(self.ctx.h)
+        self.busy = False
+        return m.n_vertices, m.n_tris
+
+    def mesh(self):
+        m = ftr.ftr_frame_info(self.ctx.h)
+        v = np.zeros((m["n_vertices"], 3), np.float32)
+        t = np.zeros((m["n_tris"], 3), np.int32)
+        ftr.ftr_mesh_copy(self.ctx.h, v, None, t)
+        return v, t
+
+    def close(self):
+        self.ctx.close()
+
+
+def run_batch(frames, grids, bboxes, sequential=False):
+    """Reconstruct ``frames`` (FrameInput list) on one slot each, all queued at
+    once (or one after another); returns (seconds, [(n_vertices, n_tris)])."""
+    torch = _torch()
+    slots = [Slot(g, b, f, f.n_points) for f, g, b in zip(frames, grids, bboxes)]
+    # warm-up: capture every slot's graph
+    for s, f in zip(slots, frames):
+        s.submit(f)
+    for s in slots:
+        s.finish()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = []
+    if sequential:
+        for s, f in zip(slots, frames):
+            s.submit(f)
+            out.append(s.finish())
+    else:
+        for s, f in zip(slots, frames):
+            s.submit(f)
+        out = [s.finish() for s in slots]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for s in slots:
+        s.close()
+    return dt, out
+
+
+@dataclass
+class Session:
+    """A live capture rig: grid, bbox and a cycle of frames (continuous motion)."""
+    sid: int
+    grid_n: tuple
+    bbox: tuple
+    frames: list
+    rate_hz: float = 30.0
+    slot: object = None
+    queue: list = field(default_factory=list)
+
+
+class Server:
+    """Continuous-batching request loop over resident per-session slots."""
+
+    def __init__(self, hbm_budget_bytes):
+        self.budget = int(hbm_budget_bytes)
+        self.used = 0
+        self.sessions = []
+        self.rejected = []
+
+    def admit(self, sess):
+        """Create the session's slot if its device memory fits the budget."""
+        slot = Slot(sess.grid_n, sess.bbox, sess.frames[0], max(f.n_points for f in sess.frames))
+        need = slot.device_bytes()
+        if self.used + need > self.budget:
+            slot.close()
+            self.rejected.append(sess.sid)
+            return False
+        self.used += need
+        sess.slot = slot
+        self.sessions.append(sess)
+        return True
+
+    def run(self, duration_s, seed=0, saturate=False, keep_meshes=None):
+        """Serve every admitted session for ``duration_s`` seconds of arrivals
+        (Poisson, rate_hz each; ``saturate`` makes every frame available at
+        t = 0).  Returns latency and throughput statistics."""
+        torch = _torch()
+        rng = np.random.default_rng(seed)
+        arrivals = []
+        for s in self.sessions:
+            t = 0.0
+            k = 0
+            while True:
+                t += 0.0 if saturate else rng.exponential(1.0 / s.rate_hz)
+                if (not saturate and t > duration_s) or (saturate and k >= int(duration_s * s.rate_hz)):
+                    break
+                arrivals.append((t, s.sid, k))
+                k += 1
+        arrivals.sort()
+        by_id = {s.sid: s for s in self.sessions}
+        # warm-up: one frame per session (graph capture)
+        for s in self.sessions:
+            s.slot.submit(s.frames[0])
+        for s in self.sessions:
+            s.slot.finish()
+        torch.cuda.synchronize()
+        lat, done_frames, meshes = [], 0, {}
+        nxt = 0
+        pending = len(arrivals)
+        t0 = time.perf_counter()
+        while pending:
+            now = time.perf_counter() - t0
+            while nxt < len(arrivals) and arrivals[nxt][0] <= now:
+                ta, sid, k = arrivals[nxt]
+                by_id[sid].queue.append((ta, k))
+                nxt += 1
+            for s in self.sessions:
+                sl = s.slot
+                if sl.busy and sl.ready():
+                    nv, nt = sl.finish()
+                    ta, k = sl.tag
+                    lat.append(time.perf_counter() - t0 - ta)
+                    done_frames += 1
+                    pending -= 1
+                    if keep_meshes is not None and (s.sid, k) in keep_meshes:
+                        meshes[(s.sid, k)] = sl.mesh()
+                if not sl.busy and s.queue:
+                    ta, k = s.queue.pop(0)
+                    sl.submit(s.frames[k % len(s.frames)], tag=(ta, k))
+        wall = time.perf_counter() - t0
+        lat_ms = np.array(lat) * 1e3
+        return {"frames": done_frames, "seconds": wall, "frames_per_s": done_frames / wall,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_ms": float(lat_ms.mean()), "sessions": len(self.sessions), "rejected": list(self.rejected),
+                "hbm_bytes": self.used, "meshes": meshes}
+
+    def close(self):
+        for s in self.sessions:
+            s.slot.close()
+        self.sessions = []

@@ -1,0 +1,83 @@
+"""Batched frames and the continuous-batching serving loop (GPU).
+
+Each frame's result must be the same alone and in the mix: every slot owns
+its context, the splat is exact integer arithmetic and every kernel is
+deterministic, so meshes are compared bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+from datagen import human_frame
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+BOX = (-1.0, -0.05, -1.0, 1.0, 1.95, 1.0)
+
+
+@pytest.fixture(scope="module")
+def rt():
+    G.require_gpu()
+    from paper_1712_03084_gb300 import serve
+    return serve
+
+
+def _frames(seed, n, K=3):
+    out = []
+    for i in range(n):
+        fr = human_frame(seed=seed + i, K=K, **G.SMALL_VIEWS)
+        out.append(fr)
+    return out
+
+
+def test_batch_matches_sequential_and_alone(rt):
+    grids = [(64, 64, 64), (96, 96, 96), (64, 128, 64), (96, 96, 96)]
+    frs = _frames(50, 4)
+    fins = [rt.FrameInput.from_frame(f) for f in frs]
+    boxes = [BOX] * 4
+    _, par = rt.run_batch(fins, grids, boxes)
+    _, seq = rt.run_batch(fins, grids, boxes, sequential=True)
+    assert par == seq
+    # alone: one slot, one frame
+    s = rt.Slot(grids[1], BOX, fins[1], fins[1].n_points)
+    s.submit(fins[1])
+    assert s.finish() == par[1]
+    s.close()
+
+
+def test_server_mix_equals_alone_and_reports_latency(rt):
+    specs = [((64, 64, 64), 3, 60), ((96, 96, 96), 4, 70), ((64, 64, 64), 3, 80)]
+    sessions = []
+    for sid, (grid, K, seed) in enumerate(specs):
+        fins = [rt.FrameInput.from_frame(f) for f in _frames(seed, 2, K)]
+        sessions.append(rt.Session(sid, grid, BOX, fins, rate_hz=60.0))
+    srv = rt.Server(hbm_budget_bytes=64 << 30)
+    for s in sessions:
+        assert srv.admit(s)
+    keep = {(0, 0), (1, 1), (2, 0)}
+    stats = srv.run(duration_s=0.4, seed=3, keep_meshes=keep)
+    srv.close()
+    assert stats["frames"] > 10 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    for (sid, k), (v, t) in stats["meshes"].items():
+        sess = sessions[sid]
+        alone = rt.Slot(sess.grid_n, BOX, sess.frames[0], max(f.n_points for f in sess.frames))
+        alone.submit(sess.frames[k % len(sess.frames)])
+        alone.finish()
+        va, ta = alone.mesh()
+        alone.close()
+        assert np.array_equal(v, va) and np.array_equal(t, ta)
+    assert len(stats["meshes"]) >= 2
+
+
+def test_admission_respects_the_hbm_budget(rt):
+    fins = [rt.FrameInput.from_frame(f) for f in _frames(90, 1)]
+    probe = rt.Slot((96, 96, 96), BOX, fins[0], fins[0].n_points)
+    one = probe.device_bytes()
+    probe.close()
+    srv = rt.Server(hbm_budget_bytes=int(one * 1.5))
+    a = rt.Session(0, (96, 96, 96), BOX, fins)
+    b = rt.Session(1, (96, 96, 96), BOX, fins)
+    assert srv.admit(a) and not srv.admit(b)
+    assert srv.rejected == [1] and srv.used <= srv.budget
+    srv.close()
