@@ -455,12 +455,12 @@ def run_ours(args, rank, world, local_rank):
 
 def _mixed_frame(seed, grid_choices, rng, device):
     """One frame of the batched/served configurations: 3-6 cameras of 512x424
-    (pixel supersampling x1..x3 spans 50k-400k points), ring 2.0-3.0 m,
+    (pixel supersampling x1..x2.5 spans ~50k-400k points), ring 2.0-3.0 m,
     joint angles +-40 deg, 1920x1080 RGB, grid drawn from grid_choices."""
     from datagen import human_frame
     K = int(rng.integers(3, 7))
     ring = float(rng.uniform(2.0, 3.0))
-    ss = float(rng.choice([1.0, 1.5, 2.0, 3.0]))
+    ss = float(rng.choice([1.0, 1.5, 2.0, 2.5]))
     n = int(rng.choice(grid_choices))
     fr = human_frame(seed=seed, K=K, ring=ring, depth_wh=(int(512 * ss), int(424 * ss)), fxy=365.0 * ss,
                      device=device)
@@ -486,7 +486,7 @@ def run_multi(args, rank, dev):
     out["batched"] = {"frames": 16, "frames_per_s": round(16 / dt_par, 1),
                       "sequential_frames_per_s": round(16 / dt_seq, 1),
                       "points": [int(f.n_points) for f in frames], "grids": [g[0] for g in grids],
-                      "config": "16 frames, grids {128,192,256}^3, 3-6 cameras 512x424 (supersampled x1-x3), "
+                      "config": "16 frames, grids {128,192,256}^3, 3-6 cameras 512x424 (supersampled x1-x2.5), "
                                 "ring 2-3 m, joint angles +-40 deg, 1920x1080 RGB; one resident slot and stream per "
                                 "frame, each frame one CUDA-graph replay; timed host-side incl. input copies"}
     del frames

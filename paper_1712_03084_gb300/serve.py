@@ -232,11 +232,14 @@ class Server:
                 k += 1
         arrivals.sort()
         by_id = {s.sid: s for s in self.sessions}
-        # warm-up: one frame per session (graph capture)
-        for s in self.sessions:
-            s.slot.submit(s.frames[0])
-        for s in self.sessions:
-            s.slot.finish()
+        # warm-up: every frame of every session once, so each slot's buffers
+        # reach their final size (growing them frees memory, which waits for
+        # the whole device) and its graph is captured before arrivals start
+        for j in range(max(len(s.frames) for s in self.sessions)):
+            for s in self.sessions:
+                s.slot.submit(s.frames[j % len(s.frames)])
+            for s in self.sessions:
+                s.slot.finish()
         torch.cuda.synchronize()
         lat, done_frames, meshes = [], 0, {}
         nxt = 0
