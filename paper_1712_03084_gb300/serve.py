@@ -18,6 +18,7 @@ it only moves buffers and orders calls into the C ABI.
   flight (continuous batching); per-frame latency = completion - arrival.
 """
 
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -244,6 +245,7 @@ class Server:
         lat, done_frames, meshes = [], 0, {}
         nxt = 0
         pending = len(arrivals)
+        gc.disable()                  # no collector pauses inside the loop
         t0 = time.perf_counter()
         while pending:
             now = time.perf_counter() - t0
@@ -265,6 +267,7 @@ class Server:
                     ta, k = s.queue.pop(0)
                     sl.submit(s.frames[k % len(s.frames)], tag=(ta, k))
         wall = time.perf_counter() - t0
+        gc.enable()
         lat_ms = np.array(lat) * 1e3
         return {"frames": done_frames, "seconds": wall, "frames_per_s": done_frames / wall,
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
