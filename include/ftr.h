@@ -52,19 +52,27 @@ typedef enum {
     FTR_EINVAL = -1,    /* bad argument; nothing was enqueued                   */
     FTR_ENOMEM = -2,    /* device allocation failed                             */
     FTR_ECUDA = -3,     /* a CUDA call failed; the context may be unusable      */
-    FTR_ETIMEOUT = -4,  /* reserved for bounded device waits                    */
+    FTR_ETIMEOUT = -4,  /* a bounded device wait gave up (tensor-core completion) */
     FTR_ESTATE = -5,    /* call out of order (e.g. extract before solve)        */
     FTR_ECAPACITY = -6  /* caller buffers too small for the result (see ftr_frame_finish) */
 } ftr_status;
 
 enum { FTR_SPLAT_WEIGHTED = 0, FTR_SPLAT_SIMPLE = 1 };
-enum { FTR_PREC_FP32 = 0 };
+/*
+ * Arithmetic of the FFT passes.  FTR_PREC_FP32: fp32 register butterflies.
+ * FTR_PREC_BF16X3 / FTR_PREC_FP16X3: every small DFT of the transforms runs
+ * on the tensor cores with each operand split into two 16-bit parts (bf16 or
+ * fp16) and three products accumulated in fp32; twiddles, filter and the rest
+ * stay fp32.  Not in the paper (Sec. III-B uses fp32 FFTs); the split
+ * variants need every grid size in {64, 128, 256, 384}.
+ */
+enum { FTR_PREC_FP32 = 0, FTR_PREC_BF16X3 = 1, FTR_PREC_FP16X3 = 2 };
 
 typedef struct {
     float sigma1_scale;   /* sigma1 = scale * half voxel diagonal (Sec. III-B); default 1   */
     float sigma2_ratio2;  /* sigma2^2 / sigma1^2 (Sec. III-B: 3/2); default 1.5              */
     int splat_mode;       /* FTR_SPLAT_WEIGHTED eq.(1)(2) | FTR_SPLAT_SIMPLE nearest node   */
-    int precision;        /* FTR_PREC_FP32 (only value accepted)                             */
+    int precision;        /* FTR_PREC_FP32 (default), FTR_PREC_BF16X3 or FTR_PREC_FP16X3       */
     void* stream;         /* cudaStream_t to order all work on; NULL = context-owned stream  */
 } ftr_params;
 

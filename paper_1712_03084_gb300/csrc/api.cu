@@ -32,6 +32,18 @@ int cuda_fail(ftr_ctx* c, cudaError_t e, const char* what) {
                    cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+// After a stream synchronisation: FTR_ETIMEOUT if a tensor-core completion
+// wait of the split-precision passes gave up since the last check.
+int tc_check(ftr_ctx* c, const char* who) {
+    if (!c->d_tc_err) return FTR_OK;
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, who);
+    if (!flag) return FTR_OK;
+    cudaMemset(c->d_tc_err, 0, sizeof(int));
+    return set_err(c, FTR_ETIMEOUT, "%s: a tensor-core completion wait timed out", who);
+}
+
 void prof_begin(ftr_ctx* c, int st) {
     if (!c->prof) return;
     if (c->ev_pending[st]) {
@@ -179,6 +191,8 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_s1);
     dfree(c->d_A);
     for (int a = 0; a < 3; ++a) dfree(c->d_tw[a]);
+    dfree(c->d_tc_table);
+    dfree(c->d_tc_err);
     dfree(c->d_level);
     dfree(c->d_levelf);
     dfree(c->d_level_part);
@@ -226,7 +240,12 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     if (p) prm = *p;
     if (!(prm.sigma1_scale > 0.f) || !(prm.sigma2_ratio2 > 1.0f)) return FTR_EINVAL;
     if (prm.splat_mode != FTR_SPLAT_WEIGHTED && prm.splat_mode != FTR_SPLAT_SIMPLE) return FTR_EINVAL;
-    if (prm.precision != FTR_PREC_FP32) return FTR_EINVAL;
+    if (prm.precision != FTR_PREC_FP32 && prm.precision != FTR_PREC_BF16X3 && prm.precision != FTR_PREC_FP16X3)
+        return FTR_EINVAL;
+    if (prm.precision != FTR_PREC_FP32) {
+        for (int a = 0; a < 3; ++a)
+            if (!tc_supported_n(grid_n[a])) return FTR_EINVAL;
+    }
 
     ftr_ctx* c = new (std::nothrow) ftr_ctx();
     if (!c) return FTR_ENOMEM;
@@ -312,6 +331,21 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
             tw[m] = make_float2((float)cos(ang), (float)(-sin(ang)));
         }
         if ((e = cudaMemcpy(c->d_tw[a], tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return FTR_ECUDA;
+        }
+    }
+    if (prm.precision != FTR_PREC_FP32) {
+        std::vector<unsigned char> tab;
+        tc_build_table(prm.precision, tab);
+        if ((e = dalloc(&c->d_tc_table, tab.size())) != cudaSuccess || (e = dalloc(&c->d_tc_err, 1)) != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return FTR_ENOMEM;
+        }
+        if ((e = cudaMemcpy(c->d_tc_table, tab.data(), tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemset(c->d_tc_err, 0, sizeof(int))) != cudaSuccess || (e = tc_prepare(c)) != cudaSuccess) {
             free_all(c);
             delete c;
             return FTR_ECUDA;
@@ -446,6 +480,7 @@ int ftr_solve(ftr_ctx* c, double* iso_level_out) {
         if ((e = cudaMemcpyAsync(&c->level_host, c->d_level, sizeof(double), cudaMemcpyDeviceToHost, c->stream)))
             return cuda_fail(c, e, "ftr_solve: level copy");
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve");
+        if (int st = tc_check(c, "ftr_solve")) return st;
         *iso_level_out = c->level_host;
     }
     return FTR_OK;
@@ -498,6 +533,7 @@ int ftr_extract_mesh(ftr_ctx* c, ftr_mesh* out) {
     if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: count");
     if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
+    if (int st = tc_check(c, "ftr_extract_mesh")) return st;
     const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
     if (na > c->cap_mc_nodes || nv > c->cap_verts || nt > c->cap_tris) {
         // the buffers were too small: the kernels skipped the writes past them
@@ -822,6 +858,11 @@ int ftr_frame_finish(ftr_ctx* c, ftr_mesh* out) {
     if (!c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_frame_finish: nothing pending");
     cudaError_t e;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish");
+    if (int st = tc_check(c, "ftr_frame_finish")) {
+        c->mesh_pending = false;
+        c->tex_pending = false;
+        return st;
+    }
     const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
     if (na > c->cap_mc_nodes || nv > c->cap_verts || nt > c->cap_tris) {
         if ((e = grow_mesh(c, na, nv, nt)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_finish: grow");
@@ -874,6 +915,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
     b += 5 * c->Mh * (int64_t)sizeof(float2) + c->M * (int64_t)sizeof(float);
     b += (int64_t)(c->g.n[0] + c->g.n[1] + c->g.n[2]) * (int64_t)sizeof(float2);
+    if (c->d_tc_table) b += (int64_t)tc_table_bytes() + 16;
     b += (2 * c->level_blocks + 8) * (int64_t)sizeof(double);
     b += (6 * (int64_t)c->mc_blocks + 16) * (int64_t)sizeof(int);
     b += c->cap_mc_nodes * (int64_t)sizeof(int4) + c->cap_verts * 6 * (int64_t)sizeof(float) +

@@ -140,6 +140,7 @@ cudaError_t run_fx(ftr_ctx* c) {
 cudaError_t fft_fx_init() { return upload_w96_table(); }
 
 cudaError_t launch_fx(ftr_ctx* c) {
+    if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 0);
     switch (c->g.n[0]) {
         case 32: return run_fx<32>(c);
         case 48: return run_fx<48>(c);

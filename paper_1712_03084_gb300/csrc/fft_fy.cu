@@ -107,6 +107,7 @@ cudaError_t run_fy(ftr_ctx* c) {
 cudaError_t fft_fy_init() { return upload_w96_table(); }
 
 cudaError_t launch_fy(ftr_ctx* c) {
+    if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 1);
     switch (c->g.n[1]) {
         case 32: return run_fy<32>(c);
         case 48: return run_fy<48>(c);

@@ -119,6 +119,7 @@ cudaError_t run_fz(ftr_ctx* c) {
 cudaError_t fft_fz_init() { return upload_w96_table(); }
 
 cudaError_t launch_fz(ftr_ctx* c) {
+    if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 2);
     switch (c->g.n[2]) {
         case 32: return run_fz<32>(c);
         case 48: return run_fz<48>(c);

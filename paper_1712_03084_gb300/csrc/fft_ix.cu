@@ -92,6 +92,7 @@ cudaError_t run_ix(ftr_ctx* c) {
 cudaError_t fft_ix_init() { return upload_w96_table(); }
 
 cudaError_t launch_ix(ftr_ctx* c) {
+    if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 4);
     switch (c->g.n[0]) {
         case 32: return run_ix<32>(c);
         case 48: return run_ix<48>(c);

@@ -65,6 +65,7 @@ cudaError_t run_iy(ftr_ctx* c) {
 cudaError_t fft_iy_init() { return upload_w96_table(); }
 
 cudaError_t launch_iy(ftr_ctx* c) {
+    if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 3);
     switch (c->g.n[1]) {
         case 32: return run_iy<32>(c);
         case 48: return run_iy<48>(c);

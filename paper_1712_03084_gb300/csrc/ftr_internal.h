@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ftr.h"
 
@@ -115,6 +116,8 @@ struct ftr_ctx {
     float2* d_s1 = nullptr;    // 2 x Mh  [kx][ky][z]
     float* d_A = nullptr;      // M       [z][y][x]
     float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
+    unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
+    int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
 
     // level
     double* d_level = nullptr;     // [0] L, [1] accepted count
@@ -198,6 +201,13 @@ cudaError_t launch_fz(ftr_ctx* c);
 cudaError_t launch_iy(ftr_ctx* c);
 cudaError_t launch_ix(ftr_ctx* c);
 cudaError_t launch_level(ftr_ctx* c);
+// tensor-core split-precision passes (fft_tc.cu): pass 0 x fwd, 1 y fwd,
+// 2 z fwd + filter + z inv, 3 y inv, 4 x inv
+bool tc_supported_n(int n);
+size_t tc_table_bytes();
+void tc_build_table(int precision, std::vector<unsigned char>& out);
+cudaError_t launch_tc_pass(ftr_ctx* c, int pass);
+cudaError_t tc_prepare(ftr_ctx* c);
 cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan; totals to h_mc_tot
 cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
 cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);

@@ -19,6 +19,10 @@ LIB_PATH = os.path.join(_HERE, "lib", "libftr.so")
 FTR_OK = 0
 FTR_SPLAT_WEIGHTED = 0
 FTR_SPLAT_SIMPLE = 1
+FTR_PREC_FP32 = 0
+FTR_PREC_BF16X3 = 1
+FTR_PREC_FP16X3 = 2
+FTR_ETIMEOUT = -4
 MAX_TRIS_PER_CASE = 5
 
 _lib = None
@@ -334,11 +338,12 @@ class Context:
     """Owns one ftr_ctx; methods forward to the C-named calls above."""
 
     def __init__(self, grid_n, bbox, sigma1_scale=1.0, sigma2_ratio2=1.5, splat_mode=FTR_SPLAT_WEIGHTED,
-                 stream=None):
+                 stream=None, precision=FTR_PREC_FP32):
         p = ftr_default_params()
         p.sigma1_scale = sigma1_scale
         p.sigma2_ratio2 = sigma2_ratio2
         p.splat_mode = splat_mode
+        p.precision = precision
         p.stream = stream
         self.grid_n = tuple(int(v) for v in grid_n)
         self.bbox = tuple(float(v) for v in bbox)

@@ -54,6 +54,18 @@ def test_create_rejects_bad_grids_without_gpu(lib):
             ftr.ftr_create(grid, box)
 
 
+def test_create_rejects_split_precision_on_unsupported_grids_without_gpu(lib):
+    """The tensor-core variants need every axis in {64, 128, 256, 384}; other
+    grids and unknown precision codes are rejected before any device call."""
+    from paper_1712_03084_gb300 import ftr
+    for grid, prec in [((96, 96, 96), ftr.FTR_PREC_BF16X3), ((64, 64, 48), ftr.FTR_PREC_FP16X3),
+                       ((512, 512, 512), ftr.FTR_PREC_BF16X3), ((64, 64, 64), 3), ((64, 64, 64), -1)]:
+        p = ftr.ftr_default_params()
+        p.precision = prec
+        with pytest.raises(ftr.FtrError):
+            ftr.ftr_create(grid, (0, 0, 0, 1, 1, 1), p)
+
+
 def test_product_path_does_not_touch_the_oracle():
     pkg = os.path.join(ROOT, "paper_1712_03084_gb300")
     for dirpath, _, files in os.walk(pkg):
