@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi clocks")
     ap.add_argument("--no-multi", action="store_true", help="skip the batched and served configurations")
+    ap.add_argument("--no-precision", action="store_true", help="skip the split-precision configuration")
+    ap.add_argument("--precision-oracle", action="store_true",
+                    help="also compare the split-precision results with the FP64 oracle (minutes of CPU)")
     return ap.parse_args()
 
 
@@ -421,6 +424,12 @@ def run_ours(args, rank, world, local_rank):
         ctx.close()
         ctx = None
         multi = run_multi(args, rank, dev, plain_frame=fr)
+    prec = None
+    if not args.no_precision:
+        if ctx is not None:
+            ctx.close()
+            ctx = None
+        prec = run_precision(args, rank, dev, fr)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -450,6 +459,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if multi:
         line.update(multi)
+    if prec:
+        line.update(prec)
     return line
 
 
@@ -533,6 +544,118 @@ def run_multi(args, rank, dev, plain_frame=None):
                                "texturing on, 120 GB HBM admission budget; latency = completion - arrival (host "
                                "clock), inputs copied from pinned host memory per frame"}
     return out
+
+
+PREC_NAMES = ((0, "fp32"), (1, "bf16x3"), (2, "fp16x3"))
+
+
+def run_precision(args, rank, dev, fr256):
+    """fp32 vs the split-precision tensor-core FFT passes on the human frame at
+    256^3 and 384^3: graph frames/s, FFT stage time, and the error of A, L and
+    the mesh against the fp32 path (and, with --precision-oracle, against the
+    FP64 oracle)."""
+    import torch
+    from datagen import frame_config, human_frame
+    from paper_1712_03084_gb300 import ftr
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    steps = max(10, min(args.steps, 30))
+    out = {}
+    for gname in ("human256", "human384"):
+        cfg = frame_config(gname)
+        grid, box = cfg["grid_n"], cfg["bbox"]
+        fr = fr256 if gname == "human256" else human_frame(seed=args.seed + rank, K=cfg["K"], ring=cfg["ring"],
+                                                             height=cfg["height"])
+        tol = depth_tol(cfg)
+        K = len(fr["views"])
+        P = torch.from_numpy(fr["points"]).to(dev)
+        N = torch.from_numpy(fr["normals"]).to(dev)
+        W = torch.from_numpy(fr["weights"]).to(dev)
+        cams = list(fr["per_camera"])
+        dviews = []
+        for v in fr["views"]:
+            d = dict(v)
+            for k in ("depth", "conf", "rgb"):
+                d[k] = torch.from_numpy(v[k]).to(dev)
+            dviews.append(d)
+        cap = grid[0] * grid[1] * grid[2] // 64
+        outs = [torch.empty((cap, K), dtype=torch.float32, device=dev),
+                torch.empty((cap, K, 2), dtype=torch.float32, device=dev),
+                torch.empty((cap, 3), dtype=torch.uint8, device=dev),
+                torch.empty((cap,), dtype=torch.uint8, device=dev)]
+        res, ref = {}, None
+        orc = None
+        if args.precision_oracle and rank == 0:
+            from oracle import pipeline
+            h = max((box[3 + a] - box[a]) / grid[a] for a in range(3))
+            t0 = time.perf_counter()
+            from datagen import f32_box
+            r = pipeline.reconstruct(fr["points"], fr["normals"], fr["weights"], grid, f32_box(box))
+            orc = {"A": r["A"], "L": r["L"], "V": r["mesh"]["vertices"], "h": h,
+                   "span": float(r["A"].max() - r["A"].min()), "s": time.perf_counter() - t0}
+            del r
+        for prec, pname in PREC_NAMES:
+            stream = torch.cuda.Stream(device=dev)
+            ctx = ftr.Context(grid, box, stream=stream.cuda_stream, precision=prec)
+
+            def frame():
+                ctx.reset()
+                for (s, n) in cams:
+                    ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+                ftr.ftr_frame_launch(ctx.h, dviews, tol, *outs, cap)
+
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    frame()
+                    ftr.ftr_frame_finish(ctx.h)
+                for i in range(steps):
+                    flush.fill_(float(i))
+                    evs[i][0].record(stream)
+                    frame()
+                    evs[i][1].record(stream)
+                    ftr.ftr_frame_finish(ctx.h)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            # FFT stage times from one profiled pass of separate launches
+            ctx.profile_enable(True)
+            with torch.cuda.stream(stream):
+                for i in range(steps):
+                    flush.fill_(float(i))
+                    ctx.reset()
+                    for (s, n) in cams:
+                        ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+                    ctx.solve(want_level=False)
+            torch.cuda.synchronize()
+            prof = ctx.profile_read()
+            ctx.profile_enable(False)
+            fft_ms = sum(t / n for k, (t, n) in prof.items() if k.startswith("fft_") and n)
+            L = ctx.solve()
+            A = ctx.field_A()
+            verts = ctx.mesh_numpy()["vertices"]
+            ctx.close()
+            e = {"frames_per_s": round(1000.0 / ms, 1), "ms_per_frame": round(ms, 4), "fft_ms": round(fft_ms, 4)}
+            if ref is None:
+                ref = (A, L, verts)
+            else:
+                e["A_rel_l2_vs_fp32"] = float(f"{np.linalg.norm(A - ref[0]) / np.linalg.norm(ref[0]):.3e}")
+            if orc is not None:
+                from scipy.spatial import cKDTree
+                da, _ = cKDTree(orc["V"]).query(verts)
+                db, _ = cKDTree(verts).query(orc["V"])
+                e["vs_oracle"] = {
+                    "A_rel_l2": float(f"{np.linalg.norm(A - orc['A']) / np.linalg.norm(orc['A']):.3e}"),
+                    "dL_over_span": float(f"{abs(L - orc['L']) / orc['span']:.3e}"),
+                    "hausdorff_voxels": float(f"{max(da.max(), db.max()) / orc['h']:.3e}")}
+            res[pname] = e
+            del A
+        res["config"] = (f"{gname}: 4-camera human frame, {grid[0]}^3 over a 2.0 m cube, {len(fr['points'])} points; "
+                         f"graph frames (solve + mesh + texture), {steps} timed frames, L2 flushed between frames")
+        if orc is not None:
+            res["oracle_seconds"] = round(orc["s"], 1)
+        out[gname] = res
+        del P, N, W, dviews, outs
+        torch.cuda.empty_cache()
+    return {"precision": out}
 
 
 def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):

@@ -19,4 +19,5 @@ from .scenes import (  # noqa: F401
     human_primitives,
     human_frame,
     frame_config,
+    f32_box,
 )

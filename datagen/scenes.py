@@ -369,6 +369,12 @@ def rgb_view(rgb_cam, prims, params, chunk=1 << 19, device=None):
 
 # --------------------------------------------------------------------------- frames
 
+def f32_box(box):
+    """The bounding box as the C ABI receives it (float32 per coordinate),
+    as float64 values: the oracle must see the same box the kernels see."""
+    return tuple(float(np.float32(v)) for v in box)
+
+
 def frame_config(name):
     """Named workloads: grid, bbox and capture geometry."""
     if name == "sphere64":

@@ -8,7 +8,7 @@ import functools
 
 import numpy as np
 
-from datagen import frame_config, human_frame, sphere_points
+from datagen import f32_box, frame_config, human_frame, sphere_points
 from oracle import conventions as cv
 from oracle import pipeline
 
@@ -50,7 +50,8 @@ def case_inputs(name):
 def oracle_result(name):
     c = CASES[name]
     P, N, W, views = case_inputs(name)
-    return pipeline.reconstruct(P, N, W, c["grid"], c["bbox"], mode=c.get("mode", cv.SPLAT_WEIGHTED))
+    # the oracle gets the box exactly as the kernels do (float32 coordinates)
+    return pipeline.reconstruct(P, N, W, c["grid"], f32_box(c["bbox"]), mode=c.get("mode", cv.SPLAT_WEIGHTED))
 
 
 def rel_l2(a, b):

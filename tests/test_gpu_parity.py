@@ -65,7 +65,7 @@ def test_marching_cubes_bit_exact_on_oracle_field(ftr, name):
     r = G.oracle_result(name)
     A32 = r["A"].astype(np.float32)
     L = r["L"]
-    ref = omc.marching_cubes(A32.astype(np.float64), L, c["grid"], c["bbox"])
+    ref = omc.marching_cubes(A32.astype(np.float64), L, c["grid"], G.f32_box(c["bbox"]))
     ctx = ftr.Context(c["grid"], c["bbox"])
     ctx.set_indicator(A32, L)
     assert np.array_equal(ctx.cube_classes(), ref["classes"].astype(np.uint8))
