@@ -285,6 +285,8 @@ def run_ours(args, rank, world, local_rank):
     tol = depth_tol(cfg)
     stream = torch.cuda.Stream(device=dev)
     ctx = ftr.Context(grid, box, stream=stream.cuda_stream)
+    tune_us = ctx.autotune()          # tile plans of the y, z, inverse-y passes (cached per grid)
+    plan = ctx.plan()
     K = len(fr["views"])
 
     # device-resident inputs
@@ -451,6 +453,8 @@ def run_ours(args, rank, world, local_rank):
                                "512x424 depth (fx=fy=365), 1920x1080 RGB, ring 2.5 m",
                    "grid": list(grid), "points": int(info["points_in"]), "vertices": int(info["n_vertices"]),
                    "triangles": int(info["n_tris"]), "cameras": K, "parallelism": f"replicas{world}",
+                   "plan": {"lines_per_cta_y_z_iy": list(plan),
+                            "autotune_us_per_launch": [[round(float(v), 2) for v in row] for row in tune_us]},
                    "l2": "flushed between steps (256 MiB write, untimed)"},
         "latency_ms": {"p50": round(float(np.percentile(step_ms_sorted, 50)), 4),
                        "p99": round(float(np.percentile(step_ms_sorted, 99)), 4)},

@@ -216,6 +216,30 @@ int ftr_frame_info(ftr_ctx* ctx, int64_t* info, int n);
  * brick tables, point store, mesh buffers and staging). */
 int64_t ftr_device_bytes(const ftr_ctx* ctx);
 
+/*
+ * Tile plans (no counterpart in the paper, which gives no kernel design).
+ * The y, z and inverse-y FFT passes each move F lines per CTA, F in
+ * {8, 16, 32}; every plan computes bit-identical results (each line's
+ * arithmetic does not depend on F), only the speed differs.
+ *
+ * ftr_autotune times the three F of each pass on this context's grid (a few
+ * launches each, on the context's own buffers, so no frame may be pending:
+ * FTR_ESTATE) and keeps the fastest; the choice is cached per device and
+ * grid for the process, so later contexts of the same grid take it without
+ * timing.  report (nullable): 9 floats, microseconds per launch of F = 8, 16,
+ * 32 for the y, z and inverse-y passes (0 = not timed: cached, or the
+ * variant does not fit in shared memory).  Waits for the stream.  Split
+ * precision contexts keep F = 16 (their passes have no variants).
+ */
+int ftr_autotune(ftr_ctx* ctx, float* report);
+
+/* The plan in use: plan[0..2] = lines per CTA of the y, z and inverse-y passes. */
+int ftr_get_plan(const ftr_ctx* ctx, int* plan);
+
+/* Force a plan: each entry 8, 16 or 32 and a divisor of the axis the pass
+ * tiles (n_z for the y passes, n_y for the z pass), else FTR_EINVAL. */
+int ftr_set_plan(ftr_ctx* ctx, const int* plan);
+
 /* Message of the last error on this context (never NULL). */
 const char* ftr_last_error(const ftr_ctx* ctx);
 

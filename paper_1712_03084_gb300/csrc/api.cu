@@ -7,8 +7,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <array>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "ftr_internal.h"
@@ -900,6 +903,105 @@ int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return FTR_ECUDA;
         *points_dropped = (int64_t)d;
+    }
+    return FTR_OK;
+}
+
+namespace {
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int, int>, std::array<int, 3>> g_plans;   // (device, n) -> lines per CTA
+
+bool valid_lines(int f) { return f == 8 || f == 16 || f == 32; }
+
+// F lines per CTA must tile the axis the pass strides over (z for the y
+// passes, y for the z pass).
+bool plan_fits(const ftr_ctx* c, int pass, int f) {
+    const int n = pass == 1 ? c->g.n[1] : c->g.n[2];
+    return valid_lines(f) && n % f == 0;
+}
+}  // namespace
+
+int ftr_get_plan(const ftr_ctx* c, int* plan) {
+    if (!c || !plan) return FTR_EINVAL;
+    for (int i = 0; i < 3; ++i) plan[i] = c->plan_lines[i];
+    return FTR_OK;
+}
+
+int ftr_set_plan(ftr_ctx* c, const int* plan) {
+    if (!c || !plan) return FTR_EINVAL;
+    for (int i = 0; i < 3; ++i)
+        if (!plan_fits(c, i, plan[i]))
+            return set_err(c, FTR_EINVAL, "ftr_set_plan: lines per CTA must be 8, 16 or 32 and divide the grid");
+    if (c->p.precision != FTR_PREC_FP32) return set_err(c, FTR_EINVAL, "ftr_set_plan: fp32 passes only");
+    for (int i = 0; i < 3; ++i) c->plan_lines[i] = plan[i];
+    c->graph_valid = false;
+    return FTR_OK;
+}
+
+int ftr_autotune(ftr_ctx* c, float* report) {
+    if (!c) return FTR_EINVAL;
+    if (report)
+        for (int i = 0; i < 9; ++i) report[i] = 0.f;
+    if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_autotune: a frame is pending");
+    if (c->p.precision != FTR_PREC_FP32) return FTR_OK;
+    const auto key = std::make_tuple(c->device, c->g.n[0], c->g.n[1], c->g.n[2]);
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find(key);
+        if (it != g_plans.end()) {
+            for (int i = 0; i < 3; ++i) c->plan_lines[i] = it->second[i];
+            c->graph_valid = false;
+            return FTR_OK;
+        }
+    }
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_autotune");
+    // every z-plane live, so that the forward passes do their full work; the
+    // next splat rewrites these values
+    const int meta[4] = {c->n_bricks, 0, 0, c->g.nb[2] - 1};
+    if ((e = cudaMemcpyAsync(c->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_autotune");
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    const int F[3] = {8, 16, 32};
+    const int reps = 5;
+    std::array<int, 3> best = {16, 16, 16};
+    for (int pass = 0; pass < 3; ++pass) {
+        float best_us = 1e30f;
+        for (int v = 0; v < 3; ++v) {
+            if (!plan_fits(c, pass, F[v])) continue;
+            c->plan_lines[pass] = F[v];
+            auto run = [&]() { return pass == 0 ? launch_fy(c) : (pass == 1 ? launch_fz(c) : launch_iy(c)); };
+            if (run() != cudaSuccess) {     // the variant does not fit: skip it
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(t0, c->stream);
+            for (int r = 0; r < reps; ++r) run();
+            cudaEventRecord(t1, c->stream);
+            if ((e = cudaEventSynchronize(t1)) != cudaSuccess) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+                return cuda_fail(c, e, "ftr_autotune");
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            const float us = 1000.f * ms / reps;
+            if (report) report[3 * pass + v] = us;
+            if (us < best_us) {
+                best_us = us;
+                best[pass] = F[v];
+            }
+        }
+        c->plan_lines[pass] = best[pass];
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    c->graph_valid = false;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        g_plans[key] = best;
     }
     return FTR_OK;
 }

@@ -21,6 +21,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 namespace ftr {
 
 // W_96^j = exp(-2 pi i j / 96); filled from the host (double cos/sin) once per
@@ -168,6 +172,27 @@ template <int N>
 struct MinCtas {
     static constexpr int value = N <= 256 ? 3 : 1;
 };
+// The same register budget per thread for other tile heights F (lines per
+// CTA): F = 8 asks for twice the CTAs of F = 16, F = 32 half (at least one).
+template <int N, int F>
+struct MinCtasF {
+    static constexpr int raw = MinCtas<N>::value * 16 / F;
+    static constexpr int value = raw < 1 ? 1 : raw;
+};
+
+// Raise a kernel's dynamic shared-memory limit to `bytes`, once per device.
+template <class K>
+inline cudaError_t ensure_smem(K kernel, size_t bytes, int device) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair((const void*)kernel, device);
+    if (done.count(key)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
 __host__ __device__ constexpr int make_odd(int v) { return (v & 1) ? v : v + 1; }
 
 // Shared-memory exchange layout for F lines of length N: element (f, j, k1)

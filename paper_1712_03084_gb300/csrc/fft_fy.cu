@@ -14,92 +14,98 @@
 namespace ftr {
 namespace {
 
-constexpr int kLines = 16;
-
 // Load line f's elements y = N2 n1 + r (contiguous) and run step 1.
-template <int N>
+template <int N, int F>
 __device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r, int f, float2* smem,
                                            const float2* __restrict__ tw) {
-    using X = Xchg<N, kLines>;
+    using X = Xchg<N, F>;
     float2 v[X::N1];
 #pragma unroll
     for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = src[X::N2 * n1 + r];
-    fft_step1<N, kLines, -1>(v, f, r, smem, tw);
+    fft_step1<N, F, -1>(v, f, r, smem, tw);
 }
 
-template <int N>
-__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT, MinCtas<N>::value)
+// F lines per CTA (the tile plan; 8, 16 or 32).
+template <int N, int F>
+__global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     k_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
          const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta) {
-    using X = Xchg<N, kLines>;
+    using X = Xchg<N, F>;
     extern __shared__ float2 smem[];
     const int nz = g.n[2];
-    const int z0 = blockIdx.x * kLines;
+    const int z0 = blockIdx.x * F;
     const int kx = blockIdx.y;
     const int tid = threadIdx.x;
     // tiles outside the slab of touched bricks are zero; the z pass treats
-    // them as zero without reading, so nothing is read or written here
+    // them as zero without reading, so nothing is read or written here (a
+    // tile that straddles the slab edge is transformed whole: its lines
+    // outside the slab are never read by the z pass)
     int zl, zh;
     live_z_range(meta, zl, zh);
-    if (z0 < zl || z0 >= zh) return;
+    if (z0 + F <= zl || z0 >= zh) return;
     // step-1 mapping: element index fastest (contiguous y lines)
     const int f1 = tid / X::NT, r1 = tid % X::NT;
     // step-2 mapping: line index fastest (contiguous z in the output)
-    const int f2 = tid % kLines, i2 = tid / kLines;
+    const int f2 = tid % F, i2 = tid / F;
     const size_t out_base = (size_t)(z0 + f2) + (size_t)nz * ((size_t)N * kx);
     // the transformed x component waits in shared memory (line index fastest)
     float2* stash = smem + X::SIZE;
     const float2* line = s0 + (size_t)N * (z0 + f1 + (size_t)nz * kx);
     // x component: transform along y and park it (line index fastest)
-    if (r1 < X::N2) load_step1<N>(line, r1, f1, smem, tw);
+    if (r1 < X::N2) load_step1<N, F>(line, r1, f1, smem, tw);
     __syncthreads();
     float2 o[X::N2];
-    if (i2 < X::N1) fft_step2<N, kLines, -1>(o, f2, i2, smem);
+    if (i2 < X::N1) fft_step2<N, F, -1>(o, f2, i2, smem);
     __syncthreads();
     if (i2 < X::N1) {
 #pragma unroll
-        for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (kLines + 1) * (i2 + X::N1 * k2)] = o[k2];
+        for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (F + 1) * (i2 + X::N1 * k2)] = o[k2];
     }
     // y component: transform, then W = x + j w_y y goes out as field 0
-    if (r1 < X::N2) load_step1<N>(line + Mh, r1, f1, smem, tw);
+    if (r1 < X::N2) load_step1<N, F>(line + Mh, r1, f1, smem, tw);
     __syncthreads();
-    if (i2 < X::N1) fft_step2<N, kLines, -1>(o, f2, i2, smem);
+    if (i2 < X::N1) fft_step2<N, F, -1>(o, f2, i2, smem);
     __syncthreads();
     if (i2 < X::N1) {
 #pragma unroll
         for (int k2 = 0; k2 < X::N2; ++k2) {
             const int ky = i2 + X::N1 * k2;
             const float wy = (ky == N / 2) ? 0.f : wy_scale * (float)signed_bin(ky, N);
-            const float2 w = stash[f2 + (kLines + 1) * ky];
+            const float2 w = stash[f2 + (F + 1) * ky];
             s1[out_base + (size_t)nz * ky] = make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x);
         }
     }
     // z component: transform and write as field 1
-    if (r1 < X::N2) load_step1<N>(line + 2 * Mh, r1, f1, smem, tw);
+    if (r1 < X::N2) load_step1<N, F>(line + 2 * Mh, r1, f1, smem, tw);
     __syncthreads();
     if (i2 < X::N1) {
-        fft_step2<N, kLines, -1>(o, f2, i2, smem);
+        fft_step2<N, F, -1>(o, f2, i2, smem);
 #pragma unroll
         for (int k2 = 0; k2 < X::N2; ++k2) s1[Mh + out_base + (size_t)nz * (i2 + X::N1 * k2)] = o[k2];
     }
 }
 
-template <int N>
-cudaError_t run_fy(ftr_ctx* c) {
-    using X = Xchg<N, kLines>;
-    const size_t smem = sizeof(float2) * (X::SIZE + (kLines + 1) * N);
-    static bool attr_done[64] = {};
-    if (!attr_done[c->device & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(k_fy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[c->device & 63] = true;
-    }
-    dim3 grid(c->g.n[2] / kLines, c->g.n[0] / 2 + 1);
+template <int N, int F>
+cudaError_t run_fy_f(ftr_ctx* c) {
+    using X = Xchg<N, F>;
+    const size_t smem = sizeof(float2) * (X::SIZE + (F + 1) * N);
+    cudaError_t e = ensure_smem(k_fy<N, F>, smem, c->device);
+    if (e != cudaSuccess) return e;
+    dim3 grid(c->g.n[2] / F, c->g.n[0] / 2 + 1);
     const float wy_scale = (float)(2.0 * 3.14159265358979323846 / (c->g.n[1] * c->g.h[1]));
-    k_fy<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,
+    k_fy<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,
                                                        c->d_meta);
     c->launches++;
     return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t run_fy(ftr_ctx* c) {
+    switch (c->plan_lines[0]) {
+        case 8: return run_fy_f<N, 8>(c);
+        case 32: return run_fy_f<N, 32>(c);
+        default: return run_fy_f<N, 16>(c);
+    }
 }
 
 }  // namespace

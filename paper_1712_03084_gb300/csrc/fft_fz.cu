@@ -15,30 +15,29 @@
 namespace ftr {
 namespace {
 
-constexpr int kLines = 16;
-
 // Load line f's elements z = N2 n1 + r (zero outside [zl, zh)) and run step 1.
-template <int N>
+template <int N, int F>
 __device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r, int f, int zl, int zh,
                                            float2* smem, const float2* __restrict__ tw) {
-    using X = Xchg<N, kLines>;
+    using X = Xchg<N, F>;
     float2 v[X::N1];
 #pragma unroll
     for (int n1 = 0; n1 < X::N1; ++n1) {
         const int z = X::N2 * n1 + r;
         v[n1] = (z >= zl && z < zh) ? src[z] : make_float2(0.f, 0.f);
     }
-    fft_step1<N, kLines, -1>(v, f, r, smem, tw);
+    fft_step1<N, F, -1>(v, f, r, smem, tw);
 }
 
-template <int N>
-__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT, MinCtas<N>::value)
+// F lines per CTA (the tile plan; 8, 16 or 32).
+template <int N, int F>
+__global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     k_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
          float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta) {
-    using X = Xchg<N, kLines>;
+    using X = Xchg<N, F>;
     extern __shared__ float2 smem[];
     const int ny = g.n[1], nx = g.n[0];
-    const int ky0 = blockIdx.x * kLines;
+    const int ky0 = blockIdx.x * F;
     const int kx = blockIdx.y;
     const int tid = threadIdx.x;
     const int f = tid / X::NT, r = tid % X::NT;
@@ -46,21 +45,21 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT, MinCtas<N>::valu
     live_z_range(meta, zl, zh);
     const size_t line = (size_t)N * ((size_t)(ky0 + f) + (size_t)ny * kx);
     // forward z transforms of W (field 0) and of the x/y-transformed V_z (field 1)
-    if (r < X::N2) load_step1<N>(s1 + line, r, f, zl, zh, smem, tw);
+    if (r < X::N2) load_step1<N, F>(s1 + line, r, f, zl, zh, smem, tw);
     __syncthreads();
     // the transformed W waits in shared memory (the same thread reads it back)
     float2* stash = smem + X::SIZE;
     float2 xw[X::N2];
     if (r < X::N1) {
-        fft_step2<N, kLines, -1>(xw, f, r, smem);
+        fft_step2<N, F, -1>(xw, f, r, smem);
 #pragma unroll
-        for (int k2 = 0; k2 < X::N2; ++k2) stash[f + (kLines + 1) * (r + X::N1 * k2)] = xw[k2];
+        for (int k2 = 0; k2 < X::N2; ++k2) stash[f + (F + 1) * (r + X::N1 * k2)] = xw[k2];
     }
     __syncthreads();
-    if (r < X::N2) load_step1<N>(s1 + Mh + line, r, f, zl, zh, smem, tw);
+    if (r < X::N2) load_step1<N, F>(s1 + Mh + line, r, f, zl, zh, smem, tw);
     __syncthreads();
     float2 xh[X::N2];
-    if (r < X::N1) fft_step2<N, kLines, -1>(xh, f, r, smem);
+    if (r < X::N1) fft_step2<N, F, -1>(xh, f, r, smem);
     __syncthreads();
     if (r < X::N1) {
         const int ky = ky0 + f;
@@ -75,43 +74,48 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT, MinCtas<N>::valu
             const float den = base + wzd * wzd;
             const float s = den > 0.f ? inv_m / den : 0.f;
             // S = W^ + j w_z V^_z
-            const float2 w = stash[f + (kLines + 1) * kz];
+            const float2 w = stash[f + (F + 1) * kz];
             const float2 sv = make_float2(w.x - wzn * xh[k2].y, w.y + wzn * xh[k2].x);
             xw[k2] = make_float2(sv.x * s, sv.y * s);
         }
         (void)nx;
-        fft_step1_swapped<N, kLines, +1>(xw, f, r, smem, tw);
+        fft_step1_swapped<N, F, +1>(xw, f, r, smem, tw);
     }
     __syncthreads();
     if (r < X::N2) {
         float2 o[X::N1];
-        fft_step2_swapped<N, kLines, +1>(o, f, r, smem);
+        fft_step2_swapped<N, F, +1>(o, f, r, smem);
         float2* dst = s1 + line;
 #pragma unroll
         for (int k2 = 0; k2 < X::N1; ++k2) dst[r + X::N2 * k2] = o[k2];
     }
 }
 
-template <int N>
-cudaError_t run_fz(ftr_ctx* c) {
-    using X = Xchg<N, kLines>;
-    const size_t smem = sizeof(float2) * (X::SIZE + (kLines + 1) * N);
-    static bool attr_done[64] = {};
-    if (!attr_done[c->device & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(k_fz<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[c->device & 63] = true;
-    }
-    dim3 grid(c->g.n[1] / kLines, c->g.n[0] / 2 + 1);
+template <int N, int F>
+cudaError_t run_fz_f(ftr_ctx* c) {
+    using X = Xchg<N, F>;
+    const size_t smem = sizeof(float2) * (X::SIZE + (F + 1) * N);
+    cudaError_t e = ensure_smem(k_fz<N, F>, smem, c->device);
+    if (e != cudaSuccess) return e;
+    dim3 grid(c->g.n[1] / F, c->g.n[0] / 2 + 1);
     const double two_pi = 2.0 * 3.14159265358979323846;
     const float wx = (float)(two_pi / (c->g.n[0] * c->g.h[0]));
     const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
     const float wz = (float)(two_pi / (c->g.n[2] * c->g.h[2]));
     const float inv_m = (float)(1.0 / (double)c->M);
-    k_fz<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
+    k_fz<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
                                                        c->d_meta);
     c->launches++;
     return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t run_fz(ftr_ctx* c) {
+    switch (c->plan_lines[1]) {
+        case 8: return run_fz_f<N, 8>(c);
+        case 32: return run_fz_f<N, 32>(c);
+        default: return run_fz_f<N, 16>(c);
+    }
 }
 
 }  // namespace

@@ -10,19 +10,18 @@
 namespace ftr {
 namespace {
 
-constexpr int kLines = 16;
-
-template <int N>
-__global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
+// F lines per CTA (the tile plan; 8, 16 or 32).
+template <int N, int F>
+__global__ void __launch_bounds__(F * Xchg<N, F>::NT)
     k_iy(GridDev g, const float2* __restrict__ src, float2* __restrict__ dst, const float2* __restrict__ tw) {
-    using X = Xchg<N, kLines>;
+    using X = Xchg<N, F>;
     extern __shared__ float2 smem[];
     const int nz = g.n[2];
-    const int z0 = blockIdx.x * kLines;
+    const int z0 = blockIdx.x * F;
     const int kx = blockIdx.y;
     const int tid = threadIdx.x;
     // step 1: line index fastest (the input is contiguous along z)
-    const int f1 = tid % kLines, j1 = tid / kLines;
+    const int f1 = tid % F, j1 = tid / F;
     if (j1 < X::N2) {
         float2 v[X::N1];
 #pragma unroll
@@ -30,34 +29,39 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
             const int ky = X::N2 * n1 + j1;
             v[n1] = src[(size_t)(z0 + f1) + (size_t)nz * ((size_t)ky + (size_t)N * kx)];
         }
-        fft_step1<N, kLines, +1>(v, f1, j1, smem, tw);
+        fft_step1<N, F, +1>(v, f1, j1, smem, tw);
     }
     __syncthreads();
     // step 2: element index fastest (the output is contiguous along y)
     const int f2 = tid / X::NT, i2 = tid % X::NT;
     if (i2 < X::N1) {
         float2 o[X::N2];
-        fft_step2<N, kLines, +1>(o, f2, i2, smem);
+        fft_step2<N, F, +1>(o, f2, i2, smem);
         float2* out = dst + (size_t)N * ((size_t)(z0 + f2) + (size_t)nz * kx);
 #pragma unroll
         for (int k2 = 0; k2 < X::N2; ++k2) out[i2 + X::N1 * k2] = o[k2];
     }
 }
 
-template <int N>
-cudaError_t run_iy(ftr_ctx* c) {
-    using X = Xchg<N, kLines>;
+template <int N, int F>
+cudaError_t run_iy_f(ftr_ctx* c) {
+    using X = Xchg<N, F>;
     const size_t smem = sizeof(float2) * X::SIZE;
-    static bool attr_done[64] = {};
-    if (!attr_done[c->device & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(k_iy<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_done[c->device & 63] = true;
-    }
-    dim3 grid(c->g.n[2] / kLines, c->g.n[0] / 2 + 1);
-    k_iy<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->d_s0, c->d_tw[1]);
+    cudaError_t e = ensure_smem(k_iy<N, F>, smem, c->device);
+    if (e != cudaSuccess) return e;
+    dim3 grid(c->g.n[2] / F, c->g.n[0] / 2 + 1);
+    k_iy<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->d_s0, c->d_tw[1]);
     c->launches++;
     return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t run_iy(ftr_ctx* c) {
+    switch (c->plan_lines[2]) {
+        case 8: return run_iy_f<N, 8>(c);
+        case 32: return run_iy_f<N, 32>(c);
+        default: return run_iy_f<N, 16>(c);
+    }
 }
 
 }  // namespace

@@ -116,6 +116,7 @@ struct ftr_ctx {
     float2* d_s1 = nullptr;    // 2 x Mh  [kx][ky][z]
     float* d_A = nullptr;      // M       [z][y][x]
     float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
+    int plan_lines[3] = {16, 16, 16};      // lines per CTA of the y, z and inverse-y passes
     unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
     int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
 

@@ -81,6 +81,9 @@ _SIGNATURES = [
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ftr_frame_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("ftr_device_bytes", ctypes.c_int64, [ctypes.c_void_p]),
+    ("ftr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_field_A", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -264,6 +267,25 @@ def ftr_device_bytes(ctx):
     return int(load().ftr_device_bytes(ctx))
 
 
+def ftr_autotune(ctx):
+    """Time the tile plans; returns the 3 x 3 microseconds per launch (rows: y,
+    z, inverse-y passes; columns: 8, 16, 32 lines per CTA; 0 = not timed)."""
+    rep = np.zeros(9, np.float32)
+    _check(load().ftr_autotune(ctx, rep.ctypes.data), ctx)
+    return rep.reshape(3, 3)
+
+
+def ftr_get_plan(ctx):
+    plan = np.zeros(3, np.int32)
+    _check(load().ftr_get_plan(ctx, plan.ctypes.data), ctx)
+    return tuple(int(v) for v in plan)
+
+
+def ftr_set_plan(ctx, plan):
+    arr = np.ascontiguousarray(plan, dtype=np.int32)
+    _check(load().ftr_set_plan(ctx, arr.ctypes.data), ctx)
+
+
 def ftr_last_error(ctx):
     return load().ftr_last_error(ctx).decode()
 
@@ -397,6 +419,15 @@ class Context:
 
     def stats(self):
         return ftr_stats(self.h)
+
+    def autotune(self):
+        return ftr_autotune(self.h)
+
+    def plan(self):
+        return ftr_get_plan(self.h)
+
+    def set_plan(self, plan):
+        ftr_set_plan(self.h, plan)
 
     def frame_info(self):
         return ftr_frame_info(self.h)

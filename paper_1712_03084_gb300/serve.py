@@ -10,7 +10,9 @@ run concurrently on the device.  Nothing here does reconstruction arithmetic:
 it only moves buffers and orders calls into the C ABI.
 
 * ``run_batch``: B frames of mixed grid sizes, one slot each, all submitted at
-  once; throughput against the same frames one after another.
+  once; throughput against the same frames one after another.  Each slot's
+  FFT tile plan is autotuned for its grid size when the slot is created
+  (``ftr_autotune``, cached per grid, so only the first slot of a size pays).
 * ``Server``: live sessions (each a camera rig with a grid size) are admitted
   while their device memory fits an HBM budget; frames arrive per session as
   a Poisson process; a frame is dispatched as soon as its session's slot is
@@ -76,6 +78,7 @@ class Slot:
         self.bbox = tuple(bbox)
         self.stream = torch.cuda.Stream(device=self.dev)
         self.ctx = ftr.Context(grid_n, bbox, stream=self.stream.cuda_stream)
+        self.ctx.autotune()           # tile plans: timed once per grid size, then cached
         self.point_cap = int(point_cap)
         z = dict(dtype=torch.float32, device=self.dev)
         self.P = torch.empty((self.point_cap, 3), **z)
