@@ -285,8 +285,6 @@ def run_ours(args, rank, world, local_rank):
     tol = depth_tol(cfg)
     stream = torch.cuda.Stream(device=dev)
     ctx = ftr.Context(grid, box, stream=stream.cuda_stream)
-    tune_us = ctx.autotune()          # tile plans of the y, z, inverse-y passes (cached per grid)
-    plan = ctx.plan()
     K = len(fr["views"])
 
     # device-resident inputs
@@ -339,6 +337,13 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_clocks:
         clocks.start()
         time.sleep(1.0)
+    with torch.cuda.stream(stream):
+        step()
+        finish()
+    # tile plans of the y, z and inverse-y passes, timed on this frame's live
+    # slab (cached per grid for the process), then the warm-up proper
+    tune_us = ctx.autotune()
+    plan = ctx.plan()
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             step()

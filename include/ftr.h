@@ -222,13 +222,17 @@ int64_t ftr_device_bytes(const ftr_ctx* ctx);
  * {8, 16, 32}; every plan computes bit-identical results (each line's
  * arithmetic does not depend on F), only the speed differs.
  *
- * ftr_autotune times the three F of each pass on this context's grid (a few
+ * ftr_autotune times each pass's candidate F on this context's grid (a few
  * launches each, on the context's own buffers, so no frame may be pending:
- * FTR_ESTATE) and keeps the fastest; the choice is cached per device and
- * grid for the process, so later contexts of the same grid take it without
- * timing.  report (nullable): 9 floats, microseconds per launch of F = 8, 16,
- * 32 for the y, z and inverse-y passes (0 = not timed: cached, or the
- * variant does not fit in shared memory).  Waits for the stream.  Split
+ * FTR_ESTATE; the last solved frame's live z-slab is used when there is one,
+ * else every plane; the fields of that frame are overwritten, so solve again
+ * before extracting) and keeps the fastest.  Candidates are the F that
+ * divide the grid and leave at least two CTAs resident per SM (one CTA that
+ * fills an SM stalls when other contexts' frames run concurrently).  The
+ * choice is cached per device and grid for the process: later contexts of
+ * the same grid take it without timing.  report (nullable): 9 floats,
+ * microseconds per launch of F = 8, 16, 32 for the y, z and inverse-y passes
+ * (0 = not timed: cached or not a candidate).  Waits for the stream.  Split
  * precision contexts keep F = 16 (their passes have no variants).
  */
 int ftr_autotune(ftr_ctx* ctx, float* report);

@@ -956,11 +956,14 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     }
     cudaError_t e;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_autotune");
-    // every z-plane live, so that the forward passes do their full work; the
-    // next splat rewrites these values
-    const int meta[4] = {c->n_bricks, 0, 0, c->g.nb[2] - 1};
-    if ((e = cudaMemcpyAsync(c->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-        return cuda_fail(c, e, "ftr_autotune");
+    // the live z-slab of the last solved frame when there is one (the forward
+    // passes skip planes outside it), else every plane live; a later splat
+    // rewrites these values
+    if (!c->solved) {
+        const int meta[4] = {c->n_bricks, 0, 0, c->g.nb[2] - 1};
+        if ((e = cudaMemcpyAsync(c->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "ftr_autotune");
+    }
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -973,6 +976,17 @@ int ftr_autotune(ftr_ctx* c, float* report) {
             if (!plan_fits(c, pass, F[v])) continue;
             c->plan_lines[pass] = F[v];
             auto run = [&]() { return pass == 0 ? launch_fy(c) : (pass == 1 ? launch_fz(c) : launch_iy(c)); };
+            // candidates keep at least two CTAs per SM: a CTA that fills an SM
+            // alone waits for a whole SM to drain when frames of other
+            // contexts run concurrently
+            int occ = 0;
+            c->occ_query = &occ;
+            const cudaError_t qe = run();
+            c->occ_query = nullptr;
+            if (qe != cudaSuccess || occ < 2) {
+                cudaGetLastError();
+                continue;
+            }
             if (run() != cudaSuccess) {     // the variant does not fit: skip it
                 cudaGetLastError();
                 continue;
@@ -999,6 +1013,8 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     c->graph_valid = false;
+    c->solved = false;       // the timing runs overwrote the spectra and the indicator
+    c->meshed = false;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         g_plans[key] = best;

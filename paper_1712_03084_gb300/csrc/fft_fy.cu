@@ -91,6 +91,8 @@ cudaError_t run_fy_f(ftr_ctx* c) {
     const size_t smem = sizeof(float2) * (X::SIZE + (F + 1) * N);
     cudaError_t e = ensure_smem(k_fy<N, F>, smem, c->device);
     if (e != cudaSuccess) return e;
+    if (c->occ_query)   // the autotuner asks how many CTAs of this plan fit on an SM
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(c->occ_query, k_fy<N, F>, F * X::NT, smem);
     dim3 grid(c->g.n[2] / F, c->g.n[0] / 2 + 1);
     const float wy_scale = (float)(2.0 * 3.14159265358979323846 / (c->g.n[1] * c->g.h[1]));
     k_fy<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,

@@ -97,6 +97,8 @@ cudaError_t run_fz_f(ftr_ctx* c) {
     const size_t smem = sizeof(float2) * (X::SIZE + (F + 1) * N);
     cudaError_t e = ensure_smem(k_fz<N, F>, smem, c->device);
     if (e != cudaSuccess) return e;
+    if (c->occ_query)   // the autotuner asks how many CTAs of this plan fit on an SM
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(c->occ_query, k_fz<N, F>, F * X::NT, smem);
     dim3 grid(c->g.n[1] / F, c->g.n[0] / 2 + 1);
     const double two_pi = 2.0 * 3.14159265358979323846;
     const float wx = (float)(two_pi / (c->g.n[0] * c->g.h[0]));

@@ -49,6 +49,8 @@ cudaError_t run_iy_f(ftr_ctx* c) {
     const size_t smem = sizeof(float2) * X::SIZE;
     cudaError_t e = ensure_smem(k_iy<N, F>, smem, c->device);
     if (e != cudaSuccess) return e;
+    if (c->occ_query)   // the autotuner asks how many CTAs of this plan fit on an SM
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(c->occ_query, k_iy<N, F>, F * X::NT, smem);
     dim3 grid(c->g.n[2] / F, c->g.n[0] / 2 + 1);
     k_iy<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->d_s0, c->d_tw[1]);
     c->launches++;

@@ -117,6 +117,7 @@ struct ftr_ctx {
     float* d_A = nullptr;      // M       [z][y][x]
     float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
     int plan_lines[3] = {16, 16, 16};      // lines per CTA of the y, z and inverse-y passes
+    int* occ_query = nullptr;              // set: the pass launchers report occupancy instead of launching
     unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
     int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
 
