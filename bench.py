@@ -541,7 +541,7 @@ def run_multi(args, rank, dev, plain_frame=None):
     srv = serve.Server(hbm_budget_bytes=120 * (1 << 30))
     admitted = [srv.admit(s) for s in sessions]
     live = srv.run(duration_s=2.0, seed=7 + rank)
-    sat = srv.run(duration_s=1.0, seed=8 + rank, saturate=True)
+    sat = srv.run(duration_s=3.0, seed=8 + rank, saturate=True)
     srv.close()
     out["served"] = {"sessions": len(sessions), "admitted": int(sum(admitted)), "hbm_gb": round(srv.used / 2 ** 30, 2),
                      "grids": [s.grid_n[0] for s in sessions], "cameras": [len(s.frames[0].views) for s in sessions],

@@ -267,6 +267,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         g.inv_h[a] = 1.0 / g.h[a];
         g.hf[a] = (float)g.h[a];
         g.inv_hf[a] = (float)g.inv_h[a];
+        g.inv_h_lo[a] = (float)(g.inv_h[a] - (double)g.inv_hf[a]);
         g.bminf[a] = bbox[a];
         diag2 += g.h[a] * g.h[a];
     }

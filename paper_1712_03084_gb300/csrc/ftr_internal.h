@@ -45,6 +45,7 @@ struct GridDev {
     double inv_h[3];
     float hf[3];
     float inv_hf[3];
+    float inv_h_lo[3];         // inv_h - (float)inv_h: 1/h as a float pair (inv_hf, inv_h_lo)
     float bminf[3];
     float inv_s1sq, inv_s2sq;  // 1/sigma1^2, 1/sigma2^2 (world units)
     double v_scale;            // sigma2/sigma1 (weighted) or 1 (simple)

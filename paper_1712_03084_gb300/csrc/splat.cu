@@ -6,7 +6,8 @@
 // over the 4^3 nodes floor(t)-1 .. floor(t)+2 around each point.  The grid is
 // cut into 8^3-node bricks; only bricks touched by some stencil get storage.
 // Per frame:
-//   ingest  point -> (floor t, t - floor t, W, N), acceptance test in FP64
+//   ingest  point -> (floor t, t - floor t, W, N); t as a float pair, the
+//           float64 path only within 1e-5 of a decision
 //   count   per point, +1 on every brick its stencil overlaps
 //   scan    one CTA: brick offsets, dense slot per touched brick
 //   fill    per point, append its index to each overlapped brick's list
@@ -42,6 +43,40 @@ __device__ __forceinline__ double node_t(double x, double bmin, double h, double
     return t;
 }
 
+// The same t without float64 arithmetic: x - b_min exactly as a sum of two
+// floats (two-sum), times 1/h held as a float pair, gives t = th + tl with an
+// error below 1e-11 for t < 2^9 (|tl| stays below ~5e-5).  The fraction
+// r = (th - floor th) + tl is rounded once (error < 6e-8); floor(t), the
+// nearest-node round-up and acceptance (floor(t) in [1, n - 3]) follow from
+// it.  Returns false when r lies within 1e-6 of 0, 1/2 or 1, where node_t
+// decides instead.
+__device__ __forceinline__ bool node_t_pair(float x, float bmin, float ih, float ih_lo, int& fl, float& fr,
+                                            bool& up) {
+    const float s = x - bmin;
+    const float bb = s - x;
+    const float e = (x - (s - bb)) + (-bmin - bb);
+    const float p = s * ih;
+    const float tl = fmaf(s, ih, -p) + fmaf(s, ih_lo, e * ih);
+    const float th = p - 0.5f;
+    if (!(fabsf(th) < 8388608.0f)) return false;   // NaN, inf or huge: float64 path
+    const float f = floorf(th);
+    float r = (th - f) + tl;                       // th - f is exact
+    int fi = (int)f;
+    const float band = 1e-6f;
+    if (fabsf(r) < band || fabsf(r - 1.0f) < band || fabsf(r - 0.5f) < band) return false;
+    if (r < 0.f) {
+        r += 1.0f;
+        fi -= 1;
+    } else if (r > 1.0f) {
+        r -= 1.0f;
+        fi += 1;
+    }
+    fl = fi;
+    fr = r;
+    up = r > 0.5f;
+    return true;
+}
+
 __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
                          float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
@@ -55,14 +90,28 @@ __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict_
     int up = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double t = node_t((double)pts[3 * i + c], g.bmin[c], g.h[c], g.inv_h[c], (double)g.n[c]);
-        bool in = (t >= 1.0) && (t < (double)g.n[c] - 2.0);   // false for NaN
-        ok = ok && in;
-        if (in) {
-            double f = floor(t);
-            fl[c] = (int)f;
-            fr[c] = (float)(t - f);
-            if (floor(t + 0.5) > f) up |= 1 << c;
+        const float x = pts[3 * i + c];
+        int fli;
+        float r;
+        bool u;
+        if (node_t_pair(x, g.bminf[c], g.inv_hf[c], g.inv_h_lo[c], fli, r, u)) {
+            const bool in = fli >= 1 && fli <= g.n[c] - 3;   // 1 <= t < n - 2
+            ok = ok && in;
+            if (in) {
+                fl[c] = fli;
+                fr[c] = r;
+                if (u) up |= 1 << c;
+            }
+        } else {
+            const double t = node_t((double)x, g.bmin[c], g.h[c], g.inv_h[c], (double)g.n[c]);
+            const bool in = (t >= 1.0) && (t < (double)g.n[c] - 2.0);   // false for NaN
+            ok = ok && in;
+            if (in) {
+                const double f = floor(t);
+                fl[c] = (int)f;
+                fr[c] = (float)(t - f);
+                if (floor(t + 0.5) > f) up |= 1 << c;
+            }
         }
     }
     if (!ok) {
