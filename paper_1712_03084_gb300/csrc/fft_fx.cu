@@ -23,6 +23,7 @@ template <int N>
 __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     k_fx(GridDev g, const int* __restrict__ slot_tab, const float* __restrict__ vpool, float2* __restrict__ s0,
          int64_t Mh, const float2* __restrict__ tw, float wx_scale, const int* __restrict__ meta) {
+    pdl_wait();
     using X = Xchg<N, kLines>;
     constexpr int NB = N / kBrick;
     constexpr int NKX = N / 2 + 1;
@@ -129,7 +130,7 @@ cudaError_t run_fx(ftr_ctx* c) {
     }
     dim3 grid(c->g.n[1] / kRows, c->g.n[2]);
     const float wx_scale = (float)(2.0 * 3.14159265358979323846 / (c->g.n[0] * c->g.h[0]));
-    k_fx<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_brick_slot, c->d_vpool, c->d_s0, c->Mh,
+    launch_pdl(k_fx<N>, grid, kLines * X::NT, smem, c->stream, c->g, c->d_brick_slot, c->d_vpool, c->d_s0, c->Mh,
                                                        c->d_tw[0], wx_scale, c->d_meta);
     c->launches++;
     return cudaGetLastError();

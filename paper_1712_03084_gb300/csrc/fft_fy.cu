@@ -30,6 +30,7 @@ template <int N, int F>
 __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     k_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
          const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta) {
+    pdl_wait();
     using X = Xchg<N, F>;
     extern __shared__ float2 smem[];
     const int nz = g.n[2];
@@ -95,7 +96,7 @@ cudaError_t run_fy_f(ftr_ctx* c) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(c->occ_query, k_fy<N, F>, F * X::NT, smem);
     dim3 grid(c->g.n[2] / F, c->g.n[0] / 2 + 1);
     const float wy_scale = (float)(2.0 * 3.14159265358979323846 / (c->g.n[1] * c->g.h[1]));
-    k_fy<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,
+    launch_pdl(k_fy<N, F>, grid, F * X::NT, smem, c->stream, c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,
                                                        c->d_meta);
     c->launches++;
     return cudaGetLastError();

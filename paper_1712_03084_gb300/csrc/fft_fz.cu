@@ -34,6 +34,7 @@ template <int N, int F>
 __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     k_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
          float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta) {
+    pdl_wait();
     using X = Xchg<N, F>;
     extern __shared__ float2 smem[];
     const int ny = g.n[1], nx = g.n[0];
@@ -105,7 +106,7 @@ cudaError_t run_fz_f(ftr_ctx* c) {
     const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
     const float wz = (float)(two_pi / (c->g.n[2] * c->g.h[2]));
     const float inv_m = (float)(1.0 / (double)c->M);
-    k_fz<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
+    launch_pdl(k_fz<N, F>, grid, F * X::NT, smem, c->stream, c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
                                                        c->d_meta);
     c->launches++;
     return cudaGetLastError();

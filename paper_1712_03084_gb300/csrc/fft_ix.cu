@@ -20,6 +20,7 @@ constexpr int kHs = kRows + 1;
 template <int N>
 __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     k_ix(GridDev g, const float2* __restrict__ src, float* __restrict__ A, const float2* __restrict__ tw) {
+    pdl_wait();
     using X = Xchg<N, kLines>;
     constexpr int NKX = N / 2 + 1;
     extern __shared__ float2 smem[];
@@ -82,7 +83,7 @@ cudaError_t run_ix(ftr_ctx* c) {
         attr_done[c->device & 63] = true;
     }
     dim3 grid(c->g.n[1] / kRows, c->g.n[2]);
-    k_ix<N><<<grid, kLines * X::NT, smem, c->stream>>>(c->g, c->d_s0, c->d_A, c->d_tw[0]);
+    launch_pdl(k_ix<N>, grid, kLines * X::NT, smem, c->stream, c->g, c->d_s0, c->d_A, c->d_tw[0]);
     c->launches++;
     return cudaGetLastError();
 }

@@ -14,6 +14,7 @@ namespace {
 template <int N, int F>
 __global__ void __launch_bounds__(F * Xchg<N, F>::NT)
     k_iy(GridDev g, const float2* __restrict__ src, float2* __restrict__ dst, const float2* __restrict__ tw) {
+    pdl_wait();
     using X = Xchg<N, F>;
     extern __shared__ float2 smem[];
     const int nz = g.n[2];
@@ -52,7 +53,7 @@ cudaError_t run_iy_f(ftr_ctx* c) {
     if (c->occ_query)   // the autotuner asks how many CTAs of this plan fit on an SM
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(c->occ_query, k_iy<N, F>, F * X::NT, smem);
     dim3 grid(c->g.n[2] / F, c->g.n[0] / 2 + 1);
-    k_iy<N, F><<<grid, F * X::NT, smem, c->stream>>>(c->g, c->d_s1, c->d_s0, c->d_tw[1]);
+    launch_pdl(k_iy<N, F>, grid, F * X::NT, smem, c->stream, c->g, c->d_s1, c->d_s0, c->d_tw[1]);
     c->launches++;
     return cudaGetLastError();
 }

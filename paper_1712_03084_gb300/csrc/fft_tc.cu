@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(kFxLines * Plan<N>::N1)
     k_tc_fx(GridDev g, const int* __restrict__ slot_tab, const float* __restrict__ vpool, float2* __restrict__ s0,
             int64_t Mh, const float2* __restrict__ tw, float wx_scale, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
+    pdl_wait();
     using E = Tc<N, kFxLines, P, true, false>;
     constexpr int N1 = E::N1, N2 = E::N2;
     constexpr int NB = N / kBrick;
@@ -410,6 +411,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     k_tc_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
             const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
+    pdl_wait();
     using E = Tc<N, kLines16, P, true, false>;
     constexpr int N1 = E::N1, N2 = E::N2;
     constexpr int F = kLines16;
@@ -461,6 +463,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     k_tc_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
             float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
+    pdl_wait();
     using E = Tc<N, kLines16, P, true, true>;
     constexpr int N1 = E::N1, N2 = E::N2;
     constexpr int F = kLines16;
@@ -523,6 +526,7 @@ template <int N, int P>
 __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     k_tc_iy(GridDev g, const float2* __restrict__ src, float2* __restrict__ dst, const float2* __restrict__ tw,
             const unsigned char* __restrict__ table, int* err) {
+    pdl_wait();
     using E = Tc<N, kLines16, P, false, true>;
     constexpr int N1 = E::N1, N2 = E::N2;
     constexpr int F = kLines16;
@@ -560,6 +564,7 @@ template <int N, int P>
 __global__ void __launch_bounds__(kIxLines * Plan<N>::N1)
     k_tc_ix(GridDev g, const float2* __restrict__ src, float* __restrict__ A, const float2* __restrict__ tw,
             const unsigned char* __restrict__ table, int* err) {
+    pdl_wait();
     using E = Tc<N, kIxLines, P, false, true>;
     constexpr int N1 = E::N1, N2 = E::N2;
     constexpr int NKX = N / 2 + 1;
@@ -640,7 +645,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             if (!launch) return cudaSuccess;
             dim3 grid(c->g.n[1] / kFxRows, c->g.n[2]);
             const float wx = (float)(two_pi / (c->g.n[0] * c->g.h[0]));
-            k_tc_fx<N, P><<<grid, E::T, smem, c->stream>>>(c->g, c->d_brick_slot, c->d_vpool, c->d_s0, c->Mh,
+            launch_pdl(k_tc_fx<N, P>, grid, E::T, smem, c->stream, c->g, c->d_brick_slot, c->d_vpool, c->d_s0, c->Mh,
                                                           c->d_tw[0], wx, c->d_meta, tab, err);
             break;
         }
@@ -651,7 +656,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             if (!launch) return cudaSuccess;
             dim3 grid(c->g.n[2] / kLines16, c->g.n[0] / 2 + 1);
             const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
-            k_tc_fy<N, P><<<grid, E::T, smem, c->stream>>>(c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy,
+            launch_pdl(k_tc_fy<N, P>, grid, E::T, smem, c->stream, c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy,
                                                           c->d_meta, tab, err);
             break;
         }
@@ -665,7 +670,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
             const float wz = (float)(two_pi / (c->g.n[2] * c->g.h[2]));
             const float inv_m = (float)(1.0 / (double)c->M);
-            k_tc_fz<N, P><<<grid, E::T, smem, c->stream>>>(c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
+            launch_pdl(k_tc_fz<N, P>, grid, E::T, smem, c->stream, c->g, c->d_s1, c->Mh, c->d_tw[2], wx, wy, wz, inv_m,
                                                           c->d_meta, tab, err);
             break;
         }
@@ -675,7 +680,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             if ((e = set_smem(k_tc_iy<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
             dim3 grid(c->g.n[2] / kLines16, c->g.n[0] / 2 + 1);
-            k_tc_iy<N, P><<<grid, E::T, smem, c->stream>>>(c->g, c->d_s1, c->d_s0, c->d_tw[1], tab, err);
+            launch_pdl(k_tc_iy<N, P>, grid, E::T, smem, c->stream, c->g, c->d_s1, c->d_s0, c->d_tw[1], tab, err);
             break;
         }
         default: {
@@ -684,7 +689,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             if ((e = set_smem(k_tc_ix<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
             dim3 grid(c->g.n[1] / kIxRows, c->g.n[2]);
-            k_tc_ix<N, P><<<grid, E::T, smem, c->stream>>>(c->g, c->d_s0, c->d_A, c->d_tw[0], tab, err);
+            launch_pdl(k_tc_ix<N, P>, grid, E::T, smem, c->stream, c->g, c->d_s0, c->d_A, c->d_tw[0], tab, err);
             break;
         }
     }

@@ -136,6 +136,7 @@ struct ftr_ctx {
     int mc_blocks = 0;             // grid rows n_y n_z
     int* d_mc_blk = nullptr;       // 3 x mc_blocks (per grid row: active nodes, vertices, triangles)
     int3* d_mc_tile = nullptr;     // tile sums / offsets of the chunk scan
+    unsigned* d_mc_bits = nullptr; // inside bits, 32 nodes per word, rows padded to a power-of-two word count
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
     int4* d_mc_nodes = nullptr;
@@ -181,6 +182,31 @@ struct ftr_ctx {
 
 namespace ftr {
 
+// Programmatic dependent launch.  Frame kernels are launched with
+// launch_pdl: the launch of the next kernel in the stream may overlap the
+// completion of its predecessor; every such kernel starts with pdl_wait()
+// (returns once the predecessor has completed and its writes are visible; a
+// no-op for a plain launch).  No kernel triggers its successor early: CTAs
+// parked in the wait would hold SM resources that concurrent frames on other
+// streams need.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // error helpers (api.cu)
 int set_err(ftr_ctx* c, int code, const char* fmt, ...);
 int cuda_fail(ftr_ctx* c, cudaError_t e, const char* what);
@@ -211,8 +237,9 @@ size_t tc_table_bytes();
 void tc_build_table(int precision, std::vector<unsigned char>& out);
 cudaError_t launch_tc_pass(ftr_ctx* c, int pass);
 cudaError_t tc_prepare(ftr_ctx* c);
-cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan; totals to h_mc_tot
+cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan
 cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
+cudaError_t launch_mc_totals(ftr_ctx* c);      // totals (active, verts, tris) to h_mc_tot
 cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);
 cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev);
 cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
                                                             const int64_t* __restrict__ npts,
                                                             const float* __restrict__ A, double* part,
                                                             unsigned* ticket, double* level, float* levelf) {
+    pdl_wait();
     __shared__ double sh[kThreads / 32];
     __shared__ bool last;
     const int nx = g.n[0];
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
 }  // namespace
 
 cudaError_t launch_level(ftr_ctx* c) {
-    k_level_partial<<<c->level_blocks, kThreads, 0, c->stream>>>(c->g, c->pts.base, c->pts.frac, c->d_npts, c->d_A,
+    launch_pdl(k_level_partial, c->level_blocks, kThreads, 0, c->stream, c->g, c->pts.base, c->pts.frac, c->d_npts, c->d_A,
                                                                  c->d_level_part, c->d_ticket, c->d_level,
                                                                  c->d_levelf);
     c->launches++;

@@ -81,6 +81,7 @@ __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict_
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
                          float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
                          int64_t* npts_dev) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *npts_dev = base + n;   // points stored so far: later kernels read the count here
     if (i >= n) return;
@@ -146,6 +147,7 @@ __device__ __forceinline__ bool stencil_bricks(const int4 b, int mode, int lo[3]
 // launch does not depend on it.
 __global__ void k_brick_count(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
                               int* cnt) {
+    pdl_wait();
     const int64_t n = *npts;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lo[3], hi[3];
@@ -158,6 +160,7 @@ __global__ void k_brick_count(const int4* __restrict__ pbase, const int64_t* __r
 
 __global__ void k_brick_fill(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
                              int* cursor, int* entries) {
+    pdl_wait();
     const int64_t n = *npts;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lo[3], hi[3];
@@ -214,6 +217,7 @@ __device__ __forceinline__ int2 block_scan2(int2 v, int2& total, int2* sh) {
 }
 
 __global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restrict__ cnt, int nb, int2* tile_sum) {
+    pdl_wait();
     __shared__ int2 sh[kScanT / 32];
     int2 v = make_int2(0, 0);
     for (int k = 0; k < kTile / kScanT; ++k) {
@@ -232,6 +236,7 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restric
 // One CTA: exclusive scan of the tile sums in place; totals into meta.
 __global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int2* tile_sum, int ntiles, int nb, int* off,
                                                             int* meta) {
+    pdl_wait();
     __shared__ int2 sh[kScanT / 32];
     int2 carry = make_int2(0, 0);
     for (int base = 0; base < ntiles; base += kScanT) {
@@ -255,6 +260,7 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int2* tile_sum, int 
 __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restrict__ cnt, int nb, int nbxy,
                                                              const int2* __restrict__ tile_off, int* off,
                                                              int* cursor, int* slot, int* active, int* meta) {
+    pdl_wait();
     __shared__ int2 sh[kScanT / 32];
     int2 run = tile_off[blockIdx.x];
     int zmin = 0x7fffffff, zmax = -1;
@@ -338,6 +344,7 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const float4* __restrict__ pnrm,
                                                              const int* __restrict__ wild_weights,
                                                              float* __restrict__ vpool) {
+    pdl_wait();
     __shared__ __align__(16) unsigned acc[8][kBrickVox];   // fast: [c] hi, [4 + c] lo; slow: 4 x int64
     __shared__ int4 s_base[kStage];
     __shared__ float4 s_frac[kStage];
@@ -487,7 +494,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n) {
     if (n == 0) return cudaSuccess;
     // small CTAs spread the few float64 operations per point over every SM
-    k_ingest<<<blocks_for(n, 32), 32, 0, c->stream>>>(pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
+    launch_pdl(k_ingest, blocks_for(n, 32), 32, 0, c->stream, pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
                                                        c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts);
     c->launches++;
     return cudaGetLastError();
@@ -500,24 +507,24 @@ cudaError_t launch_splat(ftr_ctx* c) {
     if (sms <= 0) sms = 152;
     prof_begin(c, ST_SPLAT_BIN);
     if ((e = cudaMemsetAsync(c->d_brick_cnt, 0, sizeof(int) * c->n_bricks, c->stream)) != cudaSuccess) return e;
-    k_brick_count<<<sms * 2, 256, 0, c->stream>>>(c->pts.base, c->d_npts, c->g, c->d_brick_cnt);
+    launch_pdl(k_brick_count, sms * 2, 256, 0, c->stream, c->pts.base, c->d_npts, c->g, c->d_brick_cnt);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ntiles = (c->n_bricks + kTile - 1) / kTile;
-    k_brick_tile_sums<<<ntiles, kScanT, 0, c->stream>>>(c->d_brick_cnt, c->n_bricks, c->d_tile);
-    k_brick_tile_scan<<<1, kScanT, 0, c->stream>>>(c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta);
-    k_brick_tile_write<<<ntiles, kScanT, 0, c->stream>>>(c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
+    launch_pdl(k_brick_tile_sums, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->d_tile);
+    launch_pdl(k_brick_tile_scan, 1, kScanT, 0, c->stream, c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta);
+    launch_pdl(k_brick_tile_write, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
                                                         c->d_tile, c->d_brick_off, c->d_brick_cursor,
                                                         c->d_brick_slot, c->d_active, c->d_meta);
     c->launches += 3;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_brick_fill<<<sms * 2, 256, 0, c->stream>>>(c->pts.base, c->d_npts, c->g, c->d_brick_cursor, c->d_entries);
+    launch_pdl(k_brick_fill, sms * 2, 256, 0, c->stream, c->pts.base, c->d_npts, c->g, c->d_brick_cursor, c->d_entries);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     prof_end(c, ST_SPLAT_BIN);
     prof_begin(c, ST_SPLAT_ACC);
     const int grid = sms * 4;
-    k_splat_accum<<<grid, kAccThreads, 0, c->stream>>>(c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
+    launch_pdl(k_splat_accum, grid, kAccThreads, 0, c->stream, c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
                                                        c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool);
     c->launches++;
     prof_end(c, ST_SPLAT_ACC);

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
                                                  const int* __restrict__ nv_dev, double tau,
                                                  float* __restrict__ wout, float* __restrict__ uvout,
                                                  uint8_t* __restrict__ rgbout, uint8_t* __restrict__ texout) {
+    pdl_wait();
     if (nv_dev) nv = min(nv, (int64_t)nv_dev[0]);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / G;
@@ -177,10 +178,10 @@ cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t 
     const unsigned blocks = (unsigned)((nv * G + 255) / 256);
     const double tau = (double)depth_tol;
     switch (G) {
-        case 1: k_texture<1><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
-        case 2: k_texture<2><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
-        case 4: k_texture<4><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
-        default: k_texture<8><<<blocks, 256, 0, c->stream>>>(vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 1: launch_pdl(k_texture<1>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 2: launch_pdl(k_texture<2>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 4: launch_pdl(k_texture<4>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        default: launch_pdl(k_texture<8>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
     }
     c->launches++;
     prof_end(c, ST_TEXTURE);
