@@ -202,6 +202,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_ticket);
     dfree(c->d_mc_blk);
     dfree(c->d_mc_tile);
+    dfree(c->d_mc_bits);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
     dfree(c->d_mc_nodes);
@@ -320,6 +321,11 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     c->mc_blocks = grid_n[1] * grid_n[2];      // marching cubes counts per grid row
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
     ALLOC(c->d_mc_tile, (c->mc_blocks + 2047) / 2048 + 1);
+    {
+        int wp = 1;
+        while (wp < (grid_n[0] + 31) / 32) wp <<= 1;
+        ALLOC(c->d_mc_bits, (size_t)c->mc_blocks * wp);
+    }
     ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
 #undef ALLOC
     if ((e = cudaMallocHost((void**)&c->h_mc_tot, 4 * sizeof(int))) != cudaSuccess) {
@@ -536,6 +542,7 @@ int ftr_extract_mesh(ftr_ctx* c, ftr_mesh* out) {
     // counts, offsets and the emission run back to back; the host waits once
     if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: count");
     if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
+    if ((e = launch_mc_totals(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: totals");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
     if (int st = tc_check(c, "ftr_extract_mesh")) return st;
     const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
@@ -715,8 +722,9 @@ cudaError_t enqueue_frame(ftr_ctx* c, const ViewSet& vs, float tol, const ftr_te
         const int64_t limit = out_capacity < c->cap_verts ? out_capacity : c->cap_verts;
         e = launch_texture_bounded(c, vs, tol, limit, c->d_mc_off + 3 * (c->mc_blocks + 1) + 1, out.weights, out.uv,
                                    out.rgb, out.textured);
+        if (e != cudaSuccess) return e;
     }
-    return e;
+    return launch_mc_totals(c);
 }
 
 }  // namespace
@@ -798,6 +806,7 @@ int ftr_extract_mesh_async(ftr_ctx* c) {
     }
     if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: count");
     if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: emit");
+    if ((e = launch_mc_totals(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: totals");
     c->meshed = false;
     c->mesh_pending = true;
     c->tex_pending = false;
@@ -1037,6 +1046,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     if (c->d_tc_table) b += (int64_t)tc_table_bytes() + 16;
     b += (2 * c->level_blocks + 8) * (int64_t)sizeof(double);
     b += (6 * (int64_t)c->mc_blocks + 16) * (int64_t)sizeof(int);
+    b += (int64_t)c->mc_blocks * 16 * (int64_t)sizeof(unsigned);   // inside bits (upper bound)
     b += c->cap_mc_nodes * (int64_t)sizeof(int4) + c->cap_verts * 6 * (int64_t)sizeof(float) +
          c->cap_tris * 3 * (int64_t)sizeof(int32_t);
     return b;

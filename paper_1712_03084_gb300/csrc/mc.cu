@@ -8,22 +8,25 @@
 // triangles follow cell order then table order, so the mesh does not depend
 // on scheduling.
 //
-// One warp walks one grid row (y, z) in 32-node segments.  Per segment it
-// loads the rows (y, z), (y+1, z), (y, z+1), (y+1, z+1) once, turns them into
-// four 32-bit ballots, and reads every node's edge bits and cube class from
-// those masks (the +x neighbour is the next bit; lane 31 fetches the first
-// node of the next segment).  Launches:
+// The inside bits are computed once (one warp per grid row, one ballot per
+// 32 nodes: 1 bit per node, 2 MB at 256^3) and both passes below work on
+// 32-node words: a thread takes word w of row (y, z) and the same word of
+// the rows (y+1, z), (y, z+1), (y+1, z+1); XORs give the crossing edges
+// toward +x, +y, +z and AND/OR of the eight corner masks the cells whose
+// corners differ (exactly the cells with triangles).  Launches:
+//   bits   the inside bits of every node
 //   count  per row: active nodes (owning a vertex or lower corner of a cell
 //          with triangles), vertices, triangles
 //   scan   three coalesced launches: exclusive offsets of the row counts
-//   emit   rows with surface only: one 16-byte record per active node (node,
-//          edge bits | class << 8, first vertex, first triangle), vertex
-//          positions t = (L - A0)/(A1 - A0) in float64 and normals -grad A
-//          (central differences, one-sided at the border, lerped); in-row
-//          offsets come from ballot popcounts
+//   emit   rows with surface only: per word an exclusive prefix over the
+//          row's words, then its active nodes in x order: one 16-byte
+//          record per node (node, edge bits | class << 8, first vertex,
+//          first triangle), vertex positions t = (L - A0)/(A1 - A0) and
+//          normals -grad A (central differences, one-sided at the border,
+//          lerped)
 //   tris   one thread per active node: triangle corners from the case table;
-//          an edge owned by another node is found by binary search in the
-//          sorted node records.
+//          an edge owned by another node is found by a short scan of that
+//          node's row records.
 #include <cuda_runtime.h>
 
 #include "ftr_internal.h"
@@ -65,162 +68,117 @@ __device__ __forceinline__ NodeInfo classify_node(const float* __restrict__ A, i
 
 constexpr int kRowsPerCta = kMcThreads / 32;
 
-// One 128-node segment of row (y, z) starting at x0: lane l holds nodes
-// x0 + 4l .. x0 + 4l + 3.  bits[r] packs, for the rows r = (y,z), (y+1,z),
-// (y,z+1), (y+1,z+1), bit j = (A >= L) at node j of the lane and bit 4 = the
-// same at the lane's +x neighbour of node 3.
-struct Seg4 {
-    int bits[4];
-};
-
-__device__ __forceinline__ int nib(float4 v, float L) {
-    return (v.x >= L) | ((v.y >= L) << 1) | ((v.z >= L) << 2) | ((v.w >= L) << 3);
-}
-
-__device__ __forceinline__ Seg4 seg_load(const float* __restrict__ A, int64_t rowbase, int x0, int nx,
-                                         int64_t sy, int64_t sz, bool hy, bool hz, float L) {
-    const int lane = threadIdx.x & 31;
-    const int x = x0 + 4 * lane;
-    const bool valid = x < nx;
-    const float4* p = reinterpret_cast<const float4*>(A + rowbase + x);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 r00 = valid ? p[0] : z4;
-    const float4 r10 = (valid && hy) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy) : z4;
-    const float4 r01 = (valid && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sz) : z4;
-    const float4 r11 = (valid && hy && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy + sz) : z4;
-    Seg4 s;
-    s.bits[0] = valid ? nib(r00, L) : 0;
-    s.bits[1] = (valid && hy) ? nib(r10, L) : 0;
-    s.bits[2] = (valid && hz) ? nib(r01, L) : 0;
-    s.bits[3] = (valid && hy && hz) ? nib(r11, L) : 0;
-    // +x neighbour of node 3: the next lane's node 0, or the next segment's
-    // first node for lane 31
-    int nb[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) nb[r] = __shfl_down_sync(0xffffffffu, s.bits[r], 1) & 1;
-    if (lane == 31) {
-        const int64_t n = rowbase + x + 4;
-        const bool more = x + 4 < nx;
-        nb[0] = more && A[n] >= L;
-        nb[1] = more && hy && A[n + sy] >= L;
-        nb[2] = more && hz && A[n + sz] >= L;
-        nb[3] = more && hy && hz && A[n + sy + sz] >= L;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) s.bits[r] |= nb[r] << 4;
-    return s;
-}
-
-// Edge bits and cube class of node j (0..3) of this lane.
-__device__ __forceinline__ NodeInfo seg_node(const Seg4& s, int j, int x, int nx, bool hy, bool hz) {
-    const bool hx = x < nx - 1;
-    const int b0 = (s.bits[0] >> j) & 1, bx = (s.bits[0] >> (j + 1)) & 1;
-    const int by = (s.bits[1] >> j) & 1, bxy = (s.bits[1] >> (j + 1)) & 1;
-    const int bz = (s.bits[2] >> j) & 1, bxz = (s.bits[2] >> (j + 1)) & 1;
-    const int byz = (s.bits[3] >> j) & 1, bxyz = (s.bits[3] >> (j + 1)) & 1;
-    NodeInfo r;
-    r.flags = (hx && bx != b0) | ((hy && by != b0) << 1) | ((hz && bz != b0) << 2);
-    r.cls = (hx && hy && hz)
-                ? (b0 | (bx << 1) | (by << 2) | (bxy << 3) | (bz << 4) | (bxz << 5) | (byz << 6) | (bxyz << 7))
-                : 0;
-    return r;
-}
-
 __device__ __forceinline__ int ntri_of(int cls) { return (cls == 0 || cls == 255) ? 0 : c_ntri[cls]; }
 
-// Loads of one segment (issued before any of them is used).
-struct SegLoads {
-    float4 r00, r10, r01, r11;
-    float e[4];
-};
-
-__device__ __forceinline__ SegLoads seg_issue(const float* __restrict__ A, int64_t rowbase, int x0, int nx,
-                                              int64_t sy, int64_t sz, bool hy, bool hz) {
-    const int lane = threadIdx.x & 31;
-    const int x = x0 + 4 * lane;
-    const bool valid = x < nx;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    SegLoads l;
-    l.r00 = valid ? *reinterpret_cast<const float4*>(A + rowbase + x) : z4;
-    l.r10 = (valid && hy) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy) : z4;
-    l.r01 = (valid && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sz) : z4;
-    l.r11 = (valid && hy && hz) ? *reinterpret_cast<const float4*>(A + rowbase + x + sy + sz) : z4;
-    const bool more = lane == 31 && x + 4 < nx;
-    const int64_t n = rowbase + x + 4;
-    l.e[0] = more ? A[n] : 0.f;
-    l.e[1] = (more && hy) ? A[n + sy] : 0.f;
-    l.e[2] = (more && hz) ? A[n + sz] : 0.f;
-    l.e[3] = (more && hy && hz) ? A[n + sy + sz] : 0.f;
-    return l;
-}
-
-__device__ __forceinline__ Seg4 seg_bits_of(const SegLoads& l, int x0, int nx, bool hy, bool hz, float L) {
-    const int lane = threadIdx.x & 31;
-    const int x = x0 + 4 * lane;
-    const bool valid = x < nx;
-    Seg4 s;
-    s.bits[0] = valid ? nib(l.r00, L) : 0;
-    s.bits[1] = (valid && hy) ? nib(l.r10, L) : 0;
-    s.bits[2] = (valid && hz) ? nib(l.r01, L) : 0;
-    s.bits[3] = (valid && hy && hz) ? nib(l.r11, L) : 0;
-    int nb[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) nb[r] = __shfl_down_sync(0xffffffffu, s.bits[r], 1) & 1;
-    if (lane == 31) {
-        const bool more = x + 4 < nx;
-        nb[0] = more && l.e[0] >= L;
-        nb[1] = more && hy && l.e[1] >= L;
-        nb[2] = more && hz && l.e[2] >= L;
-        nb[3] = more && hy && hz && l.e[3] >= L;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) s.bits[r] |= nb[r] << 4;
-    return s;
-}
-
-template <int SEGS>
-__global__ void __launch_bounds__(kMcThreads) k_mc_count(GridDev g, const float* __restrict__ A,
-                                                         const float* __restrict__ levelf, int* __restrict__ cnt,
-                                                         int nrows) {
-    const float L = levelf[0];
+// ---------------------------------------------------------------- bit masks
+// The inside bits (A >= L) of every node, 32 per word: word w of grid row r
+// (y + n_y z) holds x = 32 w .. 32 w + 31 (bit i = node 32 w + i; zero past
+// n_x); rows are `wp` words apart (wp = the words per row rounded up to a
+// power of two).  One warp per row, one ballot per word.
+__global__ void __launch_bounds__(kMcThreads) k_mc_bits(GridDev g, const float* __restrict__ A,
+                                                        const float* __restrict__ levelf, unsigned* __restrict__ bits,
+                                                        int nrows, int wp) {
+    pdl_wait();
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows) return;                    // warp-uniform
     const int lane = threadIdx.x & 31;
+    const float L = levelf[0];
+    const int nx = g.n[0];
+    const float* a = A + (int64_t)row * nx;
+    const int nw = (nx + 31) >> 5;
+    unsigned mine = 0u;
+    for (int w = 0; w < nw; ++w) {
+        const int x = 32 * w + lane;
+        const bool in = x < nx && a[x] >= L;
+        const unsigned b = __ballot_sync(0xffffffffu, in);
+        if (lane == w) mine = b;
+    }
+    if (lane < wp) bits[(int64_t)row * wp + lane] = lane < nw ? mine : 0u;
+}
+
+// Per (row, word): the masks of the nodes of word w that own a crossing
+// edge toward +x, +y, +z, and that are the lower corner of a cell whose
+// corners are not all on one side ("mixed": exactly the cells with
+// triangles).  Nodes with any of the four are the row's active nodes.
+struct WordMasks {
+    unsigned ex, ey, ez, mixed;
+    unsigned c[8];   // corner bits of the cells whose lower corner is in the word
+};
+
+__device__ __forceinline__ WordMasks word_masks(const unsigned* __restrict__ bits, int row, int w, int nw, int wp,
+                                                int x_count, bool hy, bool hz, int ny) {
+    const int64_t r00 = (int64_t)row * wp, r10 = r00 + wp, r01 = r00 + (int64_t)ny * wp, r11 = r01 + wp;
+    const bool more = w + 1 < nw;
+    const unsigned b00 = bits[r00 + w], n00 = more ? bits[r00 + w + 1] : 0u;
+    const unsigned b10 = hy ? bits[r10 + w] : 0u, n10 = (hy && more) ? bits[r10 + w + 1] : 0u;
+    const unsigned b01 = hz ? bits[r01 + w] : 0u, n01 = (hz && more) ? bits[r01 + w + 1] : 0u;
+    const unsigned b11 = (hy && hz) ? bits[r11 + w] : 0u, n11 = (hy && hz && more) ? bits[r11 + w + 1] : 0u;
+    // nodes of the word that exist, and those with a +x neighbour
+    const int base = 32 * w;
+    const unsigned valid = x_count - base >= 32 ? 0xffffffffu : ((1u << (x_count - base)) - 1u);
+    const unsigned vx = x_count - 1 - base >= 32 ? 0xffffffffu
+                        : (x_count - 1 - base <= 0 ? 0u : ((1u << (x_count - 1 - base)) - 1u));
+    WordMasks m;
+    m.c[0] = b00;
+    m.c[1] = (b00 >> 1) | (n00 << 31);
+    m.c[2] = b10;
+    m.c[3] = (b10 >> 1) | (n10 << 31);
+    m.c[4] = b01;
+    m.c[5] = (b01 >> 1) | (n01 << 31);
+    m.c[6] = b11;
+    m.c[7] = (b11 >> 1) | (n11 << 31);
+    m.ex = (m.c[0] ^ m.c[1]) & vx;
+    m.ey = hy ? ((b00 ^ b10) & valid) : 0u;
+    m.ez = hz ? ((b00 ^ b01) & valid) : 0u;
+    unsigned all = 0xffffffffu, any = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        all &= m.c[k];
+        any |= m.c[k];
+    }
+    m.mixed = (hy && hz) ? ((any & ~all) & vx) : 0u;
+    return m;
+}
+
+__device__ __forceinline__ int cell_class(const WordMasks& m, int i) {
+    int cls = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cls |= (int)((m.c[k] >> i) & 1u) << k;
+    return cls;
+}
+
+// Thread per (row, word), rows in groups of wp lanes: active nodes, vertices
+// and triangles of the row.
+__global__ void __launch_bounds__(kMcThreads) k_mc_count_bits(GridDev g, const unsigned* __restrict__ bits,
+                                                              int* __restrict__ cnt, int nrows, int wp) {
+    pdl_wait();
+    __shared__ unsigned char s_ntri[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(t / wp), w = (int)(t % wp);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int y = row % ny, z = row / ny;
-    const bool hy = y < ny - 1, hz = z < nz - 1;
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const int64_t rowbase = (int64_t)row * nx;
-    SegLoads ld[SEGS];
-#pragma unroll
-    for (int k = 0; k < SEGS; ++k) ld[k] = seg_issue(A, rowbase, 128 * k, nx, sy, sz, hy, hz);
+    const int nw = (nx + 31) >> 5;
     int na = 0, nv = 0, nt = 0;
-#pragma unroll
-    for (int k = 0; k < SEGS; ++k) {
-        const int x0 = 128 * k;
-        const Seg4 sb = seg_bits_of(ld[k], x0, nx, hy, hz, L);
-        const int xl = x0 + 4 * lane;
-        // all four rows agree on all five bits: no edge or cell changes here
-        const int all = sb.bits[0] & sb.bits[1] & sb.bits[2] & sb.bits[3];
-        const int any = sb.bits[0] | sb.bits[1] | sb.bits[2] | sb.bits[3];
-        if (xl < nx && !(all == 0x1f || any == 0)) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const NodeInfo ni = seg_node(sb, j, xl + j, nx, hy, hz);
-                const int t = ntri_of(ni.cls);
-                na += (ni.flags != 0 || t > 0);
-                nv += __popc(ni.flags);
-                nt += t;
-            }
+    if (row < nrows && w < nw) {
+        const int y = row % ny, z = row / ny;
+        const WordMasks m = word_masks(bits, row, w, nw, wp, nx, y < ny - 1, z < nz - 1, ny);
+        na = __popc(m.ex | m.ey | m.ez | m.mixed);
+        nv = __popc(m.ex) + __popc(m.ey) + __popc(m.ez);
+        unsigned mm = m.mixed;
+        while (mm) {
+            const int i = __ffs(mm) - 1;
+            mm &= mm - 1;
+            nt += s_ntri[cell_class(m, i)];
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        na += __shfl_down_sync(0xffffffffu, na, o);
-        nv += __shfl_down_sync(0xffffffffu, nv, o);
-        nt += __shfl_down_sync(0xffffffffu, nt, o);
+    // sum over the wp lanes of the row (aligned groups inside a warp)
+    for (int o = 1; o < wp; o <<= 1) {
+        na += __shfl_xor_sync(0xffffffffu, na, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        nt += __shfl_xor_sync(0xffffffffu, nt, o);
     }
-    if (lane == 0) {
+    if (w == 0 && row < nrows) {
         cnt[row] = na;
         cnt[nrows + row] = nv;
         cnt[2 * nrows + row] = nt;
@@ -272,6 +230,7 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
 constexpr int kScanTile = 2048;
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_tile_sums(const int* __restrict__ blk, int nb, int3* tile) {
+    pdl_wait();
     __shared__ int3 sh[kMcThreads / 32];
     int3 v = make_int3(0, 0, 0);
     for (int k = 0; k < kScanTile / kMcThreads; ++k) {
@@ -288,6 +247,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_tile_sums(const int* __restri
 }
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_tile_scan(int3* tile, int ntiles, int nb, int* off) {
+    pdl_wait();
     __shared__ int3 sh[kMcThreads / 32];
     int3 carry = make_int3(0, 0, 0);
     for (int base = 0; base < ntiles; base += kMcThreads) {
@@ -312,6 +272,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_tile_scan(int3* tile, int nti
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_tile_write(const int* __restrict__ blk, int nb,
                                                               const int3* __restrict__ tile, int* off) {
+    pdl_wait();
     __shared__ int3 sh[kMcThreads / 32];
     int3 run = tile[blockIdx.x];
     for (int k = 0; k < kScanTile / kMcThreads; ++k) {
@@ -378,76 +339,79 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
     }
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_emit(GridDev g, const float* __restrict__ A,
-                                                        const float* __restrict__ levelf,
-                                                        const int* __restrict__ cnt, const int* __restrict__ off,
-                                                        int nrows, int4* __restrict__ nodes, int cap_nodes,
-                                                        float* __restrict__ verts, float* __restrict__ vnrm,
-                                                        int cap_v) {
-    const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
-    if (row >= nrows || cnt[row] == 0) return;   // warp-uniform: no surface on this row
-    const int lane = threadIdx.x & 31;
-    const float L = levelf[0];
-    const float Ln = levelf[1];
+// Thread per (row, word) in groups of wp lanes, rows with surface only: the
+// group's exclusive prefix of (active nodes, vertices, triangles) plus the
+// row offsets give every thread its output positions; it then walks its
+// active nodes in x order writing the node record (node, edge bits | class
+// << 8, first vertex, first triangle) and the vertices of its crossing edges.
+__global__ void __launch_bounds__(kMcThreads) k_mc_emit_bits(GridDev g, const float* __restrict__ A,
+                                                             const unsigned* __restrict__ bits,
+                                                             const float* __restrict__ levelf,
+                                                             const int* __restrict__ cnt, const int* __restrict__ off,
+                                                             int nrows, int wp, int4* __restrict__ nodes,
+                                                             int cap_nodes, float* __restrict__ verts,
+                                                             float* __restrict__ vnrm, int cap_v) {
+    pdl_wait();
+    __shared__ unsigned char s_ntri[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = (int)(t / wp), w = (int)(t % wp);
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int nw = (nx + 31) >> 5;
+    const bool live = row < nrows && cnt[row] > 0;      // the same for the whole group
     const int y = row % ny, z = row / ny;
-    const bool hy = y < ny - 1, hz = z < nz - 1;
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    WordMasks m;
+    unsigned act = 0u;
+    int ca = 0, cv = 0, ct = 0;
+    if (live && w < nw) {
+        m = word_masks(bits, row, w, nw, wp, nx, y < ny - 1, z < nz - 1, ny);
+        act = m.ex | m.ey | m.ez | m.mixed;
+        ca = __popc(act);
+        cv = __popc(m.ex) + __popc(m.ey) + __popc(m.ez);
+        unsigned mm = m.mixed;
+        while (mm) {
+            const int i = __ffs(mm) - 1;
+            mm &= mm - 1;
+            ct += s_ntri[cell_class(m, i)];
+        }
+    }
+    // inclusive prefix inside the group (all lanes of the warp take part)
+    int pa = ca, pv = cv, pt = ct;
+    const int gl = (int)(threadIdx.x & 31) % wp;
+    for (int o = 1; o < wp; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, pa, o, wp);
+        const int b = __shfl_up_sync(0xffffffffu, pv, o, wp);
+        const int c = __shfl_up_sync(0xffffffffu, pt, o, wp);
+        if (gl >= o) {
+            pa += a;
+            pv += b;
+            pt += c;
+        }
+    }
+    if (!act) return;
+    const float Ln = levelf[1];
+    int ja = off[row] + pa - ca;
+    int jv = off[(nrows + 1) + row] + pv - cv;
+    int jt = off[2 * (nrows + 1) + row] + pt - ct;
     const int64_t rowbase = (int64_t)row * nx;
-    int ia = off[row];
-    int iv = off[(nrows + 1) + row];
-    int it = off[2 * (nrows + 1) + row];
-    for (int x0 = 0; x0 < nx; x0 += 128) {
-        const Seg4 sb = seg_load(A, rowbase, x0, nx, sy, sz, hy, hz, L);
-        const int xl = x0 + 4 * lane;
-        NodeInfo ni[4];
-        int ca = 0, cv = 0, ct = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            ni[j].flags = 0;
-            ni[j].cls = 0;
-            if (xl < nx) ni[j] = seg_node(sb, j, xl + j, nx, hy, hz);
-            const int t = ntri_of(ni[j].cls);
-            ca += (ni[j].flags != 0 || t > 0);
-            cv += __popc(ni[j].flags);
-            ct += t;
+    unsigned rem = act;
+    while (rem) {
+        const int i = __ffs(rem) - 1;
+        rem &= rem - 1;
+        const int x = 32 * w + i;
+        const int flags = (int)((m.ex >> i) & 1u) | ((int)((m.ey >> i) & 1u) << 1) | ((int)((m.ez >> i) & 1u) << 2);
+        const int cls = ((m.mixed >> i) & 1u) ? cell_class(m, i) : 0;
+        const int ntr = cls ? s_ntri[cls] : 0;
+        const int64_t n = rowbase + x;
+        if (ja < cap_nodes) nodes[ja] = make_int4((int)n, flags | (cls << 8), jv, jt);
+        ++ja;
+        if (flags) {
+            const int q[3] = {x, y, z};
+            emit_vertices(g, A, Ln, n, q, flags, jv, cap_v, verts, vnrm);
         }
-        // exclusive prefix over lanes (x order), then in-lane order j
-        int pa = ca, pv = cv, pt = ct;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int a = __shfl_up_sync(0xffffffffu, pa, o);
-            const int b = __shfl_up_sync(0xffffffffu, pv, o);
-            const int c = __shfl_up_sync(0xffffffffu, pt, o);
-            if (lane >= o) {
-                pa += a;
-                pv += b;
-                pt += c;
-            }
-        }
-        const int ta = __shfl_sync(0xffffffffu, pa, 31);
-        const int tv = __shfl_sync(0xffffffffu, pv, 31);
-        const int tt = __shfl_sync(0xffffffffu, pt, 31);
-        int ja = ia + pa - ca, jv = iv + pv - cv, jt = it + pt - ct;
-        if (ca > 0) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int t = ntri_of(ni[j].cls);
-                if (ni[j].flags == 0 && t == 0) continue;
-                const int64_t n = rowbase + xl + j;
-                if (ja < cap_nodes) nodes[ja] = make_int4((int)n, ni[j].flags | (ni[j].cls << 8), jv, jt);
-                ++ja;
-                if (ni[j].flags) {
-                    const int q[3] = {xl + j, y, z};
-                    emit_vertices(g, A, Ln, n, q, ni[j].flags, jv, cap_v, verts, vnrm);
-                }
-                jv += __popc(ni[j].flags);
-                jt += t;
-            }
-        }
-        ia += ta;
-        iv += tv;
-        it += tt;
+        jv += __popc(flags);
+        jt += ntr;
     }
 }
 
@@ -491,6 +455,7 @@ __device__ __forceinline__ void tris_of_node(const GridDev& g, const int4* __res
 __global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restrict__ nodes,
                                                  const int* __restrict__ totals, int cap_nodes, int cap_tris,
                                                  const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
+    pdl_wait();
     const int n_nodes = totals[0];
     if (n_nodes > cap_nodes || totals[2] > cap_tris) return;   // the host grows the buffers and runs again
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_nodes; r += gridDim.x * blockDim.x)
@@ -526,40 +491,55 @@ cudaError_t mc_init() {
     return cudaMemcpyToSymbol(c_tri, t8, sizeof(t8));
 }
 
+// Words per grid row of the inside bits, rounded up to a power of two.
+static int mc_words(int nx) {
+    const int nw = (nx + 31) / 32;
+    int wp = 1;
+    while (wp < nw) wp <<= 1;
+    return wp;
+}
+
 cudaError_t launch_mc_count(ftr_ctx* c) {
     const int nr = c->mc_blocks;              // grid rows n_y n_z
-    const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
+    const int wp = mc_words(c->g.n[0]);
     prof_begin(c, ST_MC_COUNT);
-    switch ((c->g.n[0] + 127) / 128) {
-        case 1: k_mc_count<1><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
-        case 2: k_mc_count<2><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
-        case 3: k_mc_count<3><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
-        default: k_mc_count<4><<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, nr); break;
-    }
-    c->launches++;
+    launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
+               c->d_mc_bits, nr, wp);
+    const int64_t threads = (int64_t)nr * wp;
+    launch_pdl(k_mc_count_bits, (unsigned)((threads + kMcThreads - 1) / kMcThreads), kMcThreads, 0, c->stream, c->g,
+               c->d_mc_bits, c->d_mc_blk, nr, wp);
+    c->launches += 2;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
     if (e != cudaSuccess) return e;
     prof_begin(c, ST_MC_SCAN);
     const int ntiles = (nr + kScanTile - 1) / kScanTile;
-    k_mc_tile_sums<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nr, c->d_mc_tile);
-    k_mc_tile_scan<<<1, kMcThreads, 0, c->stream>>>(c->d_mc_tile, ntiles, nr, c->d_mc_off);
-    k_mc_tile_write<<<ntiles, kMcThreads, 0, c->stream>>>(c->d_mc_blk, nr, c->d_mc_tile, c->d_mc_off);
+    launch_pdl(k_mc_tile_sums, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile);
+    launch_pdl(k_mc_tile_scan, 1, kMcThreads, 0, c->stream, c->d_mc_tile, ntiles, nr, c->d_mc_off);
+    launch_pdl(k_mc_tile_write, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile, c->d_mc_off);
     c->launches += 3;
     e = cudaGetLastError();
     prof_end(c, ST_MC_SCAN);
-    if (e != cudaSuccess) return e;
+    return e;
+}
+
+// The three totals (active nodes, vertices, triangles) into pinned host
+// memory; enqueued after the frame's last kernel so that no copy sits between
+// two kernels of the frame.
+cudaError_t launch_mc_totals(ftr_ctx* c) {
+    const int nr = c->mc_blocks;
     return cudaMemcpyAsync(c->h_mc_tot, c->d_mc_off + 3 * (nr + 1), 3 * sizeof(int), cudaMemcpyDeviceToHost,
                            c->stream);
 }
 
 cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int nr = c->mc_blocks;
-    const int ctas = (nr + kRowsPerCta - 1) / kRowsPerCta;
+    const int wp = mc_words(c->g.n[0]);
+    const int64_t threads = (int64_t)nr * wp;
     prof_begin(c, ST_MC_EMIT);
-    k_mc_emit<<<ctas, kMcThreads, 0, c->stream>>>(c->g, c->d_A, c->d_levelf, c->d_mc_blk, c->d_mc_off, nr,
-                                                  c->d_mc_nodes, (int)c->cap_mc_nodes, c->d_verts, c->d_vnrm,
-                                                  (int)c->cap_verts);
+    launch_pdl(k_mc_emit_bits, (unsigned)((threads + kMcThreads - 1) / kMcThreads), kMcThreads, 0, c->stream, c->g,
+               c->d_A, c->d_mc_bits, c->d_levelf, c->d_mc_blk, c->d_mc_off, nr, wp, c->d_mc_nodes,
+               (int)c->cap_mc_nodes, c->d_verts, c->d_vnrm, (int)c->cap_verts);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);
@@ -567,7 +547,7 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     prof_begin(c, ST_MC_TRIS);
-    k_mc_tris<<<(sms > 0 ? sms : 152) * 4, 256, 0, c->stream>>>(c->g, c->d_mc_nodes, c->d_mc_off + 3 * (nr + 1),
+    launch_pdl(k_mc_tris, (sms > 0 ? sms : 152) * 4, 256, 0, c->stream, c->g, c->d_mc_nodes, c->d_mc_off + 3 * (nr + 1),
                                                                  (int)c->cap_mc_nodes, (int)c->cap_tris,
                                                                  c->d_mc_off, c->d_tris);
     c->launches++;
