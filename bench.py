@@ -204,10 +204,11 @@ def algorithmic_bytes(stage, info, grid, k_views):
         return c8 * mh_full + 4 * M
     if stage == "splat_accum":
         return info["pairs"] * (4 + 48) + info["bricks"] * 512 * 3 * 4
-    if stage == "mc_count":
-        return 4 * M
-    if stage == "mc_emit":
-        return 4 * M + 24 * info["n_vertices"]
+    if stage == "mc_count":           # A read once, the inside bits written (count reads them from L2)
+        return 4 * M + M // 8
+    if stage == "mc_emit":            # bits of the rows, A at both ends of each crossing edge, vertices,
+        # normals and one 16-byte record per vertex-owning node written
+        return M // 8 + info["n_vertices"] * (8 + 24 + 16)
     if stage == "texture":
         return info["n_vertices"] * (12 + k_views * 12 + 4)
     return None
