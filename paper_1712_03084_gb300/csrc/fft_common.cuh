@@ -271,6 +271,12 @@ __device__ __forceinline__ void live_z_range(const int* __restrict__ meta, int& 
     zh = ((bmax + 1) * 8 + 15) & ~15;
 }
 
+// Ask L2 to fetch the 128-byte line holding p (no register is written, so
+// later loads of the line find it in L2 instead of DRAM).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Signed frequency index of bin k on an axis of length n (Nyquist -> -n/2).
 __device__ __forceinline__ int signed_bin(int k, int n) { return k < n / 2 ? k : k - n; }
 

@@ -52,6 +52,15 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     // the transformed x component waits in shared memory (line index fastest)
     float2* stash = smem + X::SIZE;
     const float2* line = s0 + (size_t)N * (z0 + f1 + (size_t)nz * kx);
+    // the y and z components' lines go to L2 while the x component is
+    // transformed (one prefetch per 128-byte line per thread)
+    if (r1 < X::N2 && (r1 & 15) == 0) {
+#pragma unroll
+        for (int n1 = 0; n1 < X::N1; ++n1) {
+            prefetch_l2(line + Mh + X::N2 * n1 + r1);
+            prefetch_l2(line + 2 * Mh + X::N2 * n1 + r1);
+        }
+    }
     // x component: transform along y and park it (line index fastest)
     if (r1 < X::N2) load_step1<N, F>(line, r1, f1, smem, tw);
     __syncthreads();

@@ -45,6 +45,14 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     int zl, zh;
     live_z_range(meta, zl, zh);
     const size_t line = (size_t)N * ((size_t)(ky0 + f) + (size_t)ny * kx);
+    // field 1 goes to L2 while field 0 is transformed
+    if (r < X::N2 && (r & 15) == 0) {
+#pragma unroll
+        for (int n1 = 0; n1 < X::N1; ++n1) {
+            const int z = X::N2 * n1 + r;
+            if (z >= zl && z < zh) prefetch_l2(s1 + Mh + line + z);
+        }
+    }
     // forward z transforms of W (field 0) and of the x/y-transformed V_z (field 1)
     if (r < X::N2) load_step1<N, F>(s1 + line, r, f, zl, zh, smem, tw);
     __syncthreads();

@@ -29,9 +29,21 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     const int y0 = blockIdx.x * kRows;
     const int z = blockIdx.y;
     const int tid = threadIdx.x;
-    for (int k = tid; k < kRows * NKX; k += blockDim.x) {
-        const int row = k & (kRows - 1), kx = k >> 4;
-        hs[kx * kHs + row] = src[(size_t)(y0 + row) + (size_t)ny * (z + (size_t)nz * kx)];
+    // every load of the staging is issued before the first shared-memory store
+    constexpr int kPer = (kRows * NKX + kLines * Xchg<N, kLines>::NT - 1) / (kLines * Xchg<N, kLines>::NT);
+    {
+        float2 st[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int k = tid + i * (int)blockDim.x;
+            const int row = k & (kRows - 1), kx = k >> 4;
+            st[i] = k < kRows * NKX ? src[(size_t)(y0 + row) + (size_t)ny * (z + (size_t)nz * kx)] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int k = tid + i * (int)blockDim.x;
+            if (k < kRows * NKX) hs[(k >> 4) * kHs + (k & (kRows - 1))] = st[i];
+        }
     }
     __syncthreads();
     const int f1 = tid % kLines, j1 = tid / kLines;

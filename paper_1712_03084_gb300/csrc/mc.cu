@@ -21,13 +21,14 @@
 //   emit   rows with surface only: per word an exclusive prefix over the
 //          row's words, then its active nodes in x order: one 16-byte
 //          record per node (node, edge bits | class << 8, first vertex,
-//          first triangle), vertex positions t = (L - A0)/(A1 - A0) and
-//          normals -grad A (central differences, one-sided at the border,
-//          lerped)
-//   tris   one thread per active node: triangle corners from the case table;
-//          an edge owned by another node is found by a short scan of that
-//          node's row records.
+//          first triangle)
+//   tris   one thread per active node: the vertices of its crossing edges
+//          (t = (L - A0)/(A1 - A0), normal -grad A by central differences,
+//          one-sided at the border, lerped), then its triangles' corners
+//          from the case table; an edge owned by another node is found by a
+//          short scan of that node's row records.
 #include <cuda_runtime.h>
+#include <math.h>
 
 #include "ftr_internal.h"
 
@@ -87,11 +88,19 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_bits(GridDev g, const float* 
     const float* a = A + (int64_t)row * nx;
     const int nw = (nx + 31) >> 5;
     unsigned mine = 0u;
-    for (int w = 0; w < nw; ++w) {
-        const int x = 32 * w + lane;
-        const bool in = x < nx && a[x] >= L;
-        const unsigned b = __ballot_sync(0xffffffffu, in);
-        if (lane == w) mine = b;
+    // up to 8 words per batch: all loads are issued before the first ballot
+    for (int w0 = 0; w0 < nw; w0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int x = 32 * (w0 + k) + lane;
+            v[k] = (w0 + k < nw && x < nx) ? a[x] : -INFINITY;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const unsigned b = __ballot_sync(0xffffffffu, v[k] >= L);
+            if (lane == w0 + k) mine = b;
+        }
     }
     if (lane < wp) bits[(int64_t)row * wp + lane] = lane < nw ? mine : 0u;
 }
@@ -343,14 +352,12 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
 // group's exclusive prefix of (active nodes, vertices, triangles) plus the
 // row offsets give every thread its output positions; it then walks its
 // active nodes in x order writing the node record (node, edge bits | class
-// << 8, first vertex, first triangle) and the vertices of its crossing edges.
-__global__ void __launch_bounds__(kMcThreads) k_mc_emit_bits(GridDev g, const float* __restrict__ A,
-                                                             const unsigned* __restrict__ bits,
-                                                             const float* __restrict__ levelf,
+// << 8, first vertex, first triangle).  Vertices are computed per record by
+// k_mc_tris, one thread per node.
+__global__ void __launch_bounds__(kMcThreads) k_mc_emit_bits(GridDev g, const unsigned* __restrict__ bits,
                                                              const int* __restrict__ cnt, const int* __restrict__ off,
                                                              int nrows, int wp, int4* __restrict__ nodes,
-                                                             int cap_nodes, float* __restrict__ verts,
-                                                             float* __restrict__ vnrm, int cap_v) {
+                                                             int cap_nodes) {
     pdl_wait();
     __shared__ unsigned char s_ntri[256];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
@@ -390,7 +397,6 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_bits(GridDev g, const fl
         }
     }
     if (!act) return;
-    const float Ln = levelf[1];
     int ja = off[row] + pa - ca;
     int jv = off[(nrows + 1) + row] + pv - cv;
     int jt = off[2 * (nrows + 1) + row] + pt - ct;
@@ -406,10 +412,6 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_bits(GridDev g, const fl
         const int64_t n = rowbase + x;
         if (ja < cap_nodes) nodes[ja] = make_int4((int)n, flags | (cls << 8), jv, jt);
         ++ja;
-        if (flags) {
-            const int q[3] = {x, y, z};
-            emit_vertices(g, A, Ln, n, q, flags, jv, cap_v, verts, vnrm);
-        }
         jv += __popc(flags);
         jt += ntr;
     }
@@ -452,14 +454,28 @@ __device__ __forceinline__ void tris_of_node(const GridDev& g, const int4* __res
     }
 }
 
-__global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const int4* __restrict__ nodes,
+// One thread per node record: the vertices on its crossing edges, then its
+// triangles.
+__global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const float* __restrict__ A,
+                                                 const float* __restrict__ levelf, const int4* __restrict__ nodes,
                                                  const int* __restrict__ totals, int cap_nodes, int cap_tris,
-                                                 const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
+                                                 const int* __restrict__ off_rows, int32_t* __restrict__ tris,
+                                                 float* __restrict__ verts, float* __restrict__ vnrm, int cap_v) {
     pdl_wait();
     const int n_nodes = totals[0];
     if (n_nodes > cap_nodes || totals[2] > cap_tris) return;   // the host grows the buffers and runs again
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_nodes; r += gridDim.x * blockDim.x)
+    const float Ln = levelf[1];
+    const int nx = g.n[0], ny = g.n[1];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_nodes; r += gridDim.x * blockDim.x) {
+        const int4 rec = nodes[r];
+        const int flags = rec.y & 7;
+        if (flags) {
+            const int row = rec.x / nx;
+            const int q[3] = {rec.x - row * nx, row % ny, row / ny};
+            emit_vertices(g, A, Ln, (int64_t)rec.x, q, flags, rec.z, cap_v, verts, vnrm);
+        }
         tris_of_node(g, nodes, r, off_rows, tris);
+    }
 }
 
 __global__ void k_mc_classes(GridDev g, const float* __restrict__ A, const float* __restrict__ levelf,
@@ -538,8 +554,7 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int64_t threads = (int64_t)nr * wp;
     prof_begin(c, ST_MC_EMIT);
     launch_pdl(k_mc_emit_bits, (unsigned)((threads + kMcThreads - 1) / kMcThreads), kMcThreads, 0, c->stream, c->g,
-               c->d_A, c->d_mc_bits, c->d_levelf, c->d_mc_blk, c->d_mc_off, nr, wp, c->d_mc_nodes,
-               (int)c->cap_mc_nodes, c->d_verts, c->d_vnrm, (int)c->cap_verts);
+               c->d_mc_bits, c->d_mc_blk, c->d_mc_off, nr, wp, c->d_mc_nodes, (int)c->cap_mc_nodes);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);
@@ -547,9 +562,9 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     prof_begin(c, ST_MC_TRIS);
-    launch_pdl(k_mc_tris, (sms > 0 ? sms : 152) * 4, 256, 0, c->stream, c->g, c->d_mc_nodes, c->d_mc_off + 3 * (nr + 1),
-                                                                 (int)c->cap_mc_nodes, (int)c->cap_tris,
-                                                                 c->d_mc_off, c->d_tris);
+    launch_pdl(k_mc_tris, (sms > 0 ? sms : 152) * 4, 256, 0, c->stream, c->g, c->d_A, c->d_levelf, c->d_mc_nodes,
+               c->d_mc_off + 3 * (nr + 1), (int)c->cap_mc_nodes, (int)c->cap_tris, c->d_mc_off, c->d_tris, c->d_verts,
+               c->d_vnrm, (int)c->cap_verts);
     c->launches++;
     e = cudaGetLastError();
     prof_end(c, ST_MC_TRIS);
