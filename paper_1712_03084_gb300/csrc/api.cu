@@ -306,7 +306,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_brick_cursor, c->n_bricks);
     ALLOC(c->d_brick_slot, c->n_bricks);
     ALLOC(c->d_active, c->n_bricks);
-    ALLOC(c->d_meta, 4);
+    ALLOC(c->d_meta, 8);
     ALLOC(c->d_tile, (c->n_bricks + 2047) / 2048 + 1);
     ALLOC(c->d_vpool, (size_t)c->n_bricks * 3 * kBrickVox);
     ALLOC(c->d_s0, 3 * c->Mh);

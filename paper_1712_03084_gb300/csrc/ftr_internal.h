@@ -106,7 +106,7 @@ struct ftr_ctx {
     int* d_brick_cursor = nullptr;
     int* d_brick_slot = nullptr;
     int* d_active = nullptr;
-    int* d_meta = nullptr;     // [0] active bricks, [1] entries, [2] min bz, [3] max bz
+    int* d_meta = nullptr;     // [0] active bricks, [1] entries, [2] min bz, [3] max bz, [4] accumulation ticket
     int2* d_tile = nullptr;    // per-tile sums / offsets of the brick scan
     int* d_entries = nullptr;
     int64_t cap_entries = 0;

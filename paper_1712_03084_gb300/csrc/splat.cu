@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int2* tile_sum, int 
         meta[1] = carry.x;
         meta[2] = 0x7fffffff;
         meta[3] = -1;
+        meta[4] = 0;                // brick ticket of the accumulation
     }
 }
 
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const float4* __restrict__ pfrac,
                                                              const float4* __restrict__ pnrm,
                                                              const int* __restrict__ wild_weights,
-                                                             float* __restrict__ vpool) {
+                                                             float* __restrict__ vpool, int* __restrict__ ticket) {
     pdl_wait();
     __shared__ __align__(16) unsigned acc[8][kBrickVox];   // fast: [c] hi, [4 + c] lo; slow: 4 x int64
     __shared__ int4 s_base[kStage];
@@ -356,7 +357,15 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
     const int ox = o & 3, oy = (o >> 2) & 3, oz = o >> 4;
     const int pl = tid >> 6;
     const bool weights_ok = wild_weights[0] == 0;
-    for (int s = blockIdx.x; s < nact; s += gridDim.x) {
+    __shared__ int s_brick;
+    // bricks are taken one at a time from a shared ticket, so that CTAs that
+    // drew light bricks go on to the next ones (brick costs vary with their
+    // point counts)
+    for (;;) {
+        if (tid == 0) s_brick = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int s = s_brick;
+        if (s >= nact) break;                                           // block-uniform
         const int b = active[s];
         const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
         const int orgx = bx * kBrick, orgy = by * kBrick, orgz = bz * kBrick;
@@ -525,7 +534,7 @@ cudaError_t launch_splat(ftr_ctx* c) {
     prof_begin(c, ST_SPLAT_ACC);
     const int grid = sms * 4;
     launch_pdl(k_splat_accum, grid, kAccThreads, 0, c->stream, c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
-                                                       c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool);
+               c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool, c->d_meta + 4);
     c->launches++;
     prof_end(c, ST_SPLAT_ACC);
     return cudaGetLastError();

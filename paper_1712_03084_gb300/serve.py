@@ -156,32 +156,39 @@ class Slot:
         self.ctx.close()
 
 
-def run_batch(frames, grids, bboxes, sequential=False):
+def run_batch(frames, grids, bboxes, sequential=False, rounds=3):
     """Reconstruct ``frames`` (FrameInput list) on one slot each, all queued at
-    once (or one after another); returns (seconds, [(n_vertices, n_tris)])."""
+    once (or one after another), ``rounds`` times; returns (median seconds per
+    round, [(n_vertices, n_tris)])."""
     torch = _torch()
     slots = [Slot(g, b, f, f.n_points) for f, g, b in zip(frames, grids, bboxes)]
-    # warm-up: capture every slot's graph
-    for s, f in zip(slots, frames):
-        s.submit(f)
-    for s in slots:
-        s.finish()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = []
-    if sequential:
+    # warm-up, twice: the first round sizes every slot's buffers (growing them
+    # invalidates the slot's graph), the second captures the final graphs
+    for _ in range(2):
         for s, f in zip(slots, frames):
             s.submit(f)
-            out.append(s.finish())
-    else:
-        for s, f in zip(slots, frames):
-            s.submit(f)
-        out = [s.finish() for s in slots]
+        for s in slots:
+            s.finish()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    times, out = [], []
+    gc.disable()
+    for _ in range(rounds):
+        t0 = time.perf_counter()
+        out = []
+        if sequential:
+            for s, f in zip(slots, frames):
+                s.submit(f)
+                out.append(s.finish())
+        else:
+            for s, f in zip(slots, frames):
+                s.submit(f)
+            out = [s.finish() for s in slots]
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    gc.enable()
     for s in slots:
         s.close()
-    return dt, out
+    return float(np.median(times)), out
 
 
 @dataclass
@@ -236,14 +243,16 @@ class Server:
                 k += 1
         arrivals.sort()
         by_id = {s.sid: s for s in self.sessions}
-        # warm-up: every frame of every session once, so each slot's buffers
-        # reach their final size (growing them frees memory, which waits for
-        # the whole device) and its graph is captured before arrivals start
-        for j in range(max(len(s.frames) for s in self.sessions)):
-            for s in self.sessions:
-                s.slot.submit(s.frames[j % len(s.frames)])
-            for s in self.sessions:
-                s.slot.finish()
+        # warm-up: every frame of every session, twice: the first pass sizes
+        # each slot's buffers (growing them frees memory, which waits for the
+        # whole device, and invalidates the slot's graph), the second captures
+        # the final graphs before arrivals start
+        for _ in range(2):
+            for j in range(max(len(s.frames) for s in self.sessions)):
+                for s in self.sessions:
+                    s.slot.submit(s.frames[j % len(s.frames)])
+                for s in self.sessions:
+                    s.slot.finish()
         torch.cuda.synchronize()
         lat, done_frames, meshes = [], 0, {}
         nxt = 0
