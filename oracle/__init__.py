@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle for the volumetric Fourier-transform reconstruction.
 
 TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct
-restatement of Section III-B/III-C of Alexiadis et al. (IEEE TCSVT 2017,
+restatement of Section III-A/III-B/III-C of Alexiadis et al. (IEEE TCSVT 2017,
 arXiv 1712.03084) against which the CUDA path is checked.  Only the test
 suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg
 of ``bench.py`` may import it.  The product path (the C-ABI library and its
@@ -13,6 +13,7 @@ cites the passage of the paper it follows.  Readings of points where the
 paper is silent are named constants (``oracle.conventions``).
 
 Modules
+  raw        points, normals, confidences from depth maps           (Sec. III-A)
   fft        own mixed-radix Stockham FFT + brute-force DFT        (Sec. III-B)
   splat      weighted Gaussian splat eq.(1)(2), simple splat        (Sec. III-B)
   spectral   integration filter jw/|w|^2, inverse transform         (Sec. III-B)

@@ -24,6 +24,17 @@ CUDA library states the same readings independently in its own source.
 """
 
 SIGMA2_RATIO2 = 1.5          # sigma2^2 / sigma1^2, Sec. III-B ("sigma2^2 = 3/2 sigma1^2")
+
+# Raw reconstruction (Sec. III-A).  The paper triangulates each depth map
+# (the organised-point method of its ref. [13]) and skips triangles across
+# depth discontinuities without giving the threshold; the reading here: a
+# triangle is kept iff all three pixels are foreground and the largest depth
+# difference among its corners is <= TSDC_STEP + 3 sigma(z_max) with the
+# depth noise sigma(z) = TSDC_NOISE z^2 (metres).  W2 is the mean of the
+# binary silhouette over a (2 W2_RADIUS + 1)^2 window, zero outside the image.
+TSDC_STEP = 0.03
+TSDC_NOISE = 0.0012
+W2_RADIUS = 10
 STENCIL = 4                  # 4^3 support, Sec. III-B
 STENCIL_LO = 1               # nodes floor(t)-1 .. floor(t)+2
 SPLAT_WEIGHTED = 0
