@@ -146,6 +146,29 @@ typedef struct {
     const uint8_t* rgb;       /* rgb_h x rgb_w x 3 (host or device)                       */
 } ftr_view;
 
+/*
+ * Raw reconstruction on the device (Sec. III-A), appended to the frame like
+ * ftr_splat: for each of the k views (1..8; w, h, K, world_to_cam and depth
+ * are read, the RGB fields are not), every foreground pixel (depth > 0)
+ * that lies on a kept triangle of the organised triangulation of its depth
+ * map gives the point X = R^T (x_c - t) with x_c = ((u - c_x) / f_x D,
+ * (v - c_y) / f_y D, D), the normal R^T N (N = the normalised sum of the
+ * camera-facing unit normals of the kept triangles containing the pixel;
+ * each 2 x 2 pixel quad gives the triangles (p00, p01, p10) and
+ * (p01, p11, p10), kept iff all three pixels are foreground, the largest
+ * corner depth difference is <= step + 3 noise z_max^2 and the area is not
+ * zero) and the confidence W = W1 W2, W1 = max(<-x_c / |x_c|, N>, 0), W2 = the
+ * mean of the silhouette over a (2 radius + 1)^2 window (zero outside).
+ * Points are appended in view order, row-major pixel order.  depth: device
+ * memory, h x w float32 metres, 0 = background.  step, noise: metres
+ * (negative = 0.03 and 0.0012); radius: 0..16 (negative = 10).  conf_out
+ * (nullable; entries nullable): per view a device h x w float32 map that
+ * receives W per pixel (0 where no point): the W_k of the texture stage.
+ * Waits for the stream once (the point count sizes the ingest).
+ */
+int ftr_splat_depth(ftr_ctx* ctx, const ftr_view* views, int k, double step, double noise, int radius,
+                    float* const* conf_out);
+
 typedef struct {
     float* weights;           /* n_vertices x k: W_k at the vertex, 0 if not visible       */
     float* uv;                /* n_vertices x k x 2: RGB pixel coords, (-1,-1) if w = 0    */

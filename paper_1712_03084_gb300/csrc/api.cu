@@ -195,6 +195,10 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_A);
     for (int a = 0; a < 3; ++a) dfree(c->d_tw[a]);
     dfree(c->d_tc_table);
+    dfree(c->d_raw);
+    dfree(c->d_raw_tiles);
+    dfree(c->d_raw_total);
+    if (c->h_raw_total) cudaFreeHost(c->h_raw_total);
     dfree(c->d_tc_err);
     dfree(c->d_level);
     dfree(c->d_levelf);
@@ -449,6 +453,63 @@ int ftr_splat(ftr_ctx* c, const float* points, const float* normals, const float
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat");
     }
     return FTR_OK;
+}
+
+int ftr_splat_depth(ftr_ctx* c, const ftr_view* views, int k, double step, double noise, int radius,
+                    float* const* conf_out) {
+    if (!c) return FTR_EINVAL;
+    if (k < 1 || k > kMaxViews || !views) return set_err(c, FTR_EINVAL, "ftr_splat_depth: 1 <= k <= 8 views");
+    if (step < 0.0) step = 0.03;
+    if (noise < 0.0) noise = 0.0012;
+    if (radius < 0) radius = 10;
+    if (radius > raw_max_radius() || !(step >= 0.0) || !(noise >= 0.0))
+        return set_err(c, FTR_EINVAL, "ftr_splat_depth: radius <= 16, finite step and noise");
+    int64_t pixels = 0;
+    for (int i = 0; i < k; ++i) {
+        const ftr_view& v = views[i];
+        if (v.w < 2 || v.h < 2 || v.w > 16384 || v.h > 16384 || !v.depth || !is_device_ptr(v.depth))
+            return set_err(c, FTR_EINVAL, "ftr_splat_depth: view %d needs a device depth map of at least 2 x 2", i);
+        if (!(v.K[0] != 0.f) || !(v.K[4] != 0.f)) return set_err(c, FTR_EINVAL, "ftr_splat_depth: view %d focal", i);
+        if (conf_out && conf_out[i] && !is_device_ptr(conf_out[i]))
+            return set_err(c, FTR_EINVAL, "ftr_splat_depth: confidence maps must be device memory");
+        pixels += (int64_t)v.w * v.h;
+    }
+    cudaError_t e;
+    const int tiles = raw_tiles(views, k);
+    if (pixels > c->raw_cap) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c->d_raw);
+        if ((e = dalloc(&c->d_raw, (size_t)pixels * 7)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth");
+        c->raw_cap = pixels;
+    }
+    if (tiles > c->raw_tiles_cap) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c->d_raw_tiles);
+        if ((e = dalloc(&c->d_raw_tiles, (size_t)tiles)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth");
+        c->raw_tiles_cap = tiles;
+    }
+    if (!c->d_raw_total) {
+        if ((e = dalloc(&c->d_raw_total, 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth");
+        if ((e = cudaMallocHost((void**)&c->h_raw_total, sizeof(int))) != cudaSuccess)
+            return cuda_fail(c, e, "ftr_splat_depth");
+    }
+    RawParams rp;
+    rp.step = step;
+    rp.noise = noise;
+    rp.step_f = (float)step;
+    rp.noise_f = (float)noise;
+    rp.radius = radius;
+    float* P = c->d_raw;
+    float* N = P + 3 * pixels;
+    float* W = P + 6 * pixels;
+    if ((e = launch_raw(c, rp, views, k, conf_out, P, N, W, c->d_raw_tiles, c->d_raw_total)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_splat_depth: raw reconstruction");
+    // the point count decides the ingest launch: one wait per call
+    if ((e = cudaMemcpyAsync(c->h_raw_total, c->d_raw_total, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_splat_depth");
+    return ftr_splat(c, P, N, W, (int64_t)*c->h_raw_total);
 }
 
 int ftr_solve(ftr_ctx* c, double* iso_level_out) {
@@ -1044,6 +1105,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     b += 5 * c->Mh * (int64_t)sizeof(float2) + c->M * (int64_t)sizeof(float);
     b += (int64_t)(c->g.n[0] + c->g.n[1] + c->g.n[2]) * (int64_t)sizeof(float2);
     if (c->d_tc_table) b += (int64_t)tc_table_bytes() + 16;
+    b += c->raw_cap * 7 * (int64_t)sizeof(float) + c->raw_tiles_cap * (int64_t)sizeof(int);
     b += (2 * c->level_blocks + 8) * (int64_t)sizeof(double);
     b += (6 * (int64_t)c->mc_blocks + 16) * (int64_t)sizeof(int);
     b += (int64_t)c->mc_blocks * 16 * (int64_t)sizeof(unsigned);   // inside bits (upper bound)

@@ -122,6 +122,14 @@ struct ftr_ctx {
     unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
     int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
 
+    // raw reconstruction scratch (ftr_splat_depth)
+    float* d_raw = nullptr;                // 7 floats per pixel capacity: P (3), N (3), W
+    int64_t raw_cap = 0;                   // pixels
+    int* d_raw_tiles = nullptr;            // per-tile counts / offsets
+    int64_t raw_tiles_cap = 0;
+    int* d_raw_total = nullptr;            // device total of the last call
+    int* h_raw_total = nullptr;            // pinned copy
+
     // level
     double* d_level = nullptr;     // [0] L, [1] accepted count
     float* d_levelf = nullptr;     // [0] L rounded up to float32, [1] L rounded to nearest
@@ -230,6 +238,16 @@ cudaError_t launch_fz(ftr_ctx* c);
 cudaError_t launch_iy(ftr_ctx* c);
 cudaError_t launch_ix(ftr_ctx* c);
 cudaError_t launch_level(ftr_ctx* c);
+// raw reconstruction (raw.cu): depth maps -> compacted points, normals, W
+struct RawParams {
+    double step, noise;      // depth-step threshold step + 3 noise z_max^2 (metres)
+    float step_f, noise_f;
+    int radius;              // W2 window radius
+};
+cudaError_t launch_raw(ftr_ctx* c, const RawParams& rp, const ftr_view* views, int k, float* const* conf_maps,
+                       float* P, float* N, float* W, int* d_tile_cnt, int* d_total);
+int raw_tiles(const ftr_view* views, int k);
+int raw_max_radius();
 // tensor-core split-precision passes (fft_tc.cu): pass 0 x fwd, 1 y fwd,
 // 2 z fwd + filter + z inv, 3 y inv, 4 x inv
 bool tc_supported_n(int n);

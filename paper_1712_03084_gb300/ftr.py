@@ -65,6 +65,8 @@ _SIGNATURES = [
     ("ftr_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ftr_splat", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_int64]),
+    ("ftr_splat_depth", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     ("ftr_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("ftr_extract_mesh", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_mesh)]),
     ("ftr_mesh_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -202,17 +204,28 @@ def ftr_mesh_copy(ctx, vertices=None, normals=None, tris=None):
 def make_view(view):
     """ftr_view from a dict(depth, conf, rgb, K, world_to_cam, K_rgb, world_to_rgb)."""
     v = ftr_view()
-    depth, conf, rgb = view["depth"], view["conf"], view["rgb"]
+    depth, conf, rgb = view["depth"], view.get("conf"), view.get("rgb")
     v.h, v.w = int(depth.shape[0]), int(depth.shape[1])
-    v.rgb_h, v.rgb_w = int(rgb.shape[0]), int(rgb.shape[1])
+    if rgb is not None:
+        v.rgb_h, v.rgb_w = int(rgb.shape[0]), int(rgb.shape[1])
     v.K[:] = [float(x) for x in np.asarray(view["K"], dtype=np.float32).reshape(-1)]
     v.world_to_cam[:] = [float(x) for x in np.asarray(view["world_to_cam"], dtype=np.float32).reshape(-1)]
-    v.K_rgb[:] = [float(x) for x in np.asarray(view["K_rgb"], dtype=np.float32).reshape(-1)]
-    v.world_to_rgb[:] = [float(x) for x in np.asarray(view["world_to_rgb"], dtype=np.float32).reshape(-1)]
+    if "K_rgb" in view:
+        v.K_rgb[:] = [float(x) for x in np.asarray(view["K_rgb"], dtype=np.float32).reshape(-1)]
+        v.world_to_rgb[:] = [float(x) for x in np.asarray(view["world_to_rgb"], dtype=np.float32).reshape(-1)]
     v.depth = _ptr(depth, np.float32)
     v.conf = _ptr(conf, np.float32)
     v.rgb = _ptr(rgb, np.uint8)
     return v
+
+
+def ftr_splat_depth(ctx, views, step=-1.0, noise=-1.0, radius=-1, conf_out=None):
+    """Raw reconstruction of the views' device depth maps, appended to the frame."""
+    arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
+    confs = None
+    if conf_out is not None:
+        confs = (ctypes.c_void_p * len(views))(*[_ptr(c, np.float32) for c in conf_out])
+    _check(load().ftr_splat_depth(ctx, arr, len(views), float(step), float(noise), int(radius), confs), ctx)
 
 
 def ftr_texture(ctx, views, depth_tol, weights=None, uv=None, rgb=None, textured=None):
