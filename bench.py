@@ -438,6 +438,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.close()
         ctx = None
         multi = run_multi(args, rank, dev, plain_frame=fr)
+    from_depth = run_from_depth(args, rank, dev, fr, flush) if not args.no_multi else None
     prec = None
     if not args.no_precision:
         if ctx is not None:
@@ -475,6 +476,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if multi:
         line.update(multi)
+    if from_depth:
+        line.update(from_depth)
     if prec:
         line.update(prec)
     return line
@@ -672,6 +675,86 @@ def run_precision(args, rank, dev, fr256):
         del P, N, W, dviews, outs
         torch.cuda.empty_cache()
     return {"precision": out}
+
+
+def run_from_depth(args, rank, dev, fr, flush):
+    """Frames/s when the frame arrives as RGB-D images: the raw reconstruction
+    of Sec. III-A on the device (ftr_splat_depth, which also writes the W_k
+    maps the texture stage reads), then the graph frame.  Once with the
+    images resident in HBM, once copied in from pinned host memory per frame
+    (mesh and texture copied out)."""
+    import torch
+    from datagen import frame_config
+    from paper_1712_03084_gb300 import ftr
+    cfg = frame_config(f"human{GRID}")
+    grid, box = cfg["grid_n"], cfg["bbox"]
+    tol = depth_tol(cfg)
+    K = len(fr["views"])
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ftr.Context(grid, box, stream=stream.cuda_stream)
+    ctx.autotune()
+    dviews, confs = [], []
+    for v in fr["views"]:
+        d = dict(v)
+        d["depth"] = torch.from_numpy(v["depth"]).to(dev)
+        d["rgb"] = torch.from_numpy(v["rgb"]).to(dev)
+        d["conf"] = torch.zeros(v["depth"].shape, dtype=torch.float32, device=dev)
+        confs.append(d["conf"])
+        dviews.append(d)
+    hd = [torch.from_numpy(np.ascontiguousarray(v["depth"])).pin_memory() for v in fr["views"]]
+    hr = [torch.from_numpy(np.ascontiguousarray(v["rgb"])).pin_memory() for v in fr["views"]]
+    cap = grid[0] * grid[1] * grid[2] // 64
+    outs = [torch.empty((cap, K), dtype=torch.float32, device=dev),
+            torch.empty((cap, K, 2), dtype=torch.float32, device=dev),
+            torch.empty((cap, 3), dtype=torch.uint8, device=dev),
+            torch.empty((cap,), dtype=torch.uint8, device=dev)]
+    hv = torch.empty((cap, 3), dtype=torch.float32).pin_memory()
+    ht = torch.empty((2 * cap, 3), dtype=torch.int32).pin_memory()
+    hrgb = torch.empty((cap, 3), dtype=torch.uint8).pin_memory()
+
+    def frame(host):
+        if host:
+            for d, a, b in zip(dviews, hd, hr):
+                d["depth"].copy_(a, non_blocking=True)
+                d["rgb"].copy_(b, non_blocking=True)
+        ctx.reset()
+        ftr.ftr_splat_depth(ctx.h, dviews, conf_out=confs)
+        ftr.ftr_frame_launch(ctx.h, dviews, tol, *outs, cap)
+        m = ftr.ftr_frame_finish(ctx.h)
+        if host:
+            ftr.ftr_mesh_copy(ctx.h, hv[:m.n_vertices], None, ht[:m.n_tris])
+            hrgb[:m.n_vertices].copy_(outs[2][:m.n_vertices])
+        return m
+
+    res = {}
+    steps = max(10, min(args.steps, 50))
+    with torch.cuda.stream(stream):
+        for host in (False, True):
+            for _ in range(4):
+                frame(host)
+            torch.cuda.synchronize()
+            times = []
+            gc.disable()
+            for i in range(steps):
+                flush.fill_(float(i))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                m = frame(host)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            gc.enable()
+            key = "host_inputs" if host else "device_inputs"
+            res[key] = {"frames_per_s": round(steps / float(sum(times)), 1),
+                        "p50_ms": round(1000 * float(np.median(times)), 4)}
+    n_in, _ = ctx.stats()
+    ctx.close()
+    res["points"] = int(n_in)
+    res["h2d_bytes_per_frame"] = int(sum(a.numel() * 4 for a in hd) + sum(b.numel() for b in hr))
+    res["config"] = ("human256 frame as 4 RGB-D images (512x424 depth, 1920x1080 RGB): raw reconstruction "
+                     "(points, normals, W1 W2) on the device, then the graph frame with texture; host wall clock "
+                     "per frame (the raw stage waits once for its point count); host_inputs copies depth and "
+                     "RGB in and the mesh and colours out")
+    return {"from_depth": res}
 
 
 def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
