@@ -347,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
     # slab (cached per grid for the process), then the warm-up proper
     if args.plan:
         ctx.set_plan(tuple(int(v) for v in args.plan.split(",")))
-        tune_us = np.zeros((3, 3))
+        tune_us = np.zeros((3, 4))
     else:
         tune_us = ctx.autotune()
     plan = ctx.plan()

@@ -242,8 +242,10 @@ int64_t ftr_device_bytes(const ftr_ctx* ctx);
 /*
  * Tile plans (no counterpart in the paper, which gives no kernel design).
  * The y, z and inverse-y FFT passes each move F lines per CTA, F in
- * {8, 16, 32}; every plan computes bit-identical results (each line's
- * arithmetic does not depend on F), only the speed differs.
+ * {8, 16, 32}; for the y pass F = -16 means 16 lines whose three component
+ * tiles are fetched by bulk asynchronous copies at the CTA's start (lines
+ * of at most 256).  Every plan computes bit-identical results (each line's
+ * arithmetic does not depend on the plan), only the speed differs.
  *
  * ftr_autotune times each pass's candidate F on this context's grid (a few
  * launches each, on the context's own buffers, so no frame may be pending:
@@ -253,10 +255,10 @@ int64_t ftr_device_bytes(const ftr_ctx* ctx);
  * divide the grid and leave at least two CTAs resident per SM (one CTA that
  * fills an SM stalls when other contexts' frames run concurrently).  The
  * choice is cached per device and grid for the process: later contexts of
- * the same grid take it without timing.  report (nullable): 9 floats,
- * microseconds per launch of F = 8, 16, 32 for the y, z and inverse-y passes
- * (0 = not timed: cached or not a candidate).  Waits for the stream.  Split
- * precision contexts keep F = 16 (their passes have no variants).
+ * the same grid take it without timing.  report (nullable): 12 floats,
+ * microseconds per launch of F = 8, 16, 32, -16 for the y, z and inverse-y
+ * passes (0 = not timed: cached or not a candidate).  Waits for the stream.
+ * Split precision contexts keep F = 16 (their passes have no variants).
  */
 int ftr_autotune(ftr_ctx* ctx, float* report);
 
@@ -264,7 +266,8 @@ int ftr_autotune(ftr_ctx* ctx, float* report);
 int ftr_get_plan(const ftr_ctx* ctx, int* plan);
 
 /* Force a plan: each entry 8, 16 or 32 and a divisor of the axis the pass
- * tiles (n_z for the y passes, n_y for the z pass), else FTR_EINVAL. */
+ * tiles (n_z for the y passes, n_y for the z pass), or -16 for the y pass
+ * when 16 divides n_z and n_y <= 256; else FTR_EINVAL. */
 int ftr_set_plan(ftr_ctx* ctx, const int* plan);
 
 /* Message of the last error on this context (never NULL). */

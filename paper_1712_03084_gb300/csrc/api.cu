@@ -38,13 +38,21 @@ int cuda_fail(ftr_ctx* c, cudaError_t e, const char* what) {
 // After a stream synchronisation: FTR_ETIMEOUT if a tensor-core completion
 // wait of the split-precision passes gave up since the last check.
 int tc_check(ftr_ctx* c, const char* who) {
-    if (!c->d_tc_err) return FTR_OK;
-    int flag = 0;
-    cudaError_t e = cudaMemcpy(&flag, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, who);
-    if (!flag) return FTR_OK;
-    cudaMemset(c->d_tc_err, 0, sizeof(int));
-    return set_err(c, FTR_ETIMEOUT, "%s: a tensor-core completion wait timed out", who);
+    // the flags reached c->h_flags with the frame's last copy (see launch_flags)
+    if (!c->h_flags || (!c->h_flags[0] && !c->h_flags[1])) return FTR_OK;
+    c->h_flags[0] = c->h_flags[1] = 0;
+    if (c->d_tc_err) cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream);
+    if (c->d_kerr) cudaMemsetAsync(c->d_kerr, 0, sizeof(int), c->stream);
+    return set_err(c, FTR_ETIMEOUT, "%s: a device completion wait timed out", who);
+}
+
+// Enqueue the copy of the device wait flags into pinned host memory.
+cudaError_t launch_flags(ftr_ctx* c) {
+    cudaError_t e = cudaSuccess;
+    if (c->d_tc_err) e = cudaMemcpyAsync(&c->h_flags[0], c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && c->d_kerr)
+        e = cudaMemcpyAsync(&c->h_flags[1], c->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    return e;
 }
 
 void prof_begin(ftr_ctx* c, int st) {
@@ -200,6 +208,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_raw_total);
     if (c->h_raw_total) cudaFreeHost(c->h_raw_total);
     dfree(c->d_tc_err);
+    dfree(c->d_kerr);
     dfree(c->d_level);
     dfree(c->d_levelf);
     dfree(c->d_level_part);
@@ -209,6 +218,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_mc_bits);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
     dfree(c->d_mc_nodes);
     dfree(c->d_verts);
     dfree(c->d_vnrm);
@@ -311,6 +321,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_brick_slot, c->n_bricks);
     ALLOC(c->d_active, c->n_bricks);
     ALLOC(c->d_meta, 8);
+    ALLOC(c->d_kerr, 1);
     ALLOC(c->d_tile, (c->n_bricks + 2047) / 2048 + 1);
     ALLOC(c->d_vpool, (size_t)c->n_bricks * 3 * kBrickVox);
     ALLOC(c->d_s0, 3 * c->Mh);
@@ -332,7 +343,8 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     }
     ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
 #undef ALLOC
-    if ((e = cudaMallocHost((void**)&c->h_mc_tot, 4 * sizeof(int))) != cudaSuccess) {
+    if ((e = cudaMallocHost((void**)&c->h_mc_tot, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&c->h_flags, 2 * sizeof(int))) != cudaSuccess) {
         free_all(c);
         delete c;
         return FTR_ENOMEM;
@@ -371,6 +383,8 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     }
     cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_kerr, 0, sizeof(int), c->stream);
+    c->h_flags[0] = c->h_flags[1] = 0;
     cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
     cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
     double zero2[2] = {0.0, 0.0};
@@ -548,7 +562,8 @@ int ftr_solve(ftr_ctx* c, double* iso_level_out) {
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: level");
     c->solved = true;
     if (iso_level_out) {
-        if ((e = cudaMemcpyAsync(&c->level_host, c->d_level, sizeof(double), cudaMemcpyDeviceToHost, c->stream)))
+        if ((e = cudaMemcpyAsync(&c->level_host, c->d_level, sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
+            (e = launch_flags(c)))
             return cuda_fail(c, e, "ftr_solve: level copy");
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve");
         if (int st = tc_check(c, "ftr_solve")) return st;
@@ -603,7 +618,8 @@ int ftr_extract_mesh(ftr_ctx* c, ftr_mesh* out) {
     // counts, offsets and the emission run back to back; the host waits once
     if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: count");
     if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: emit");
-    if ((e = launch_mc_totals(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh: totals");
+    if ((e = launch_mc_totals(c)) != cudaSuccess || (e = launch_flags(c)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_extract_mesh: totals");
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh");
     if (int st = tc_check(c, "ftr_extract_mesh")) return st;
     const int64_t na = c->h_mc_tot[0], nv = c->h_mc_tot[1], nt = c->h_mc_tot[2];
@@ -785,7 +801,8 @@ cudaError_t enqueue_frame(ftr_ctx* c, const ViewSet& vs, float tol, const ftr_te
                                    out.rgb, out.textured);
         if (e != cudaSuccess) return e;
     }
-    return launch_mc_totals(c);
+    if ((e = launch_mc_totals(c)) != cudaSuccess) return e;
+    return launch_flags(c);
 }
 
 }  // namespace
@@ -867,7 +884,8 @@ int ftr_extract_mesh_async(ftr_ctx* c) {
     }
     if ((e = launch_mc_count(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: count");
     if ((e = launch_mc_emit(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: emit");
-    if ((e = launch_mc_totals(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_extract_mesh_async: totals");
+    if ((e = launch_mc_totals(c)) != cudaSuccess || (e = launch_flags(c)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_extract_mesh_async: totals");
     c->meshed = false;
     c->mesh_pending = true;
     c->tex_pending = false;
@@ -985,9 +1003,11 @@ std::map<std::tuple<int, int, int, int>, std::array<int, 3>> g_plans;   // (devi
 bool valid_lines(int f) { return f == 8 || f == 16 || f == 32; }
 
 // F lines per CTA must tile the axis the pass strides over (z for the y
-// passes, y for the z pass).
+// passes, y for the z pass).  -16: the y pass with bulk-copied tiles (16
+// lines, lines of at most 256).
 bool plan_fits(const ftr_ctx* c, int pass, int f) {
     const int n = pass == 1 ? c->g.n[1] : c->g.n[2];
+    if (f == -16) return pass == 0 && n % 16 == 0 && c->g.n[1] <= 256;
     return valid_lines(f) && n % f == 0;
 }
 }  // namespace
@@ -1012,7 +1032,7 @@ int ftr_set_plan(ftr_ctx* c, const int* plan) {
 int ftr_autotune(ftr_ctx* c, float* report) {
     if (!c) return FTR_EINVAL;
     if (report)
-        for (int i = 0; i < 9; ++i) report[i] = 0.f;
+        for (int i = 0; i < 12; ++i) report[i] = 0.f;
     if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_autotune: a frame is pending");
     if (c->p.precision != FTR_PREC_FP32) return FTR_OK;
     const auto key = std::make_tuple(c->device, c->g.n[0], c->g.n[1], c->g.n[2]);
@@ -1038,12 +1058,12 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
-    const int F[3] = {8, 16, 32};
+    const int F[4] = {8, 16, 32, -16};
     const int reps = 5;
     std::array<int, 3> best = {16, 16, 16};
     for (int pass = 0; pass < 3; ++pass) {
         float best_us = 1e30f;
-        for (int v = 0; v < 3; ++v) {
+        for (int v = 0; v < 4; ++v) {
             if (!plan_fits(c, pass, F[v])) continue;
             c->plan_lines[pass] = F[v];
             auto run = [&]() { return pass == 0 ? launch_fy(c) : (pass == 1 ? launch_fz(c) : launch_iy(c)); };
@@ -1073,7 +1093,7 @@ int ftr_autotune(ftr_ctx* c, float* report) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, t0, t1);
             const float us = 1000.f * ms / reps;
-            if (report) report[3 * pass + v] = us;
+            if (report) report[4 * pass + v] = us;
             if (us < best_us) {
                 best_us = us;
                 best[pass] = F[v];

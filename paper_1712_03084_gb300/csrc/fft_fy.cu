@@ -10,6 +10,7 @@
 // [k_x][k_y][z] (z fastest) for the z pass.
 #include "fft_common.cuh"
 #include "ftr_internal.h"
+#include "tc_sm100.cuh"
 
 namespace ftr {
 namespace {
@@ -95,6 +96,96 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
     }
 }
 
+// The same pass with the CTA's three component tiles (16 lines each, one
+// contiguous block per component) fetched by bulk asynchronous copies at
+// the start, so that all of its input is in flight at once; each tile's
+// buffer then serves as that component's exchange buffer, and the x
+// component's as the stash.  Waits are bounded (a timeout sets *err).
+template <int N>
+__global__ void __launch_bounds__(16 * Xchg<N, 16>::NT, 2)
+    k_fy_bulk(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
+              const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta, int* err) {
+    pdl_wait();
+    constexpr int F = 16;
+    using X = Xchg<N, F>;
+    constexpr int BUF = cmax(X::SIZE, (F + 1) * N);
+    constexpr uint32_t kBytes = F * N * sizeof(float2);
+    extern __shared__ __align__(16) float2 smem[];
+    __shared__ uint64_t mbar[3];
+    const int nz = g.n[2];
+    const int z0 = blockIdx.x * F;
+    const int kx = blockIdx.y;
+    const int tid = threadIdx.x;
+    int zl, zh;
+    live_z_range(meta, zl, zh);
+    if (z0 + F <= zl || z0 >= zh) return;
+    const size_t tile = (size_t)N * ((size_t)z0 + (size_t)nz * kx);
+    if (tid == 0) {
+        for (int c = 0; c < 3; ++c) tc::mbar_init(&mbar[c], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int c = 0; c < 3; ++c) {
+            tc::mbar_expect_tx(&mbar[c], kBytes);
+            tc::bulk_g2s(smem + c * BUF, s0 + (size_t)c * Mh + tile, kBytes, &mbar[c]);
+        }
+    }
+    __syncthreads();
+    const int f1 = tid / X::NT, r1 = tid % X::NT;
+    const int f2 = tid % F, i2 = tid / F;
+    const size_t out_base = (size_t)(z0 + f2) + (size_t)nz * ((size_t)N * kx);
+    float2* stash = smem;                      // the x component's buffer, once its exchange is done
+    float2 o[X::N2];
+    for (int c = 0; c < 3; ++c) {
+        float2* B = smem + c * BUF;
+        if (!tc::mbar_wait(&mbar[c], 0, 1u << 22)) atomicExch(err, 1);
+        float2 v[X::N1];
+        if (r1 < X::N2) {
+#pragma unroll
+            for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = B[f1 * N + X::N2 * n1 + r1];
+        }
+        __syncthreads();                       // the staged lines are in registers: B becomes the exchange
+        if (r1 < X::N2) fft_step1<N, F, -1>(v, f1, r1, B, tw);
+        __syncthreads();
+        if (i2 < X::N1) fft_step2<N, F, -1>(o, f2, i2, B);
+        if (c == 0) {
+            __syncthreads();                   // every exchange read done: B becomes the stash
+            if (i2 < X::N1) {
+#pragma unroll
+                for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (F + 1) * (i2 + X::N1 * k2)] = o[k2];
+            }
+        } else if (c == 1) {
+            if (i2 < X::N1) {
+#pragma unroll
+                for (int k2 = 0; k2 < X::N2; ++k2) {
+                    const int ky = i2 + X::N1 * k2;
+                    const float wy = (ky == N / 2) ? 0.f : wy_scale * (float)signed_bin(ky, N);
+                    const float2 w = stash[f2 + (F + 1) * ky];
+                    s1[out_base + (size_t)nz * ky] = make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x);
+                }
+            }
+        } else {
+            if (i2 < X::N1) {
+#pragma unroll
+                for (int k2 = 0; k2 < X::N2; ++k2) s1[Mh + out_base + (size_t)nz * (i2 + X::N1 * k2)] = o[k2];
+            }
+        }
+    }
+}
+
+template <int N>
+cudaError_t run_fy_bulk(ftr_ctx* c) {
+    using X = Xchg<N, 16>;
+    const size_t smem = sizeof(float2) * 3 * cmax(X::SIZE, 17 * N);
+    cudaError_t e = ensure_smem(k_fy_bulk<N>, smem, c->device);
+    if (e != cudaSuccess) return e;
+    if (c->occ_query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(c->occ_query, k_fy_bulk<N>, 16 * X::NT, smem);
+    dim3 grid(c->g.n[2] / 16, c->g.n[0] / 2 + 1);
+    const float wy_scale = (float)(2.0 * 3.14159265358979323846 / (c->g.n[1] * c->g.h[1]));
+    launch_pdl(k_fy_bulk<N>, grid, 16 * X::NT, smem, c->stream, c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy_scale,
+               c->d_meta, c->d_kerr);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 template <int N, int F>
 cudaError_t run_fy_f(ftr_ctx* c) {
     using X = Xchg<N, F>;
@@ -116,6 +207,9 @@ cudaError_t run_fy(ftr_ctx* c) {
     switch (c->plan_lines[0]) {
         case 8: return run_fy_f<N, 8>(c);
         case 32: return run_fy_f<N, 32>(c);
+        case -16:
+            if (N <= 256) return run_fy_bulk<N>(c);
+            return run_fy_f<N, 16>(c);
         default: return run_fy_f<N, 16>(c);
     }
 }

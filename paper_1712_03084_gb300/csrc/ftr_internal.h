@@ -117,10 +117,12 @@ struct ftr_ctx {
     float2* d_s1 = nullptr;    // 2 x Mh  [kx][ky][z]
     float* d_A = nullptr;      // M       [z][y][x]
     float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
-    int plan_lines[3] = {16, 16, 16};      // lines per CTA of the y, z and inverse-y passes
+    int plan_lines[3] = {16, 16, 16};      // lines per CTA of the y, z and inverse-y passes (-16: y pass
+                                           // with bulk-copied tiles)
     int* occ_query = nullptr;              // set: the pass launchers report occupancy instead of launching
     unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
     int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
+    int* d_kerr = nullptr;                 // set when a bulk-copy completion wait gave up
 
     // raw reconstruction scratch (ftr_splat_depth)
     float* d_raw = nullptr;                // 7 floats per pixel capacity: P (3), N (3), W
@@ -147,6 +149,7 @@ struct ftr_ctx {
     unsigned* d_mc_bits = nullptr; // inside bits, 32 nodes per word, rows padded to a power-of-two word count
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
+    int* h_flags = nullptr;        // pinned: the device wait flags (tensor-core, bulk copy) of the last frame
     int4* d_mc_nodes = nullptr;
     int64_t cap_mc_nodes = 0;
     float* d_verts = nullptr;
@@ -258,6 +261,7 @@ cudaError_t tc_prepare(ftr_ctx* c);
 cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan
 cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
 cudaError_t launch_mc_totals(ftr_ctx* c);      // totals (active, verts, tris) to h_mc_tot
+cudaError_t launch_flags(ftr_ctx* c);          // device wait flags to h_flags (api.cu)
 cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);
 cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev);
 cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);

@@ -1,5 +1,5 @@
 // Fifth-generation tensor-core primitives (tcgen05, Tensor Memory, mbarrier)
-// as inline PTX, for the split-precision DFT stages.
+// and bulk asynchronous copies, as inline PTX.
 //
 // Operands live in shared memory in the canonical K-major layout without
 // swizzle: a "core matrix" is 8 rows x 16 bytes stored contiguously (128 B);
@@ -75,6 +75,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
     for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
+}
+
+// Arrive on the mbarrier and raise the bytes it expects by `bytes`.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to this CTA's shared memory; completion is counted on mbar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
 }
 
 // Generic-proxy shared-memory writes become visible to the tensor cores.

@@ -281,11 +281,12 @@ def ftr_device_bytes(ctx):
 
 
 def ftr_autotune(ctx):
-    """Time the tile plans; returns the 3 x 3 microseconds per launch (rows: y,
-    z, inverse-y passes; columns: 8, 16, 32 lines per CTA; 0 = not timed)."""
-    rep = np.zeros(9, np.float32)
+    """Time the tile plans; returns the 3 x 4 microseconds per launch (rows: y,
+    z, inverse-y passes; columns: 8, 16, 32 lines per CTA and the bulk-copied
+    16-line y pass; 0 = not timed)."""
+    rep = np.zeros(12, np.float32)
     _check(load().ftr_autotune(ctx, rep.ctypes.data), ctx)
-    return rep.reshape(3, 3)
+    return rep.reshape(3, 4)
 
 
 def ftr_get_plan(ctx):

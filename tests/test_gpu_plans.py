@@ -1,4 +1,5 @@
-"""Tile plans of the y, z and inverse-y FFT passes (8, 16 or 32 lines per CTA).
+"""Tile plans of the y, z and inverse-y FFT passes (8, 16 or 32 lines per CTA;
+-16: the y pass with its tiles fetched by bulk asynchronous copies).
 
 Every plan runs the same per-line arithmetic, so the indicator must be
 bit-identical whatever the plan; the autotuner must pick a plan that fits
@@ -43,6 +44,8 @@ def test_every_plan_is_bit_identical(ftr, name):
     ref_A, ref_L = _field(ftr, name, (16, 16, 16))
     nx, ny, nz = c["grid"]
     choices = [[f for f in (8, 16, 32) if (ny if p == 1 else nz) % f == 0] for p in range(3)]
+    if nz % 16 == 0 and ny <= 256:
+        choices[0].append(-16)          # the y pass with bulk-copied tiles
     for plan in itertools.product(*choices):
         A, L = _field(ftr, name, plan)
         assert np.array_equal(A, ref_A), plan
@@ -64,9 +67,9 @@ def test_autotune_picks_a_fitting_plan_and_caches_it(ftr):
     a = ftr.Context(c["grid"], c["bbox"])
     rep = a.autotune()
     plan = a.plan()
-    assert rep.shape == (3, 3) and (rep[:, 1] > 0).all()       # F = 16 always fits and is timed
+    assert rep.shape == (3, 4) and (rep[:, 1] > 0).all()       # F = 16 always fits and is timed
     for p, f in enumerate(plan):
-        col = (8, 16, 32).index(f)
+        col = (8, 16, 32, -16).index(f)
         assert rep[p, col] > 0 and rep[p, col] == rep[p][rep[p] > 0].min()
     b = ftr.Context(c["grid"], c["bbox"])
     rep_b = b.autotune()
