@@ -439,6 +439,7 @@ def run_ours(args, rank, world, local_rank):
         ctx = None
         multi = run_multi(args, rank, dev, plain_frame=fr)
     from_depth = run_from_depth(args, rank, dev, fr, flush) if not args.no_multi else None
+    table1 = run_table1(args, rank, dev, fr, flush) if not args.no_multi else None
     prec = None
     if not args.no_precision:
         if ctx is not None:
@@ -478,6 +479,8 @@ def run_ours(args, rank, world, local_rank):
         line.update(multi)
     if from_depth:
         line.update(from_depth)
+    if table1:
+        line.update(table1)
     if prec:
         line.update(prec)
     return line
@@ -755,6 +758,62 @@ def run_from_depth(args, rank, dev, fr, flush):
                      "per frame (the raw stage waits once for its point count); host_inputs copies depth and "
                      "RGB in and the mesh and colours out")
     return {"from_depth": res}
+
+
+TABLE1_PAPER_MS = {5: (10.0, 17.0), 6: (22.0, 27.0), 7: (102.0, 163.0)}   # (simple, weighted), GTX 560
+
+
+def run_table1(args, rank, dev, fr, flush):
+    """The paper's Table I axis on GB300: simple vs weighted splat at its grid
+    shapes 2^r x 2^(r+1) x 2^r (r = 5, 6, 7) over a 1 x 2 x 1 m box around the
+    body, the same 4-camera frame; reconstruction only (splat, transforms,
+    level, marching cubes: one graph frame without texture), device-timed."""
+    import torch
+    from paper_1712_03084_gb300 import ftr
+    box = (-0.5, -0.05, -0.5, 0.5, 1.95, 0.5)
+    P = torch.from_numpy(fr["points"]).to(dev)
+    N = torch.from_numpy(fr["normals"]).to(dev)
+    W = torch.from_numpy(fr["weights"]).to(dev)
+    cams = list(fr["per_camera"])
+    steps = max(10, min(args.steps, 50))
+    out = {}
+    for r in (5, 6, 7):
+        grid = (2 ** r, 2 ** (r + 1), 2 ** r)
+        row = {"grid": list(grid)}
+        for mode, name in ((ftr.FTR_SPLAT_SIMPLE, "simple"), (ftr.FTR_SPLAT_WEIGHTED, "weighted")):
+            stream = torch.cuda.Stream(device=dev)
+            ctx = ftr.Context(grid, box, stream=stream.cuda_stream, splat_mode=mode)
+            ctx.autotune()
+
+            def frame():
+                ctx.reset()
+                for (s, n) in cams:
+                    ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+                ftr.ftr_frame_launch(ctx.h, [], 0.0)
+
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for _ in range(4):
+                    frame()
+                    ftr.ftr_frame_finish(ctx.h)
+                for i in range(steps):
+                    flush.fill_(float(i))
+                    evs[i][0].record(stream)
+                    frame()
+                    evs[i][1].record(stream)
+                    ftr.ftr_frame_finish(ctx.h)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            info = ctx.frame_info()
+            ctx.close()
+            paper = TABLE1_PAPER_MS[r][0 if name == "simple" else 1]
+            row[name] = {"ms": round(ms, 4), "vertices": int(info["n_vertices"]), "dropped": int(info["dropped"]),
+                         "paper_ms_gtx560": paper, "paper_over_ours": round(paper / ms, 1)}
+        out[f"r{r}"] = row
+    out["config"] = ("Table I axis: grids 2^r x 2^(r+1) x 2^r over a 1 x 2 x 1 m box, the human256 frame's 40,722 "
+                     "points (points outside the box dropped), splat to mesh without texture, CUDA events per "
+                     "frame, L2 flushed between frames; paper times (GTX 560, Argyris sequence) are context only")
+    return {"table1": out}
 
 
 def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):

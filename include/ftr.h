@@ -285,6 +285,14 @@ int ftr_set_field_V(ftr_ctx* ctx, const float* V);
 int ftr_get_field_A(ftr_ctx* ctx, float* out);
 /* Replace A and L (e.g. with another implementation's) before ftr_extract_mesh. */
 int ftr_set_indicator(ftr_ctx* ctx, const float* A, double level);
+/*
+ * The binarised volume of the last solve (Sec. IV feeds it to the skeleton
+ * extraction): bit = 1 iff A >= L (the marching-cubes inside test).  Layout:
+ * grid row r = y + n_y z holds ceil(n_x / 32) words, bit i of word w is node
+ * x = 32 w + i (bits past n_x are 0); out (host or device) holds
+ * n_y n_z ceil(n_x / 32) words.  FTR_ESTATE before a solve.  Waits.
+ */
+int ftr_get_inside_mask(ftr_ctx* ctx, uint32_t* out);
 /* Cube class (uint8) per cell, (n_z-1) x (n_y-1) x (n_x-1), of the current A, L. */
 int ftr_get_cube_classes(ftr_ctx* ctx, uint8_t* out);
 /* Raw copy of an internal spectrum buffer after ftr_solve: which = 0 the

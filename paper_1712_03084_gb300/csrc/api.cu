@@ -1226,6 +1226,21 @@ int ftr_get_cube_classes(ftr_ctx* c, uint8_t* out) {
     return FTR_OK;
 }
 
+int ftr_get_inside_mask(ftr_ctx* c, uint32_t* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (!c->solved) return set_err(c, FTR_ESTATE, "ftr_get_inside_mask: nothing solved");
+    cudaError_t e = launch_mc_bits(c);
+    const int wp = mc_words_per_row(c->g.n[0]);
+    const int nw = (c->g.n[0] + 31) / 32;
+    const cudaMemcpyKind kind = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(out, sizeof(uint32_t) * nw, c->d_mc_bits, sizeof(unsigned) * wp, sizeof(uint32_t) * nw,
+                              (size_t)c->mc_blocks, kind, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_get_inside_mask");
+    return FTR_OK;
+}
+
 int ftr_frame_info(ftr_ctx* c, int64_t* info, int n) {
     if (!c || !info || n < 0) return FTR_EINVAL;
     int meta[4] = {0, 0, 0, -1};

@@ -258,6 +258,8 @@ size_t tc_table_bytes();
 void tc_build_table(int precision, std::vector<unsigned char>& out);
 cudaError_t launch_tc_pass(ftr_ctx* c, int pass);
 cudaError_t tc_prepare(ftr_ctx* c);
+cudaError_t launch_mc_bits(ftr_ctx* c);        // inside bits A >= L only
+int mc_words_per_row(int nx);                  // padded words per grid row of the inside bits
 cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan
 cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
 cudaError_t launch_mc_totals(ftr_ctx* c);      // totals (active, verts, tris) to h_mc_tot

@@ -515,6 +515,16 @@ static int mc_words(int nx) {
     return wp;
 }
 
+cudaError_t launch_mc_bits(ftr_ctx* c) {
+    const int nr = c->mc_blocks;
+    launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
+               c->d_mc_bits, nr, mc_words(c->g.n[0]));
+    c->launches++;
+    return cudaGetLastError();
+}
+
+int mc_words_per_row(int nx) { return mc_words(nx); }
+
 cudaError_t launch_mc_count(ftr_ctx* c) {
     const int nr = c->mc_blocks;              // grid rows n_y n_z
     const int wp = mc_words(c->g.n[0]);

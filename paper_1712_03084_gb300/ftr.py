@@ -91,6 +91,7 @@ _SIGNATURES = [
     ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_indicator", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     ("ftr_get_cube_classes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_get_inside_mask", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_debug_buffer", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
     ("ftr_mc_table", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -463,6 +464,15 @@ class Context:
 
     def set_indicator(self, A, level):
         ftr_set_indicator(self.h, np.ascontiguousarray(A, dtype=np.float32), level)
+
+    def inside_mask(self):
+        """Binarised volume A >= L as bool [n_z, n_y, n_x]."""
+        nx, ny, nz = self.grid_n
+        nw = (nx + 31) // 32
+        words = np.zeros((nz, ny, nw), np.uint32)
+        _check(load().ftr_get_inside_mask(self.h, words.ctypes.data), self.h)
+        bits = np.unpackbits(words.view(np.uint8), axis=-1, bitorder="little")
+        return bits[..., :nx].astype(bool)
 
     def cube_classes(self):
         nx, ny, nz = self.grid_n

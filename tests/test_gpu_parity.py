@@ -290,3 +290,17 @@ def test_graph_frame_equals_separate_calls(ftr):
         assert np.array_equal(outs[0][:nv].cpu().numpy(), t_ref["weights"])
         assert np.array_equal(outs[2][:nv].cpu().numpy(), t_ref["rgb"])
     g.close()
+
+
+@pytest.mark.parametrize("name", ["sphere64", "human_aniso"])
+def test_inside_mask_is_the_binarised_volume(ftr, name):
+    """The exported binarised volume (Sec. IV's input) is exactly A >= L of
+    the solved field and level, and matches the oracle's classification."""
+    ctx, L = _run(ftr, name)
+    A = ctx.field_A()
+    m = ctx.inside_mask()
+    ctx.close()
+    assert np.array_equal(m, A.astype(np.float64) >= L)
+    r = G.oracle_result(name)
+    agree = np.mean(m == (r["A"] >= r["L"]))
+    assert agree > 0.9999
