@@ -177,7 +177,20 @@ cudaError_t grow_entries(ftr_ctx* c, int64_t need) {
     cudaStreamSynchronize(c->stream);
     dfree(c->d_entries);
     cudaError_t e = dalloc(&c->d_entries, cap);
-    if (e == cudaSuccess) c->cap_entries = cap;
+    if (e != cudaSuccess) return e;
+    c->cap_entries = cap;
+    // a heavy brick has more than one chunk of pairs: at most cap / chunk of them
+    const int64_t heavy = cap / kSplatChunk + 1;
+    if (heavy > c->cap_heavy) {
+        dfree(c->d_heavy_acc);
+        dfree(c->d_heavy_done);
+        if ((e = dalloc(&c->d_heavy_acc, (size_t)heavy * 4 * kBrickVox)) != cudaSuccess) return e;
+        if ((e = dalloc(&c->d_heavy_done, (size_t)heavy)) != cudaSuccess) return e;
+        if ((e = cudaMemset(c->d_heavy_acc, 0, sizeof(unsigned long long) * heavy * 4 * kBrickVox)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemset(c->d_heavy_done, 0, sizeof(int) * heavy)) != cudaSuccess) return e;
+        c->cap_heavy = heavy;
+    }
     return e;
 }
 
@@ -196,6 +209,10 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_active);
     dfree(c->d_meta);
     dfree(c->d_tile);
+    dfree(c->d_unit_off);
+    dfree(c->d_heavy_idx);
+    dfree(c->d_heavy_acc);
+    dfree(c->d_heavy_done);
     dfree(c->d_entries);
     dfree(c->d_vpool);
     dfree(c->d_s0);
@@ -323,6 +340,8 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_meta, 8);
     ALLOC(c->d_kerr, 1);
     ALLOC(c->d_tile, (c->n_bricks + 2047) / 2048 + 1);
+    ALLOC(c->d_unit_off, c->n_bricks + 1);
+    ALLOC(c->d_heavy_idx, c->n_bricks);
     ALLOC(c->d_vpool, (size_t)c->n_bricks * 3 * kBrickVox);
     ALLOC(c->d_s0, 3 * c->Mh);
     ALLOC(c->d_s1, 2 * c->Mh);
@@ -1121,6 +1140,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     b += (int64_t)c->stage_cap + (int64_t)c->tex_stage_cap;
     b += nb * (int64_t)sizeof(int) * 5 + (nb / 2048 + 1) * (int64_t)sizeof(int2) + 64;
     b += c->cap_entries * (int64_t)sizeof(int);
+    b += c->cap_heavy * (4 * kBrickVox * 8 + 4) + nb * 8;   // heavy-brick accumulators, chunk offsets
     b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
     b += 5 * c->Mh * (int64_t)sizeof(float2) + c->M * (int64_t)sizeof(float);
     b += (int64_t)(c->g.n[0] + c->g.n[1] + c->g.n[2]) * (int64_t)sizeof(float2);

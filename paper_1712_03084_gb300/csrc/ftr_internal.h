@@ -17,6 +17,7 @@ constexpr int kBrickVox = kBrick * kBrick * kBrick;
 constexpr int kMaxViews = 8;
 constexpr int kMcThreads = 256;           // marching-cubes CTA size (chunks of 8 grid rows)
 constexpr int kMaxTrisPerCase = 5;
+constexpr int kSplatChunk = 1024;          // (point, brick) pairs per accumulation work unit
 
 enum Stage {
     ST_INGEST = 0,
@@ -106,8 +107,14 @@ struct ftr_ctx {
     int* d_brick_cursor = nullptr;
     int* d_brick_slot = nullptr;
     int* d_active = nullptr;
-    int* d_meta = nullptr;     // [0] active bricks, [1] entries, [2] min bz, [3] max bz, [4] accumulation ticket
-    int2* d_tile = nullptr;    // per-tile sums / offsets of the brick scan
+    int* d_meta = nullptr;     // [0] active bricks, [1] entries, [2] min bz, [3] max bz, [4] accumulation
+                               // ticket, [5] accumulation chunks, [6] heavy bricks
+    int4* d_tile = nullptr;    // per-tile sums / offsets of the brick scan (pairs, touched, chunks, heavy)
+    int* d_unit_off = nullptr; // per touched brick: first accumulation chunk; [touched] = all chunks
+    int* d_heavy_idx = nullptr;  // per touched brick: index of its global accumulator, -1 for one chunk
+    unsigned long long* d_heavy_acc = nullptr;   // 4 x 512 int64 per heavy brick (zero between frames)
+    int* d_heavy_done = nullptr; // chunks finished per heavy brick (zero between frames)
+    int64_t cap_heavy = 0;
     int* d_entries = nullptr;
     int64_t cap_entries = 0;
     float* d_vpool = nullptr;  // active bricks x 3 x 512 V values

@@ -181,101 +181,134 @@ __global__ void k_brick_fill(const int4* __restrict__ pbase, const int64_t* __re
 // touched brick (-1 otherwise), the list of touched bricks and the z-range.
 constexpr int kScanT = 256;
 constexpr int kTile = 2048;
+// A brick's pairs are accumulated in chunks of at most kChunk (point, brick)
+// pairs, one chunk per CTA at a time; the 32-bit hi/lo accumulators stay exact
+// for up to 2047 contributions per voxel.
+constexpr int kChunk = kSplatChunk;
 
-__device__ __forceinline__ int2 block_scan2(int2 v, int2& total, int2* sh) {
+// Block-wide exclusive scan of four ints per thread (kScanT threads).
+__device__ __forceinline__ int4 block_scan4(int4 v, int4& total, int4* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int2 inc = v;
+    int4 inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int a = __shfl_up_sync(0xffffffffu, inc.x, o);
         const int b = __shfl_up_sync(0xffffffffu, inc.y, o);
+        const int c = __shfl_up_sync(0xffffffffu, inc.z, o);
+        const int d = __shfl_up_sync(0xffffffffu, inc.w, o);
         if (lane >= o) {
             inc.x += a;
             inc.y += b;
+            inc.z += c;
+            inc.w += d;
         }
     }
     if (lane == 31) sh[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        int2 w = lane < kScanT / 32 ? sh[lane] : make_int2(0, 0);
+        int4 w = lane < kScanT / 32 ? sh[lane] : make_int4(0, 0, 0, 0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int a = __shfl_up_sync(0xffffffffu, w.x, o);
             const int b = __shfl_up_sync(0xffffffffu, w.y, o);
+            const int c = __shfl_up_sync(0xffffffffu, w.z, o);
+            const int d = __shfl_up_sync(0xffffffffu, w.w, o);
             if (lane >= o) {
                 w.x += a;
                 w.y += b;
+                w.z += c;
+                w.w += d;
             }
         }
         if (lane < kScanT / 32) sh[lane] = w;
     }
     __syncthreads();
-    const int2 before = wid ? sh[wid - 1] : make_int2(0, 0);
+    const int4 before = wid ? sh[wid - 1] : make_int4(0, 0, 0, 0);
     total = sh[kScanT / 32 - 1];
     __syncthreads();
-    return make_int2(before.x + inc.x - v.x, before.y + inc.y - v.y);
+    return make_int4(before.x + inc.x - v.x, before.y + inc.y - v.y, before.z + inc.z - v.z,
+                     before.w + inc.w - v.w);
 }
 
-__global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restrict__ cnt, int nb, int2* tile_sum) {
+// Per brick of c (point, brick) pairs: (pairs, touched, accumulation chunks,
+// heavy = more than one chunk).
+__device__ __forceinline__ int4 brick_counts(int c) {
+    const int ch = (c + kChunk - 1) / kChunk;
+    return make_int4(c, c > 0, ch, ch > 1);
+}
+
+__global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restrict__ cnt, int nb, int4* tile_sum) {
     pdl_wait();
-    __shared__ int2 sh[kScanT / 32];
-    int2 v = make_int2(0, 0);
+    __shared__ int4 sh[kScanT / 32];
+    int4 v = make_int4(0, 0, 0, 0);
     for (int k = 0; k < kTile / kScanT; ++k) {
         const int b = blockIdx.x * kTile + k * kScanT + threadIdx.x;
         if (b < nb) {
-            const int c = cnt[b];
-            v.x += c;
-            v.y += (c > 0);
+            const int4 q = brick_counts(cnt[b]);
+            v.x += q.x;
+            v.y += q.y;
+            v.z += q.z;
+            v.w += q.w;
         }
     }
-    int2 tot;
-    block_scan2(v, tot, sh);
+    int4 tot;
+    block_scan4(v, tot, sh);
     if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
 }
 
 // One CTA: exclusive scan of the tile sums in place; totals into meta.
-__global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int2* tile_sum, int ntiles, int nb, int* off,
-                                                            int* meta) {
+__global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int4* tile_sum, int ntiles, int nb, int* off,
+                                                            int* meta, int* unit_off) {
     pdl_wait();
-    __shared__ int2 sh[kScanT / 32];
-    int2 carry = make_int2(0, 0);
+    __shared__ int4 sh[kScanT / 32];
+    int4 carry = make_int4(0, 0, 0, 0);
     for (int base = 0; base < ntiles; base += kScanT) {
         const int i = base + threadIdx.x;
-        const int2 v = i < ntiles ? tile_sum[i] : make_int2(0, 0);
-        int2 tot;
-        const int2 ex = block_scan2(v, tot, sh);
-        if (i < ntiles) tile_sum[i] = make_int2(carry.x + ex.x, carry.y + ex.y);
+        const int4 v = i < ntiles ? tile_sum[i] : make_int4(0, 0, 0, 0);
+        int4 tot;
+        const int4 ex = block_scan4(v, tot, sh);
+        if (i < ntiles) tile_sum[i] = make_int4(carry.x + ex.x, carry.y + ex.y, carry.z + ex.z, carry.w + ex.w);
         carry.x += tot.x;
         carry.y += tot.y;
+        carry.z += tot.z;
+        carry.w += tot.w;
     }
     if (threadIdx.x == 0) {
         off[nb] = carry.x;
+        unit_off[carry.y] = carry.z;   // end of the last touched brick's chunks
         meta[0] = carry.y;
         meta[1] = carry.x;
         meta[2] = 0x7fffffff;
         meta[3] = -1;
-        meta[4] = 0;                // brick ticket of the accumulation
+        meta[4] = 0;                   // chunk ticket of the accumulation
+        meta[5] = carry.z;             // chunks in all
+        meta[6] = carry.w;             // heavy bricks
     }
 }
 
 __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restrict__ cnt, int nb, int nbxy,
-                                                             const int2* __restrict__ tile_off, int* off,
-                                                             int* cursor, int* slot, int* active, int* meta) {
+                                                             const int4* __restrict__ tile_off, int* off,
+                                                             int* cursor, int* slot, int* active, int* meta,
+                                                             int* unit_off, int* heavy_idx) {
     pdl_wait();
-    __shared__ int2 sh[kScanT / 32];
-    int2 run = tile_off[blockIdx.x];
+    __shared__ int4 sh[kScanT / 32];
+    int4 run = tile_off[blockIdx.x];
     int zmin = 0x7fffffff, zmax = -1;
     for (int k = 0; k < kTile / kScanT; ++k) {
         const int b = blockIdx.x * kTile + k * kScanT + threadIdx.x;
         const int c = b < nb ? cnt[b] : 0;
-        int2 tot;
-        const int2 ex = block_scan2(make_int2(c, c > 0), tot, sh);
+        const int4 q = brick_counts(c);
+        int4 tot;
+        const int4 ex = block_scan4(q, tot, sh);
         if (b < nb) {
             off[b] = run.x + ex.x;
             cursor[b] = run.x + ex.x;
             if (c > 0) {
-                slot[b] = run.y + ex.y;
-                active[run.y + ex.y] = b;
+                const int s = run.y + ex.y;
+                slot[b] = s;
+                active[s] = b;
+                unit_off[s] = run.z + ex.z;
+                heavy_idx[s] = q.w ? run.w + ex.w : -1;
                 const int bz = b / nbxy;
                 zmin = min(zmin, bz);
                 zmax = max(zmax, bz);
@@ -285,6 +318,8 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restri
         }
         run.x += tot.x;
         run.y += tot.y;
+        run.z += tot.z;
+        run.w += tot.w;
     }
     if (zmax >= 0) {
         atomicMin(&meta[2], zmin);
@@ -316,7 +351,6 @@ __device__ __forceinline__ float fix_to_float(long long v) {
 }
 
 constexpr int kStage = 128;       // point records staged in shared memory per batch
-constexpr int kFastEntries = 2047; // the split accumulators stay exact up to this many points per brick
 
 // Fixed-point contribution round(v * 2^40) = hi 2^20 + lo with two float to
 // int conversions: hi = round(v 2^20); r = v - hi 2^-20 is exact (Sterbenz,
@@ -328,14 +362,18 @@ __device__ __forceinline__ void fix40_split(float v, int& hi, int& lo) {
     lo = __float2int_rn(fmaf(hf, -9.5367431640625e-07f, v) * 1099511627776.0f);
 }
 
-// One CTA per touched brick (persistent over the list).  64 lanes per point
-// evaluate the stencil nodes that fall inside the brick and add the
-// fixed-point contributions to shared-memory accumulators.  Integer sums are
-// exact and order-independent, so V is bit-reproducible.  Fast path: 32-bit
+// Persistent CTAs take work units from a per-frame ticket: a unit is one
+// chunk of at most kChunk (point, brick) pairs of one touched brick.  64
+// lanes per point evaluate the stencil nodes that fall inside the brick and
+// add the fixed-point contributions to shared-memory accumulators.  Integer
+// sums are exact and order-independent, so V is bit-reproducible.  32-bit
 // atomics on the (hi, lo) parts, exact while a voxel receives fewer than 2^11
-// contributions of magnitude <= 1 (at most kFastEntries points per brick,
-// weights in [0, 1]: |sum hi| < 2^31, |sum lo| < 2^30); otherwise the brick
-// takes the 64-bit atomic path.
+// contributions of magnitude <= 1 (a chunk has at most kChunk points; weights
+// in [0, 1]: |sum hi| < 2^31, |sum lo| < 2^30); weights outside [0, 1] take
+// 64-bit shared atomics.  A brick of one chunk writes V directly; the chunks
+// of a heavier brick add their exact sums into its int64 accumulator in
+// global memory, and the chunk that completes last (a per-brick counter)
+// writes V and clears the accumulator for the next frame.
 __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const int* __restrict__ active,
                                                              const int* __restrict__ meta,
                                                              const int* __restrict__ off,
@@ -344,7 +382,11 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const float4* __restrict__ pfrac,
                                                              const float4* __restrict__ pnrm,
                                                              const int* __restrict__ wild_weights,
-                                                             float* __restrict__ vpool, int* __restrict__ ticket) {
+                                                             float* __restrict__ vpool, int* __restrict__ ticket,
+                                                             const int* __restrict__ unit_off,
+                                                             const int* __restrict__ heavy_idx,
+                                                             unsigned long long* __restrict__ heavy_acc,
+                                                             int* __restrict__ heavy_done) {
     pdl_wait();
     __shared__ __align__(16) unsigned acc[8][kBrickVox];   // fast: [c] hi, [4 + c] lo; slow: 4 x int64
     __shared__ int4 s_base[kStage];
@@ -357,20 +399,35 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
     const int ox = o & 3, oy = (o >> 2) & 3, oz = o >> 4;
     const int pl = tid >> 6;
     const bool weights_ok = wild_weights[0] == 0;
-    __shared__ int s_brick;
-    // bricks are taken one at a time from a shared ticket, so that CTAs that
-    // drew light bricks go on to the next ones (brick costs vary with their
-    // point counts)
+    const int nunits = meta[5];
+    __shared__ int s_unit, s_slot;
+    __shared__ bool s_last;
     for (;;) {
-        if (tid == 0) s_brick = atomicAdd(ticket, 1);
+        if (tid == 0) {
+            const int u = atomicAdd(ticket, 1);
+            int sl = 0;
+            if (u < nunits) {      // the touched brick whose chunks hold unit u
+                int lo = 0, hi = nact - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (unit_off[mid] <= u) lo = mid;
+                    else hi = mid - 1;
+                }
+                sl = lo;
+            }
+            s_unit = u;
+            s_slot = sl;
+        }
         __syncthreads();
-        const int s = s_brick;
-        if (s >= nact) break;                                           // block-uniform
+        const int unit = s_unit, s = s_slot;
+        if (unit >= nunits) break;                                      // block-uniform
         const int b = active[s];
         const int bx = b % g.nb[0], by = (b / g.nb[0]) % g.nb[1], bz = b / (g.nb[0] * g.nb[1]);
         const int orgx = bx * kBrick, orgy = by * kBrick, orgz = bz * kBrick;
-        const int e0 = off[b], e1 = off[b + 1];
-        const bool fast = weights_ok && (e1 - e0) <= kFastEntries;     // block-uniform
+        const int nchunks = unit_off[s + 1] - unit_off[s];
+        const int e0 = off[b] + (unit - unit_off[s]) * kChunk;
+        const int e1 = min(off[b + 1], e0 + kChunk);
+        const bool fast = weights_ok;                                   // block-uniform
         for (int k = tid; k < 8 * kBrickVox; k += kAccThreads) (&acc[0][0])[k] = 0u;
         for (int eb = e0; eb < e1; eb += kStage) {
             const int nbatch = min(kStage, e1 - eb);
@@ -443,12 +500,37 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
         }
         __syncthreads();
         float* out = vpool + (size_t)s * 3 * kBrickVox;
+        unsigned long long* gacc = nullptr;
+        if (nchunks > 1) {
+            // add this chunk's exact sums to the brick's global accumulator
+            gacc = heavy_acc + (size_t)heavy_idx[s] * 4 * kBrickVox;
+            for (int li = tid; li < kBrickVox; li += kAccThreads) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const long long v = fast ? (long long)(int)acc[c][li] * (1ll << 20) + (long long)(int)acc[4 + c][li]
+                                             : (long long)acc64[c * kBrickVox + li];
+                    if (v != 0) atomicAdd(&gacc[c * kBrickVox + li], (unsigned long long)v);
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(&heavy_done[heavy_idx[s]], 1) == nchunks - 1;
+            __syncthreads();
+            if (!s_last) continue;                                      // block-uniform; next unit
+            __threadfence();
+        }
         for (int li = tid; li < kBrickVox; li += kAccThreads) {
             long long u[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                u[c] = fast ? (long long)(int)acc[c][li] * (1ll << 20) + (long long)(int)acc[4 + c][li]
-                            : (long long)acc64[c * kBrickVox + li];
+            for (int c = 0; c < 4; ++c) {
+                if (gacc) {
+                    u[c] = (long long)__ldcg(&gacc[c * kBrickVox + li]);
+                    gacc[c * kBrickVox + li] = 0ull;                    // cleared for the next frame
+                } else {
+                    u[c] = fast ? (long long)(int)acc[c][li] * (1ll << 20) + (long long)(int)acc[4 + c][li]
+                                : (long long)acc64[c * kBrickVox + li];
+                }
+            }
             if (u[3] > 0) {
                 // exact integer sums, one float32 quotient per voxel
                 const float sc = g.v_scale_f / fix_to_float(u[3]);
@@ -461,6 +543,7 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                 out[2 * kBrickVox + li] = 0.f;
             }
         }
+        if (gacc && tid == 0) heavy_done[heavy_idx[s]] = 0;
         __syncthreads();
     }
 }
@@ -521,10 +604,11 @@ cudaError_t launch_splat(ftr_ctx* c) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ntiles = (c->n_bricks + kTile - 1) / kTile;
     launch_pdl(k_brick_tile_sums, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->d_tile);
-    launch_pdl(k_brick_tile_scan, 1, kScanT, 0, c->stream, c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta);
+    launch_pdl(k_brick_tile_scan, 1, kScanT, 0, c->stream, c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta,
+               c->d_unit_off);
     launch_pdl(k_brick_tile_write, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
-                                                        c->d_tile, c->d_brick_off, c->d_brick_cursor,
-                                                        c->d_brick_slot, c->d_active, c->d_meta);
+               c->d_tile, c->d_brick_off, c->d_brick_cursor, c->d_brick_slot, c->d_active, c->d_meta, c->d_unit_off,
+               c->d_heavy_idx);
     c->launches += 3;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     launch_pdl(k_brick_fill, sms * 2, 256, 0, c->stream, c->pts.base, c->d_npts, c->g, c->d_brick_cursor, c->d_entries);
@@ -534,7 +618,8 @@ cudaError_t launch_splat(ftr_ctx* c) {
     prof_begin(c, ST_SPLAT_ACC);
     const int grid = sms * 4;
     launch_pdl(k_splat_accum, grid, kAccThreads, 0, c->stream, c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
-               c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool, c->d_meta + 4);
+               c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool, c->d_meta + 4, c->d_unit_off,
+               c->d_heavy_idx, c->d_heavy_acc, c->d_heavy_done);
     c->launches++;
     prof_end(c, ST_SPLAT_ACC);
     return cudaGetLastError();

@@ -31,6 +31,8 @@ CASES = {
     "human96": dict(kind="human", grid=(96, 96, 96), bbox=frame_config("human96")["bbox"], seed=11),
     "human_aniso": dict(kind="human", grid=(48, 96, 48), bbox=(-0.75, -0.05, -0.75, 0.75, 1.95, 0.75), seed=12),
     "human128": dict(kind="human", grid=(128, 128, 128), bbox=frame_config("human128")["bbox"], seed=13),
+    # dense: ~3000 (point, brick) pairs per 8^3 brick, so bricks span several accumulation chunks
+    "sphere32_dense": dict(kind="sphere", grid=(32, 32, 32), bbox=(-1.2, -1.2, -1.2, 1.2, 1.2, 1.2), n=60000),
 }
 
 SMALL_VIEWS = dict(depth_wh=(256, 212), fxy=182.5, rgb_wh=(480, 270), rgb_f=265.0)
@@ -40,7 +42,7 @@ SMALL_VIEWS = dict(depth_wh=(256, 212), fxy=182.5, rgb_wh=(480, 270), rgb_f=265.
 def case_inputs(name):
     c = CASES[name]
     if c["kind"] == "sphere":
-        P, N, W = sphere_points(20000, 0.005, seed=0)
+        P, N, W = sphere_points(c.get("n", 20000), 0.005, seed=0)
         return P, N, W, None
     fr = human_frame(seed=c["seed"], **SMALL_VIEWS)
     return fr["points"], fr["normals"], fr["weights"], fr["views"]
