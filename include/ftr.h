@@ -169,6 +169,16 @@ typedef struct {
 int ftr_splat_depth(ftr_ctx* ctx, const ftr_view* views, int k, double step, double noise, int radius,
                     float* const* conf_out);
 
+/*
+ * The same without any host wait: the ingest reads the point count on the
+ * device, so a whole frame (ftr_reset, this call, ftr_frame_launch) is
+ * queued at once.  It must be the frame's only point source: FTR_ESTATE if
+ * points were added since ftr_reset, and ftr_splat / ftr_splat_depth refuse
+ * until the next ftr_reset.  ftr_stats then reads the count from the device.
+ */
+int ftr_splat_depth_async(ftr_ctx* ctx, const ftr_view* views, int k, double step, double noise, int radius,
+                          float* const* conf_out);
+
 typedef struct {
     float* weights;           /* n_vertices x k: W_k at the vertex, 0 if not visible       */
     float* uv;                /* n_vertices x k x 2: RGB pixel coords, (-1,-1) if w = 0    */

@@ -430,6 +430,7 @@ int ftr_reset(ftr_ctx* c) {
     if (!c) return FTR_EINVAL;
     c->n_pts = 0;
     c->points_in = 0;
+    c->depth_async = false;
     c->solved = false;
     c->v_external = false;
     c->meshed = false;
@@ -443,6 +444,7 @@ int ftr_reset(ftr_ctx* c) {
 
 int ftr_splat(ftr_ctx* c, const float* points, const float* normals, const float* weights, int64_t n) {
     if (!c) return FTR_EINVAL;
+    if (c->depth_async) return set_err(c, FTR_ESTATE, "ftr_splat: the frame's points come from ftr_splat_depth_async");
     if (n < 0) return set_err(c, FTR_EINVAL, "ftr_splat: n < 0");
     if (n == 0) return FTR_OK;
     if (!points || !normals) return set_err(c, FTR_EINVAL, "ftr_splat: points and normals are required");
@@ -488,43 +490,46 @@ int ftr_splat(ftr_ctx* c, const float* points, const float* normals, const float
     return FTR_OK;
 }
 
-int ftr_splat_depth(ftr_ctx* c, const ftr_view* views, int k, double step, double noise, int radius,
-                    float* const* conf_out) {
-    if (!c) return FTR_EINVAL;
-    if (k < 1 || k > kMaxViews || !views) return set_err(c, FTR_EINVAL, "ftr_splat_depth: 1 <= k <= 8 views");
+namespace {
+
+// Validate the views and enqueue the raw reconstruction into the context's
+// scratch; *pixels = the number of pixels (a bound on the points).
+int raw_enqueue(ftr_ctx* c, const char* who, const ftr_view* views, int k, double step, double noise, int radius,
+                float* const* conf_out, int64_t* pixels_out) {
+    if (k < 1 || k > kMaxViews || !views) return set_err(c, FTR_EINVAL, "%s: 1 <= k <= 8 views", who);
     if (step < 0.0) step = 0.03;
     if (noise < 0.0) noise = 0.0012;
     if (radius < 0) radius = 10;
     if (radius > raw_max_radius() || !(step >= 0.0) || !(noise >= 0.0))
-        return set_err(c, FTR_EINVAL, "ftr_splat_depth: radius <= 16, finite step and noise");
+        return set_err(c, FTR_EINVAL, "%s: radius <= 16, finite step and noise", who);
     int64_t pixels = 0;
     for (int i = 0; i < k; ++i) {
         const ftr_view& v = views[i];
         if (v.w < 2 || v.h < 2 || v.w > 16384 || v.h > 16384 || !v.depth || !is_device_ptr(v.depth))
-            return set_err(c, FTR_EINVAL, "ftr_splat_depth: view %d needs a device depth map of at least 2 x 2", i);
-        if (!(v.K[0] != 0.f) || !(v.K[4] != 0.f)) return set_err(c, FTR_EINVAL, "ftr_splat_depth: view %d focal", i);
+            return set_err(c, FTR_EINVAL, "%s: view %d needs a device depth map of at least 2 x 2", who, i);
+        if (!(v.K[0] != 0.f) || !(v.K[4] != 0.f)) return set_err(c, FTR_EINVAL, "%s: view %d focal", who, i);
         if (conf_out && conf_out[i] && !is_device_ptr(conf_out[i]))
-            return set_err(c, FTR_EINVAL, "ftr_splat_depth: confidence maps must be device memory");
+            return set_err(c, FTR_EINVAL, "%s: confidence maps must be device memory", who);
         pixels += (int64_t)v.w * v.h;
     }
     cudaError_t e;
     const int tiles = raw_tiles(views, k);
     if (pixels > c->raw_cap) {
+        c->graph_valid = false;
         cudaStreamSynchronize(c->stream);
         dfree(c->d_raw);
-        if ((e = dalloc(&c->d_raw, (size_t)pixels * 7)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth");
+        if ((e = dalloc(&c->d_raw, (size_t)pixels * 7)) != cudaSuccess) return cuda_fail(c, e, who);
         c->raw_cap = pixels;
     }
     if (tiles > c->raw_tiles_cap) {
         cudaStreamSynchronize(c->stream);
         dfree(c->d_raw_tiles);
-        if ((e = dalloc(&c->d_raw_tiles, (size_t)tiles)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth");
+        if ((e = dalloc(&c->d_raw_tiles, (size_t)tiles)) != cudaSuccess) return cuda_fail(c, e, who);
         c->raw_tiles_cap = tiles;
     }
     if (!c->d_raw_total) {
-        if ((e = dalloc(&c->d_raw_total, 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth");
-        if ((e = cudaMallocHost((void**)&c->h_raw_total, sizeof(int))) != cudaSuccess)
-            return cuda_fail(c, e, "ftr_splat_depth");
+        if ((e = dalloc(&c->d_raw_total, 1)) != cudaSuccess) return cuda_fail(c, e, who);
+        if ((e = cudaMallocHost((void**)&c->h_raw_total, sizeof(int))) != cudaSuccess) return cuda_fail(c, e, who);
     }
     RawParams rp;
     rp.step = step;
@@ -533,16 +538,50 @@ int ftr_splat_depth(ftr_ctx* c, const ftr_view* views, int k, double step, doubl
     rp.noise_f = (float)noise;
     rp.radius = radius;
     float* P = c->d_raw;
-    float* N = P + 3 * pixels;
-    float* W = P + 6 * pixels;
-    if ((e = launch_raw(c, rp, views, k, conf_out, P, N, W, c->d_raw_tiles, c->d_raw_total)) != cudaSuccess)
-        return cuda_fail(c, e, "ftr_splat_depth: raw reconstruction");
+    if ((e = launch_raw(c, rp, views, k, conf_out, P, P + 3 * pixels, P + 6 * pixels, c->d_raw_tiles,
+                        c->d_raw_total)) != cudaSuccess)
+        return cuda_fail(c, e, who);
+    *pixels_out = pixels;
+    return FTR_OK;
+}
+
+}  // namespace
+
+int ftr_splat_depth(ftr_ctx* c, const ftr_view* views, int k, double step, double noise, int radius,
+                    float* const* conf_out) {
+    if (!c) return FTR_EINVAL;
+    if (c->depth_async) return set_err(c, FTR_ESTATE, "ftr_splat_depth: the frame's points came from the async call");
+    int64_t pixels = 0;
+    if (int st = raw_enqueue(c, "ftr_splat_depth", views, k, step, noise, radius, conf_out, &pixels)) return st;
     // the point count decides the ingest launch: one wait per call
+    cudaError_t e;
     if ((e = cudaMemcpyAsync(c->h_raw_total, c->d_raw_total, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) !=
             cudaSuccess ||
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ftr_splat_depth");
-    return ftr_splat(c, P, N, W, (int64_t)*c->h_raw_total);
+    float* P = c->d_raw;
+    return ftr_splat(c, P, P + 3 * pixels, P + 6 * pixels, (int64_t)*c->h_raw_total);
+}
+
+int ftr_splat_depth_async(ftr_ctx* c, const ftr_view* views, int k, double step, double noise, int radius,
+                          float* const* conf_out) {
+    if (!c) return FTR_EINVAL;
+    if (c->n_pts != 0 || c->depth_async)
+        return set_err(c, FTR_ESTATE, "ftr_splat_depth_async: must be the frame's only point source (after ftr_reset)");
+    int64_t pixels = 0;
+    if (int st = raw_enqueue(c, "ftr_splat_depth_async", views, k, step, noise, radius, conf_out, &pixels)) return st;
+    cudaError_t e;
+    // capacity for the bound; the ingest reads the count on the device
+    if ((e = grow_points(c, pixels)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth_async: point store");
+    float* P = c->d_raw;
+    prof_begin(c, ST_INGEST);
+    e = launch_ingest(c, P, P + 3 * pixels, P + 6 * pixels, pixels, c->d_raw_total);
+    prof_end(c, ST_INGEST);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_splat_depth_async: ingest");
+    c->n_pts = pixels;        // a bound: every consumer reads the exact count on the device
+    c->points_in = -1;
+    c->depth_async = true;
+    return FTR_OK;
 }
 
 int ftr_solve(ftr_ctx* c, double* iso_level_out) {
@@ -1004,7 +1043,16 @@ int ftr_frame_finish(ftr_ctx* c, ftr_mesh* out) {
 
 int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
     if (!c) return FTR_EINVAL;
-    if (points_in) *points_in = c->points_in;
+    if (points_in) {
+        *points_in = c->points_in;
+        if (c->points_in < 0) {     // counted on the device (ftr_splat_depth_async)
+            int64_t n = 0;
+            cudaError_t e = cudaMemcpyAsync(&n, c->d_npts, sizeof(n), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return FTR_ECUDA;
+            *points_in = n;
+        }
+    }
     if (points_dropped) {
         unsigned long long d = 0;
         cudaError_t e = cudaMemcpyAsync(&d, c->d_dropped, sizeof(d), cudaMemcpyDeviceToHost, c->stream);
@@ -1274,7 +1322,11 @@ int ftr_frame_info(ftr_ctx* c, int64_t* info, int n) {
         zl = (meta[2] * kBrick) & ~15;
         zh = ((meta[3] + 1) * kBrick + 15) & ~15;
     }
-    const int64_t v[8] = {c->points_in, (int64_t)dropped, meta[0], meta[1], zl, zh, c->n_verts, c->n_tris};
+    int64_t pin = c->points_in;
+    if (pin < 0) {
+        cudaMemcpy(&pin, c->d_npts, sizeof(pin), cudaMemcpyDeviceToHost);
+    }
+    const int64_t v[8] = {pin, (int64_t)dropped, meta[0], meta[1], zl, zh, c->n_verts, c->n_tris};
     for (int i = 0; i < n && i < 8; ++i) info[i] = v[i];
     return FTR_OK;
 }

@@ -94,7 +94,8 @@ struct ftr_ctx {
     ftr::PointStore pts;
     int64_t n_pts = 0;
     int64_t* d_npts = nullptr;         // the same count on the device (written by the ingest)
-    int64_t points_in = 0;
+    int64_t points_in = 0;             // -1: the count is on the device only (ftr_splat_depth_async)
+    bool depth_async = false;          // the frame's points come from ftr_splat_depth_async
     unsigned long long* d_dropped = nullptr;
     int* d_wild = nullptr;     // set when some accepted weight lies outside [0, 1]
     void* d_stage = nullptr;   // staging for host inputs
@@ -240,7 +241,8 @@ cudaError_t fft_ix_init();
 cudaError_t mc_init();
 
 // launchers (return cudaError_t of the launch)
-cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n);
+cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n,
+                          const int* n_dev = nullptr);   // n_dev: device count, n its bound
 cudaError_t launch_splat(ftr_ctx* c);          // bin + accumulate into d_vpool
 cudaError_t launch_fx(ftr_ctx* c);
 cudaError_t launch_fy(ftr_ctx* c);

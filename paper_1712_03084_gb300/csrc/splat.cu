@@ -77,11 +77,13 @@ __device__ __forceinline__ bool node_t_pair(float x, float bmin, float ih, float
     return true;
 }
 
+// n_dev (nullable): the point count on the device; n then only bounds it.
 __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
                          float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
-                         int64_t* npts_dev) {
+                         int64_t* npts_dev, const int* __restrict__ n_dev) {
     pdl_wait();
+    if (n_dev) n = min(n, (int64_t)*n_dev);
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *npts_dev = base + n;   // points stored so far: later kernels read the count here
     if (i >= n) return;
@@ -583,11 +585,12 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n) {
+cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n,
+                          const int* n_dev) {
     if (n == 0) return cudaSuccess;
     // small CTAs spread the few float64 operations per point over every SM
     launch_pdl(k_ingest, blocks_for(n, 32), 32, 0, c->stream, pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
-                                                       c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts);
+                                                       c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts, n_dev);
     c->launches++;
     return cudaGetLastError();
 }

@@ -67,6 +67,8 @@ _SIGNATURES = [
                                  ctypes.c_int64]),
     ("ftr_splat_depth", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    ("ftr_splat_depth_async", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     ("ftr_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("ftr_extract_mesh", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_mesh)]),
     ("ftr_mesh_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -220,13 +222,15 @@ def make_view(view):
     return v
 
 
-def ftr_splat_depth(ctx, views, step=-1.0, noise=-1.0, radius=-1, conf_out=None):
-    """Raw reconstruction of the views' device depth maps, appended to the frame."""
+def ftr_splat_depth(ctx, views, step=-1.0, noise=-1.0, radius=-1, conf_out=None, wait=True):
+    """Raw reconstruction of the views' device depth maps, appended to the
+    frame (wait=False: ftr_splat_depth_async, the frame's only point source)."""
     arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
     confs = None
     if conf_out is not None:
         confs = (ctypes.c_void_p * len(views))(*[_ptr(c, np.float32) for c in conf_out])
-    _check(load().ftr_splat_depth(ctx, arr, len(views), float(step), float(noise), int(radius), confs), ctx)
+    fn = load().ftr_splat_depth if wait else load().ftr_splat_depth_async
+    _check(fn(ctx, arr, len(views), float(step), float(noise), int(radius), confs), ctx)
 
 
 def ftr_texture(ctx, views, depth_tol, weights=None, uv=None, rgb=None, textured=None):

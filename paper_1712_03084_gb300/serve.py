@@ -4,9 +4,10 @@ Every frame slot owns one reconstruction context (its grids, FFT workspaces,
 brick tables and mesh stay resident in HBM), one CUDA stream, device staging
 buffers for the frame's points and RGB-D views, and device texture outputs.
 A submitted frame is copied in from pinned host memory and queued on the
-slot's stream as per-camera point ingests followed by one CUDA-graph replay
-of the whole reconstruction (``ftr_frame_launch``); frames on different slots
-run concurrently on the device.  Nothing here does reconstruction arithmetic:
+slot's stream as per-camera point ingests (or, for RGB-D frames, the raw
+reconstruction of the depth maps on the device) followed by one CUDA-graph
+replay of the whole reconstruction (``ftr_frame_launch``); frames on
+different slots run concurrently on the device.  Nothing here does reconstruction arithmetic:
 it only moves buffers and orders calls into the C ABI.
 
 * ``run_batch``: B frames of mixed grid sizes, one slot each, all submitted at
@@ -38,16 +39,19 @@ def _torch():
 
 @dataclass
 class FrameInput:
-    """One frame in pinned host memory."""
+    """One frame in pinned host memory: oriented points with their views, or
+    (rgbd) only the RGB-D images, whose points, normals and confidence maps
+    the device computes (Sec. III-A, ftr_splat_depth_async)."""
     points: object
     normals: object
     weights: object
     per_camera: list
     views: list          # dicts: depth, conf, rgb (pinned tensors), K, world_to_cam, K_rgb, world_to_rgb
     n_points: int = 0
+    rgbd: bool = False
 
     @classmethod
-    def from_frame(cls, fr):
+    def from_frame(cls, fr, rgbd=False):
         torch = _torch()
 
         def pin(a):
@@ -55,15 +59,18 @@ class FrameInput:
         views = []
         for v in fr["views"]:
             d = {k: v[k] for k in ("K", "world_to_cam", "K_rgb", "world_to_rgb")}
-            d["depth"], d["conf"], d["rgb"] = pin(v["depth"]), pin(v["conf"]), pin(v["rgb"])
+            d["depth"], d["rgb"] = pin(v["depth"]), pin(v["rgb"])
+            d["conf"] = None if rgbd else pin(v["conf"])
             views.append(d)
+        if rgbd:
+            return cls(None, None, None, [], views, 0, True)
         return cls(pin(fr["points"]), pin(fr["normals"]), pin(fr["weights"]), list(fr["per_camera"]), views,
                    int(len(fr["points"])))
 
     def h2d_bytes(self):
-        b = 4 * (self.points.numel() + self.normals.numel() + self.weights.numel())
+        b = 0 if self.rgbd else 4 * (self.points.numel() + self.normals.numel() + self.weights.numel())
         for v in self.views:
-            b += 4 * v["depth"].numel() + 4 * v["conf"].numel() + v["rgb"].numel()
+            b += 4 * v["depth"].numel() + v["rgb"].numel() + (0 if self.rgbd else 4 * v["conf"].numel())
         return b
 
 
@@ -80,15 +87,16 @@ class Slot:
         self.ctx = ftr.Context(grid_n, bbox, stream=self.stream.cuda_stream)
         self.ctx.autotune()           # tile plans: timed once per grid size, then cached
         self.point_cap = int(point_cap)
+        self.rgbd = template.rgbd
         z = dict(dtype=torch.float32, device=self.dev)
-        self.P = torch.empty((self.point_cap, 3), **z)
-        self.N = torch.empty((self.point_cap, 3), **z)
-        self.W = torch.empty((self.point_cap,), **z)
+        self.P = torch.empty((max(1, self.point_cap), 3), **z)
+        self.N = torch.empty((max(1, self.point_cap), 3), **z)
+        self.W = torch.empty((max(1, self.point_cap),), **z)
         self.views = []
         for v in template.views:
             d = {k: v[k] for k in ("K", "world_to_cam", "K_rgb", "world_to_rgb")}
             d["depth"] = torch.empty_like(v["depth"], device=self.dev)
-            d["conf"] = torch.empty_like(v["conf"], device=self.dev)
+            d["conf"] = torch.empty(tuple(v["depth"].shape), **z)   # rgbd: written by the raw stage
             d["rgb"] = torch.empty_like(v["rgb"], device=self.dev)
             self.views.append(d)
         K = len(self.views)
@@ -117,17 +125,28 @@ class Slot:
         """Queue one frame (copies in, ingests, graph replay); returns immediately."""
         if fin.n_points > self.point_cap:
             raise ValueError("frame has more points than the slot holds")
+        if fin.rgbd != self.rgbd or len(fin.views) != len(self.views) or any(
+                tuple(v["depth"].shape) != tuple(d["depth"].shape) or tuple(v["rgb"].shape) != tuple(d["rgb"].shape)
+                for d, v in zip(self.views, fin.views)):
+            raise ValueError("frame does not match the slot's cameras")
         torch = self.torch
         n = fin.n_points
         with torch.cuda.stream(self.stream):
-            self.P[:n].copy_(fin.points, non_blocking=True)
-            self.N[:n].copy_(fin.normals, non_blocking=True)
-            self.W[:n].copy_(fin.weights, non_blocking=True)
+            if not fin.rgbd:
+                self.P[:n].copy_(fin.points, non_blocking=True)
+                self.N[:n].copy_(fin.normals, non_blocking=True)
+                self.W[:n].copy_(fin.weights, non_blocking=True)
             for d, v in zip(self.views, fin.views):
+                for k in ("K", "world_to_cam", "K_rgb", "world_to_rgb"):
+                    d[k] = v[k]          # the frame's calibration (a change re-captures the graph)
                 d["depth"].copy_(v["depth"], non_blocking=True)
-                d["conf"].copy_(v["conf"], non_blocking=True)
+                if not fin.rgbd:
+                    d["conf"].copy_(v["conf"], non_blocking=True)
                 d["rgb"].copy_(v["rgb"], non_blocking=True)
             self.ctx.reset()
+            if fin.rgbd:
+                # points, normals and the confidence maps from the depth maps, on the device
+                ftr.ftr_splat_depth(self.ctx.h, self.views, conf_out=[d["conf"] for d in self.views], wait=False)
             for (s, c) in fin.per_camera:
                 ftr.ftr_splat(self.ctx.h, self.P[s:s + c], self.N[s:s + c], self.W[s:s + c])
             ftr.ftr_frame_launch(self.ctx.h, self.views, self.tol, self.out_w, self.out_uv, self.out_rgb,

@@ -104,3 +104,37 @@ def test_edge_cases(ftr):
         ftr.ftr_splat_depth(ctx.h, [{"depth": torch.from_numpy(quad).to(dev), "K": K, "world_to_cam": RT}],
                             radius=17)
     ctx.close()
+
+
+def test_async_depth_path_equals_the_waiting_one(ftr):
+    """ftr_splat_depth_async (device-side point count, no host wait) gives the
+    same field and level as ftr_splat_depth, inside a whole-frame graph too,
+    and enforces being the frame's only point source."""
+    import torch
+    c = G.CASES["human96"]
+    dviews = _device_views(torch, G.case_inputs("human96")[3])
+    ctx = ftr.Context(c["grid"], c["bbox"])
+    ctx.reset()
+    ftr.ftr_splat_depth(ctx.h, dviews)
+    n_sync, _ = ctx.stats()
+    L0 = ctx.solve()
+    A0 = ctx.field_A()
+    ctx.reset()
+    ftr.ftr_splat_depth(ctx.h, dviews, wait=False)
+    n_async, _ = ctx.stats()
+    L1 = ctx.solve()
+    A1 = ctx.field_A()
+    assert n_async == n_sync and L1 == L0 and np.array_equal(A1, A0)
+    with pytest.raises(ftr.FtrError):
+        ftr.ftr_splat(ctx.h, np.zeros((1, 3), np.float32), np.zeros((1, 3), np.float32))
+    for _ in range(2):               # graph capture, then replay
+        ctx.reset()
+        ftr.ftr_splat_depth(ctx.h, dviews, wait=False)
+        ftr.ftr_frame_launch(ctx.h, [], 0.02)
+        m = ftr.ftr_frame_finish(ctx.h)
+    assert np.array_equal(ctx.field_A(), A0)
+    ctx.reset()
+    ftr.ftr_splat(ctx.h, np.zeros((1, 3), np.float32), np.zeros((1, 3), np.float32))
+    with pytest.raises(ftr.FtrError):
+        ftr.ftr_splat_depth(ctx.h, dviews, wait=False)
+    ctx.close()

@@ -81,3 +81,36 @@ def test_admission_respects_the_hbm_budget(rt):
     assert srv.admit(a) and not srv.admit(b)
     assert srv.rejected == [1] and srv.used <= srv.budget
     srv.close()
+
+
+def test_rgbd_sessions_match_the_device_raw_path_alone(rt):
+    """Sessions fed as RGB-D images (points, normals and W maps computed on
+    the device without a host wait) give, in the mix, the meshes of a lone
+    context running the waiting raw-reconstruction call on the same images."""
+    import torch
+    from paper_1712_03084_gb300 import ftr
+    specs = [((64, 64, 64), 3, 110), ((96, 96, 96), 4, 120)]
+    sessions = []
+    for sid, (grid, K, seed) in enumerate(specs):
+        frs = _frames(seed, 2, K)
+        fins = [rt.FrameInput.from_frame(f, rgbd=True) for f in frs]
+        sessions.append(rt.Session(sid, grid, BOX, fins, rate_hz=60.0))
+    srv = rt.Server(hbm_budget_bytes=64 << 30)
+    for s in sessions:
+        assert srv.admit(s)
+    keep = {(0, 0), (1, 1)}
+    stats = srv.run(duration_s=0.4, seed=5, keep_meshes=keep)
+    srv.close()
+    assert stats["frames"] > 10
+    for (sid, k), (v, t) in stats["meshes"].items():
+        sess = sessions[sid]
+        fin = sess.frames[k % len(sess.frames)]
+        views = [{"depth": x["depth"].cuda(), "K": x["K"], "world_to_cam": x["world_to_cam"]} for x in fin.views]
+        ctx = ftr.Context(sess.grid_n, BOX)
+        ctx.reset()
+        ftr.ftr_splat_depth(ctx.h, views)
+        ctx.solve()
+        m = ctx.mesh_numpy()
+        ctx.close()
+        assert np.array_equal(v, m["vertices"]) and np.array_equal(t, m["tris"])
+    assert len(stats["meshes"]) == 2
