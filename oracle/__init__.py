@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle for the volumetric Fourier-transform reconstruction.
 
 TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct
-restatement of Section III-A/III-B/III-C of Alexiadis et al. (IEEE TCSVT 2017,
+restatement of Section III-A/III-B/III-C/III-E of Alexiadis et al. (IEEE TCSVT 2017,
 arXiv 1712.03084) against which the CUDA path is checked.  Only the test
 suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg
 of ``bench.py`` may import it.  The product path (the C-ABI library and its
@@ -21,6 +21,8 @@ Modules
   mc_table   marching-cubes case table generated from a face rule   (Sec. III-B, [35])
   mc         marching cubes (classes, vertices, normals, triangles) (Sec. III-B)
   texture    per-vertex visibility, weights, UVs, blended colour    (Sec. III-C)
+  render     depth / colour-per-vertex / multitexture rendering     (Sec. III-C, III-E)
+  evaluate   VRE, 2D Hausdorff, CP-RMSE, WMS3IM                     (Sec. III-E, eq. (3)-(7))
   pipeline   the whole per-frame path in the paper's order
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``
