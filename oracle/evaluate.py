@@ -128,6 +128,15 @@ def gaussian_taps():
     return np.exp(-t * t / (2.0 * SSIM_SIGMA * SSIM_SIGMA))
 
 
+def _overlap(n, d):
+    """(destination, source) slices of the pixels i with 0 <= i + d < n
+    (empty when |d| >= n)."""
+    lo, hi = max(0, -d), min(n, n - d)
+    if hi <= lo:
+        return slice(0, 0), slice(0, 0)
+    return slice(lo, hi), slice(lo + d, hi + d)
+
+
 def window_mean(img, taps):
     """Weighted mean over the (2R+1)^2 window around every pixel, the window
     cut at the border and its weights renormalised to 1."""
@@ -138,10 +147,8 @@ def window_mean(img, taps):
     for dy in range(-R, R + 1):
         for dx in range(-R, R + 1):
             wt = taps[dy + R] * taps[dx + R]
-            ys = slice(max(0, -dy), min(h, h - dy))
-            xs = slice(max(0, -dx), min(w, w - dx))
-            yd = slice(max(0, dy), min(h, h + dy))
-            xd = slice(max(0, dx), min(w, w + dx))
+            ys, yd = _overlap(h, dy)
+            xs, xd = _overlap(w, dx)
             num[ys, xs] += wt * img[yd, xd]
             den[ys, xs] += wt
     return num / den
@@ -154,10 +161,8 @@ def window_count(mask, R=SSIM_RADIUS):
     out = np.zeros((h, w), np.int64)
     for dy in range(-R, R + 1):
         for dx in range(-R, R + 1):
-            ys = slice(max(0, -dy), min(h, h - dy))
-            xs = slice(max(0, -dx), min(w, w - dx))
-            yd = slice(max(0, dy), min(h, h + dy))
-            xd = slice(max(0, dx), min(w, w + dx))
+            ys, yd = _overlap(h, dy)
+            xs, xd = _overlap(w, dx)
             out[ys, xs] += m[yd, xd]
     return out
 

@@ -99,6 +99,14 @@ def test_window_mean_is_the_normalised_library_correlation():
     m = rng.random((37, 53)) > 0.5
     cnt = ndimage.correlate(m.astype(np.int64), np.ones((11, 11), np.int64), mode="constant")
     assert np.array_equal(ev.window_count(m), cnt)
+    # images smaller than the window
+    for shape in ((3, 3), (1, 7), (6, 2)):
+        img = rng.uniform(0, 255, shape)
+        want = ndimage.correlate(img, k2, mode="constant") / ndimage.correlate(np.ones_like(img), k2, mode="constant")
+        assert np.max(np.abs(ev.window_mean(img, g) - want)) < 1e-10
+        m = rng.random(shape) > 0.3
+        cnt = ndimage.correlate(m.astype(np.int64), np.ones((11, 11), np.int64), mode="constant")
+        assert np.array_equal(ev.window_count(m), cnt)
 
 
 def _grey(v):
