@@ -196,6 +196,14 @@ typedef struct {
  */
 int ftr_texture(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out);
 
+/*
+ * The same per-vertex texture data for caller-given vertices instead of the
+ * extracted mesh: vertices n_vertices x 3 float32, the views' images and
+ * every output DEVICE memory (k = 1..8).  Only enqueues.
+ */
+int ftr_texture_vertices(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, const float* vertices,
+                         int64_t n_vertices, ftr_tex* out);
+
 /* ---- frames without a host wait in the middle --------------------------------
  *
  * ftr_extract_mesh and ftr_texture return counts or host data, so the host
@@ -318,6 +326,105 @@ int ftr_profile_read(ftr_ctx* ctx, double* ms, int64_t* counts, int max_stages);
 const char* ftr_stage_name(int stage);
 /* Number of kernels this context has launched so far. */
 int64_t ftr_launch_count(const ftr_ctx* ctx);
+
+/* ---- rendering and objective evaluation (Sec. III-C, III-E) ------------------
+ *
+ * Sec. III-E judges a reconstruction by projecting the mesh into the K + K'
+ * sensor views (K used by the reconstruction, K' held out) and comparing the
+ * rendered depth and colour with what each sensor captured.  Every pointer
+ * in this section is DEVICE memory; the render only enqueues, the two
+ * evaluations wait for the stream and return host values.
+ */
+
+typedef struct {
+    int w, h;                 /* image size, pixels                                       */
+    float K[9];               /* intrinsics, row-major 3x3                                */
+    float world_to_cam[12];   /* [R | t], row-major 3x4: x_cam = R X + t                 */
+} ftr_camera;
+
+typedef struct {
+    const float* vertices;    /* n_vertices x 3 world coordinates                         */
+    const int32_t* tris;      /* n_tris x 3 vertex indices (each < n_vertices)            */
+    int64_t n_vertices, n_tris;
+    /* colour source: at most one of vertex_rgb / tex_weights (both NULL = depth only)    */
+    const uint8_t* vertex_rgb;  /* n_vertices x 3: colour-per-vertex rendering             */
+    const float* tex_weights;   /* n_vertices x tex_k: W_k per vertex (ftr_tex.weights)    */
+    const float* tex_uv;        /* n_vertices x tex_k x 2: RGB pixel coords (ftr_tex.uv)   */
+    const ftr_view* tex_views;  /* tex_k views: only rgb_w, rgb_h and rgb are read         */
+    int tex_k;                  /* 1..8 with tex_weights                                    */
+} ftr_render_src;
+
+/*
+ * Render a triangle mesh into a pinhole camera (the depth and colour buffers
+ * of Sec. III-E; the multitexture blend of Sec. III-C).  Pixel (i, j) samples
+ * the image point (i, j).  A triangle is drawn unless a vertex has camera
+ * z < 0.01 or its screen area is 0; a pixel is covered iff its three edge
+ * functions have one sign (edges belong to both neighbours; no culling).
+ * The depth is the camera z where the pixel's ray meets the triangle's
+ * plane; the nearest surface wins (smallest (float32 z, triangle index)).
+ * Projection, coverage and depth are evaluated in float64 in a fixed
+ * operation order, so the drawn set and the depth are deterministic.
+ * depth_out: h x w float32, 0 where nothing is drawn.  rgb_out: h x w x 3
+ * u8 or NULL; with vertex_rgb the perspective-correct barycentric mean of
+ * the vertex colours; with tex_weights the blend sum_k w_k RGB_k(uv_k) /
+ * sum_k w_k over the views weighted at all three vertices, w_k and uv_k
+ * interpolated across the triangle, RGB_k sampled bilinearly (clamped);
+ * floor(c + 1/2), black where nothing is drawn or no view applies.
+ * Returns FTR_EINVAL for bad sizes, host pointers, n_tris >= 2^31 or a
+ * colour source without rgb_out.  Triangle indices are checked on the device:
+ * a triangle with an index outside [0, n_vertices) is not drawn.
+ */
+int ftr_render(ftr_ctx* ctx, const ftr_render_src* src, const ftr_camera* cam, float* depth_out,
+               uint8_t* rgb_out);
+
+typedef struct {
+    int64_t rendered_px;      /* |S_r|: pixels with rendered depth > 0                    */
+    int64_t sensor_px;        /* |S_g|: pixels with sensor depth > 0                      */
+    int64_t xor_px, or_px;    /* |S_r xor S_g|, |S_r or S_g|                              */
+    double vre;               /* eq. (3): xor / or (0 when both are empty)                */
+    double hausdorff_px;      /* eq. (4): symmetric 2D Hausdorff distance, pixels;
+                                 0 when both are empty, +inf when one is                  */
+    int64_t sensor_points;    /* I_k                                                       */
+    int64_t rendered_points;  /* J_k                                                       */
+    double cp_rmse;           /* eq. (5), depth units; nan if I_k = 0, +inf if J_k = 0    */
+} ftr_geometry_eval;
+
+/*
+ * Volume and geometry metrics of Sec. III-E (eq. (3)-(5)) for one view:
+ * rendered_depth (ftr_render of the mesh into cam) against sensor_depth,
+ * both h x w float32 (0 = background).  The points of eq. (5) are the
+ * back-projections X = z (dx, dy, 1), dy = (j - K12)/K11,
+ * dx = ((i - K02) - K01 dy)/K00, of the foreground pixels (camera
+ * coordinates).  cp_d2_out (nullable): h x w float32 receiving, per sensor
+ * pixel, the squared distance to the closest rendered point (+inf without
+ * rendered points), 0 elsewhere.  Counts and the Hausdorff distance are
+ * exact; the closest-point distances are float32, their mean is summed in
+ * float64 in a fixed order (deterministic).  Waits for the stream.
+ */
+int ftr_eval_geometry(ftr_ctx* ctx, const ftr_camera* cam, const float* rendered_depth, const float* sensor_depth,
+                      float* cp_d2_out, ftr_geometry_eval* out);
+
+typedef struct {
+    double l[3], c[3], s[3];  /* weighted means of the SSIM terms per scale, eq. (7)      */
+    double wms3im;            /* prod_j l_j^a_j c_j^b_j s_j^g_j                           */
+} ftr_appearance_eval;
+
+/*
+ * Appearance metric of Sec. III-E3 (eq. (6)(7)): WMS3IM between a rendered
+ * colour image and the sensor's, over the rendered silhouette S_r
+ * (rendered_depth > 0), at J = 3 scales with exponents a = (0, 0, 0.1333),
+ * b = g = (0.0448, 0.3001, 0.1333).  Luma Y = 0.299 R + 0.587 G + 0.114 B;
+ * N(u) = the 11 x 11 window with Gaussian weights (sigma 1.5 pixels per
+ * axis) cut at the image border and renormalised; C1 = (0.01 * 255)^2,
+ * C2 = (0.03 * 255)^2, C3 = C2 / 2; s = (sigma_XY + C3) / (sigma_X sigma_Y
+ * + C3); w(u) = silhouette pixels in the cut 11 x 11 window.  Scale j + 1
+ * is the 2 x 2 block mean (silhouette: block AND), floor(n / 2) pixels.
+ * A weighted mean <= 0 contributes 0 to the product; without silhouette
+ * pixels at some scale every field is nan.  Images h x w x 3 u8,
+ * rendered_depth h x w float32, w, h >= 1.  Waits for the stream.
+ */
+int ftr_eval_appearance(ftr_ctx* ctx, int w, int h, const float* rendered_depth, const uint8_t* rendered_rgb,
+                        const uint8_t* sensor_rgb, ftr_appearance_eval* out);
 
 /* ---- allocation-free variant ------------------------------------------------ */
 

@@ -220,6 +220,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_A);
     for (int a = 0; a < 3; ++a) dfree(c->d_tw[a]);
     dfree(c->d_tc_table);
+    eval_free(c);
     dfree(c->d_raw);
     dfree(c->d_raw_tiles);
     dfree(c->d_raw_total);
@@ -929,6 +930,26 @@ int ftr_frame_launch(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, 
     c->tex_uv = out->uv;
     c->tex_rgb = out->rgb;
     c->tex_flag = out->textured;
+    return FTR_OK;
+}
+
+int ftr_texture_vertices(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, const float* vertices,
+                         int64_t n_vertices, ftr_tex* out) {
+    if (!c || !out) return FTR_EINVAL;
+    if (k < 1 || k > kMaxViews || !views) return set_err(c, FTR_EINVAL, "ftr_texture_vertices: 1 <= k <= 8");
+    if (!(depth_tol >= 0.f) || n_vertices < 0) return set_err(c, FTR_EINVAL, "ftr_texture_vertices: bad argument");
+    if (n_vertices > 0 && !is_device_ptr(vertices))
+        return set_err(c, FTR_EINVAL, "ftr_texture_vertices: vertices must be device memory");
+    const void* outs[4] = {out->weights, out->uv, out->rgb, out->textured};
+    for (int i = 0; i < 4; ++i)
+        if (outs[i] && !is_device_ptr(outs[i]))
+            return set_err(c, FTR_EINVAL, "ftr_texture_vertices: outputs must be device memory");
+    ViewSet vs;
+    int st = device_viewset(c, views, k, vs, "ftr_texture_vertices");
+    if (st != FTR_OK) return st;
+    cudaError_t e = launch_texture_vertices(c, vs, depth_tol, vertices, n_vertices, out->weights, out->uv, out->rgb,
+                                            out->textured);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_texture_vertices");
     return FTR_OK;
 }
 

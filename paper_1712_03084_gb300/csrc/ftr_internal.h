@@ -78,6 +78,7 @@ struct ViewSet {
     int k;
     ViewDev v[kMaxViews];
 };
+struct EvalScratch;
 }  // namespace ftr
 
 struct ftr_ctx {
@@ -197,6 +198,9 @@ struct ftr_ctx {
     double prof_ms[ftr::ST_COUNT] = {};
     int64_t prof_n[ftr::ST_COUNT] = {};
     int64_t launches = 0;
+
+    // rendering / evaluation scratch (render.cu, evaluate.cu)
+    ftr::EvalScratch* ev = nullptr;
 };
 
 namespace ftr {
@@ -279,9 +283,33 @@ cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);
 
 cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv,
                            uint8_t* rgb, uint8_t* textured);
+// Same, for nv caller-given vertices (device, nv x 3).
+cudaError_t launch_texture_vertices(ftr_ctx* c, const ViewSet& vs, float depth_tol, const float* verts, int64_t nv,
+                                    float* w, float* uv, uint8_t* rgb, uint8_t* textured);
 // Same, for min(limit, *nv_dev) vertices with the count read on the device.
 cudaError_t launch_texture_bounded(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t limit,
                                    const int* nv_dev, float* w, float* uv, uint8_t* rgb, uint8_t* textured);
+
+// rendering and objective evaluation (render.cu, evaluate.cu): scratch owned
+// by the context, grown on demand, released by eval_free
+struct EvalScratch {
+    unsigned long long* zkey = nullptr;   // per pixel: (float32 z bits << 32) | triangle, ~0 = empty
+    int64_t zkey_cap = 0;
+    int* col = nullptr;                   // 2 x pixels: column distances to the sensor / rendered silhouette
+    float4* pts = nullptr;                // 2 x pixels: compacted sensor and rendered points (.w = pixel)
+    float* d2 = nullptr;                  // pixels: squared closest-point distance per sensor pixel
+    int64_t pix_cap = 0;
+    unsigned long long* cnt = nullptr;    // 8 counters (see evaluate.cu)
+    double* part = nullptr;               // per-block partial sums
+    int64_t part_cap = 0;
+    double* h_res = nullptr;              // pinned results
+    float* img = nullptr;                 // appearance planes: luma X, Y per scale
+    unsigned char* mask = nullptr;        // silhouette per scale
+    int64_t img_cap = 0;
+};
+EvalScratch* eval_scratch(ftr_ctx* c);          // created on first use; nullptr if that fails
+void eval_free(ftr_ctx* c);
+bool camera_ok(const ftr_camera* cam);         // 1 <= w, h <= 16384 and non-zero focal lengths
 
 // marching-cubes table (mc_table.cpp), generated from the face rule
 void mc_generate_table(int32_t ntri[256], int32_t tris[256 * kMaxTrisPerCase * 3]);

@@ -170,18 +170,18 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
 
 namespace {
 
-cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t nv, const int* nv_dev, float* w,
-                        float* uv, uint8_t* rgb, uint8_t* textured) {
+cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, const float* verts, int64_t nv,
+                        const int* nv_dev, float* w, float* uv, uint8_t* rgb, uint8_t* textured) {
     if (nv <= 0) return cudaSuccess;
     prof_begin(c, ST_TEXTURE);
     const int G = vs.k <= 1 ? 1 : (vs.k <= 2 ? 2 : (vs.k <= 4 ? 4 : 8));
     const unsigned blocks = (unsigned)((nv * G + 255) / 256);
     const double tau = (double)depth_tol;
     switch (G) {
-        case 1: launch_pdl(k_texture<1>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
-        case 2: launch_pdl(k_texture<2>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
-        case 4: launch_pdl(k_texture<4>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
-        default: launch_pdl(k_texture<8>, blocks, 256, 0, c->stream, vs, c->d_verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 1: launch_pdl(k_texture<1>, blocks, 256, 0, c->stream, vs, verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 2: launch_pdl(k_texture<2>, blocks, 256, 0, c->stream, vs, verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        case 4: launch_pdl(k_texture<4>, blocks, 256, 0, c->stream, vs, verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
+        default: launch_pdl(k_texture<8>, blocks, 256, 0, c->stream, vs, verts, nv, nv_dev, tau, w, uv, rgb, textured); break;
     }
     c->launches++;
     prof_end(c, ST_TEXTURE);
@@ -192,12 +192,17 @@ cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t 
 
 cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv, uint8_t* rgb,
                            uint8_t* textured) {
-    return run_texture(c, vs, depth_tol, c->n_verts, nullptr, w, uv, rgb, textured);
+    return run_texture(c, vs, depth_tol, c->d_verts, c->n_verts, nullptr, w, uv, rgb, textured);
+}
+
+cudaError_t launch_texture_vertices(ftr_ctx* c, const ViewSet& vs, float depth_tol, const float* verts, int64_t nv,
+                                    float* w, float* uv, uint8_t* rgb, uint8_t* textured) {
+    return run_texture(c, vs, depth_tol, verts, nv, nullptr, w, uv, rgb, textured);
 }
 
 cudaError_t launch_texture_bounded(ftr_ctx* c, const ViewSet& vs, float depth_tol, int64_t limit, const int* nv_dev,
                                    float* w, float* uv, uint8_t* rgb, uint8_t* textured) {
-    return run_texture(c, vs, depth_tol, limit, nv_dev, w, uv, rgb, textured);
+    return run_texture(c, vs, depth_tol, c->d_verts, limit, nv_dev, w, uv, rgb, textured);
 }
 
 }  // namespace ftr

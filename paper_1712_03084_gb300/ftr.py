@@ -56,6 +56,29 @@ class ftr_tex(ctypes.Structure):
                 ("textured", ctypes.c_void_p)]
 
 
+class ftr_camera(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int), ("h", ctypes.c_int), ("K", ctypes.c_float * 9),
+                ("world_to_cam", ctypes.c_float * 12)]
+
+
+class ftr_render_src(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("n_vertices", ctypes.c_int64),
+                ("n_tris", ctypes.c_int64), ("vertex_rgb", ctypes.c_void_p), ("tex_weights", ctypes.c_void_p),
+                ("tex_uv", ctypes.c_void_p), ("tex_views", ctypes.POINTER(ftr_view)), ("tex_k", ctypes.c_int)]
+
+
+class ftr_geometry_eval(ctypes.Structure):
+    _fields_ = [("rendered_px", ctypes.c_int64), ("sensor_px", ctypes.c_int64), ("xor_px", ctypes.c_int64),
+                ("or_px", ctypes.c_int64), ("vre", ctypes.c_double), ("hausdorff_px", ctypes.c_double),
+                ("sensor_points", ctypes.c_int64), ("rendered_points", ctypes.c_int64),
+                ("cp_rmse", ctypes.c_double)]
+
+
+class ftr_appearance_eval(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_double * 3), ("c", ctypes.c_double * 3), ("s", ctypes.c_double * 3),
+                ("wms3im", ctypes.c_double)]
+
+
 # (name, restype, argtypes) of every exported symbol
 _SIGNATURES = [
     ("ftr_default_params", None, [ctypes.POINTER(ftr_params)]),
@@ -74,6 +97,8 @@ _SIGNATURES = [
     ("ftr_mesh_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_texture", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
                                    ctypes.POINTER(ftr_tex)]),
+    ("ftr_texture_vertices", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int,
+                                            ctypes.c_float, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ftr_tex)]),
     ("ftr_extract_mesh_async", ctypes.c_int, [ctypes.c_void_p]),
     ("ftr_texture_async", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
                                          ctypes.POINTER(ftr_tex), ctypes.c_int64]),
@@ -100,6 +125,12 @@ _SIGNATURES = [
     ("ftr_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("ftr_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("ftr_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("ftr_render", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_render_src), ctypes.POINTER(ftr_camera),
+                                  ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_eval_geometry", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_camera), ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ftr_geometry_eval)]),
+    ("ftr_eval_appearance", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ftr_appearance_eval)]),
     ("ftr_iso_level_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_float), ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_void_p, ctypes.c_void_p]),
@@ -233,10 +264,64 @@ def ftr_splat_depth(ctx, views, step=-1.0, noise=-1.0, radius=-1, conf_out=None,
     _check(fn(ctx, arr, len(views), float(step), float(noise), int(radius), confs), ctx)
 
 
+def make_camera(K, world_to_cam, w, h):
+    cam = ftr_camera()
+    cam.w, cam.h = int(w), int(h)
+    cam.K[:] = [float(x) for x in np.asarray(K, dtype=np.float32).reshape(-1)]
+    cam.world_to_cam[:] = [float(x) for x in np.asarray(world_to_cam, dtype=np.float32).reshape(-1)]
+    return cam
+
+
+def ftr_render(ctx, vertices, tris, camera, depth_out, rgb_out=None, vertex_rgb=None, tex_weights=None,
+               tex_uv=None, tex_views=None, n_vertices=None, n_tris=None):
+    """Render a device mesh into ``camera`` (an ftr_camera); all buffers are
+    CUDA tensors or device addresses."""
+    src = ftr_render_src()
+    src.vertices = _ptr(vertices, np.float32)
+    src.tris = _ptr(tris, np.int32)
+    src.n_vertices = int(n_vertices if n_vertices is not None else vertices.shape[0])
+    src.n_tris = int(n_tris if n_tris is not None else tris.shape[0])
+    src.vertex_rgb = _ptr(vertex_rgb, np.uint8)
+    keep = None
+    if tex_weights is not None:
+        keep = (ftr_view * len(tex_views))(*[make_view(v) for v in tex_views])
+        src.tex_weights = _ptr(tex_weights, np.float32)
+        src.tex_uv = _ptr(tex_uv, np.float32)
+        src.tex_views = keep
+        src.tex_k = len(tex_views)
+    _check(load().ftr_render(ctx, ctypes.byref(src), ctypes.byref(camera), _ptr(depth_out, np.float32),
+                             _ptr(rgb_out, np.uint8)), ctx)
+    del keep
+
+
+def ftr_eval_geometry(ctx, camera, rendered_depth, sensor_depth, cp_d2_out=None):
+    out = ftr_geometry_eval()
+    _check(load().ftr_eval_geometry(ctx, ctypes.byref(camera), _ptr(rendered_depth, np.float32),
+                                    _ptr(sensor_depth, np.float32), _ptr(cp_d2_out, np.float32),
+                                    ctypes.byref(out)), ctx)
+    return {f: getattr(out, f) for f, _ in ftr_geometry_eval._fields_}
+
+
+def ftr_eval_appearance(ctx, rendered_depth, rendered_rgb, sensor_rgb):
+    out = ftr_appearance_eval()
+    h, w = int(rendered_depth.shape[0]), int(rendered_depth.shape[1])
+    _check(load().ftr_eval_appearance(ctx, w, h, _ptr(rendered_depth, np.float32), _ptr(rendered_rgb, np.uint8),
+                                      _ptr(sensor_rgb, np.uint8), ctypes.byref(out)), ctx)
+    return {"wms3im": out.wms3im, "l": list(out.l), "c": list(out.c), "s": list(out.s)}
+
+
 def ftr_texture(ctx, views, depth_tol, weights=None, uv=None, rgb=None, textured=None):
     arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
     t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
     _check(load().ftr_texture(ctx, arr, len(views), float(depth_tol), ctypes.byref(t)), ctx)
+
+
+def ftr_texture_vertices(ctx, views, depth_tol, vertices, weights=None, uv=None, rgb=None, textured=None):
+    """Per-vertex texture data of caller-given device vertices (all device buffers)."""
+    arr = (ftr_view * max(1, len(views)))(*[make_view(v) for v in views])
+    t = ftr_tex(_ptr(weights, np.float32), _ptr(uv, np.float32), _ptr(rgb, np.uint8), _ptr(textured, np.uint8))
+    _check(load().ftr_texture_vertices(ctx, arr, len(views), float(depth_tol), _ptr(vertices, np.float32),
+                                       int(vertices.shape[0]), ctypes.byref(t)), ctx)
 
 
 def ftr_extract_mesh_async(ctx):

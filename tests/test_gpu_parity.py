@@ -165,16 +165,27 @@ def test_edge_cases(ftr):
 
 
 def test_texture_matches_oracle_on_the_same_mesh(ftr):
-    """Sec. III-C per-vertex weights, UVs and blended colour on the GPU mesh."""
+    """Sec. III-C per-vertex weights, UVs and blended colour of the oracle's
+    mesh, textured on the GPU (ftr_texture_vertices) and by the oracle."""
+    import torch
     from oracle import texture as otex
     name = "human96"
     c = G.CASES[name]
     P, N, W, views = G.case_inputs(name)
-    ctx, _ = _run(ftr, name)
-    m = ctx.mesh_numpy()
+    verts = G.oracle_result(name)["mesh"]["vertices"].astype(np.float32)
+    nv, k = len(verts), len(views)
+    dev = torch.device("cuda", 0)
+    dviews = [{key: (torch.from_numpy(np.ascontiguousarray(v[key])).to(dev) if key in ("depth", "conf", "rgb")
+                     else v[key]) for key in v} for v in views]
+    w = torch.zeros((nv, k), dtype=torch.float32, device=dev)
+    uv = torch.zeros((nv, k, 2), dtype=torch.float32, device=dev)
+    rgb = torch.zeros((nv, 3), dtype=torch.uint8, device=dev)
+    tx = torch.zeros((nv,), dtype=torch.uint8, device=dev)
+    ctx = ftr.Context(c["grid"], c["bbox"])
     tol = float(np.float32(0.03))
-    tex = ctx.texture_numpy(views, tol, len(m["vertices"]))
-    ref = otex.texture(m["vertices"].astype(np.float64), views, tol)
+    ftr.ftr_texture_vertices(ctx.h, dviews, tol, torch.from_numpy(verts).to(dev), w, uv, rgb, tx)
+    tex = {"weights": w.cpu().numpy(), "uv": uv.cpu().numpy(), "rgb": rgb.cpu().numpy(), "textured": tx.cpu().numpy()}
+    ref = otex.texture(verts.astype(np.float64), views, tol)
     assert np.array_equal(tex["weights"] > 0, ref["weights"] > 0)
     assert np.array_equal(tex["weights"], ref["weights"].astype(np.float32))
     vis = ref["weights"] > 0
@@ -183,6 +194,16 @@ def test_texture_matches_oracle_on_the_same_mesh(ftr):
     assert np.all(tex["uv"][~vis] == -1)
     assert np.array_equal(tex["textured"], ref["textured"])
     assert np.max(np.abs(tex["rgb"].astype(int) - ref["rgb"].astype(int))) <= 1
+    # ftr_texture on the context's own mesh = ftr_texture_vertices on those vertices
+    r = G.oracle_result(name)
+    ctx.set_indicator(r["A"].astype(np.float32), r["L"])
+    m = ctx.mesh_numpy()
+    own = ctx.texture_numpy(views, tol, len(m["vertices"]))
+    n2 = len(m["vertices"])
+    w2 = torch.zeros((n2, k), dtype=torch.float32, device=dev)
+    rgb2 = torch.zeros((n2, 3), dtype=torch.uint8, device=dev)
+    ftr.ftr_texture_vertices(ctx.h, dviews, tol, torch.from_numpy(m["vertices"]).to(dev), w2, None, rgb2, None)
+    assert np.array_equal(own["weights"], w2.cpu().numpy()) and np.array_equal(own["rgb"], rgb2.cpu().numpy())
     ctx.close()
 
 
