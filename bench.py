@@ -440,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
         multi = run_multi(args, rank, dev, plain_frame=fr)
     from_depth = run_from_depth(args, rank, dev, fr, flush) if not args.no_multi else None
     table1 = run_table1(args, rank, dev, fr, flush) if not args.no_multi else None
+    evaluation = run_evaluation(args, rank, dev) if not args.no_multi else None
     prec = None
     if not args.no_precision:
         if ctx is not None:
@@ -481,6 +482,8 @@ def run_ours(args, rank, world, local_rank):
         line.update(from_depth)
     if table1:
         line.update(table1)
+    if evaluation:
+        line.update(evaluation)
     if prec:
         line.update(prec)
     return line
@@ -783,12 +786,12 @@ TABLE1_PAPER_MS = {5: (10.0, 17.0), 6: (22.0, 27.0), 7: (102.0, 163.0)}   # (sim
 
 def run_table1(args, rank, dev, fr, flush):
     """The paper's Table I axis on GB300: simple vs weighted splat at its grid
-    shapes 2^r x 2^(r+1) x 2^r (r = 5, 6, 7) over a 1 x 2 x 1 m box around the
+    shapes 2^r x 2^(r+1) x 2^r (r = 5, 6, 7) over a 1.6 x 2 x 1.6 m box around the
     body, the same 4-camera frame; reconstruction only (splat, transforms,
     level, marching cubes: one graph frame without texture), device-timed."""
     import torch
     from paper_1712_03084_gb300 import ftr
-    box = (-0.5, -0.05, -0.5, 0.5, 1.95, 0.5)
+    box = TALL_BOX
     P = torch.from_numpy(fr["points"]).to(dev)
     N = torch.from_numpy(fr["normals"]).to(dev)
     W = torch.from_numpy(fr["weights"]).to(dev)
@@ -828,10 +831,104 @@ def run_table1(args, rank, dev, fr, flush):
             row[name] = {"ms": round(ms, 4), "vertices": int(info["n_vertices"]), "dropped": int(info["dropped"]),
                          "paper_ms_gtx560": paper, "paper_over_ours": round(paper / ms, 1)}
         out[f"r{r}"] = row
-    out["config"] = ("Table I axis: grids 2^r x 2^(r+1) x 2^r over a 1 x 2 x 1 m box, the human256 frame's 40,722 "
-                     "points (points outside the box dropped), splat to mesh without texture, CUDA events per "
+    out["config"] = ("Table I axis: grids 2^r x 2^(r+1) x 2^r over a 1.6 x 2 x 1.6 m box holding the whole body, "
+                     "the human256 frame's points, splat to mesh without texture, CUDA events per "
                      "frame, L2 flushed between frames; paper times (GTX 560, Argyris sequence) are context only")
     return {"table1": out}
+
+
+# the paper's grid shape 2^r x 2^(r+1) x 2^r over a box holding the whole synthetic body (arms reach +-0.75 m)
+TALL_BOX = (-0.8, -0.05, -0.8, 0.8, 1.95, 0.8)
+EVAL_RECON_CAMS = (0, 1, 3, 5)      # Fig. 2: c0, c1, c3, c5 reconstruct; c2 and c4 are ground-truth views only
+
+
+def run_evaluation(args, rank, dev):
+    """Sec. III-E on GB300: a 6-camera frame reconstructed from cameras 0, 1,
+    3, 5 (the paper's Fig. 2 setup); the mesh is rendered into all six depth
+    and RGB views and scored with VRE, the 2D Hausdorff distance, CP-RMSE
+    and WMS3IM (colour per vertex and multitexture), at the grids
+    2^r x 2^(r+1) x 2^r (r = 5, 6, 7) and 256^3.  The evaluation of the six
+    views (18 renders, 6 geometry and 12 appearance evaluations) is timed on
+    the host around synchronised calls."""
+    import torch
+    from datagen import human_frame
+    from paper_1712_03084_gb300 import ftr
+    fr = human_frame(seed=args.seed + 77 + rank, K=6, device=dev)
+    views = fr["views"]
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    P, N, W = d(fr["points"]), d(fr["normals"]), d(fr["weights"])
+    dviews = [{"depth": d(v["depth"]), "conf": d(v["conf"]), "rgb": d(v["rgb"]), "K": v["K"],
+               "world_to_cam": v["world_to_cam"], "K_rgb": v["K_rgb"], "world_to_rgb": v["world_to_rgb"]}
+              for v in views]
+    tviews = [dviews[k] for k in EVAL_RECON_CAMS]
+    cams = [ftr.make_camera(v["K"], v["world_to_cam"], v["depth"].shape[1], v["depth"].shape[0]) for v in views]
+    rcams = [ftr.make_camera(v["K_rgb"], v["world_to_rgb"], v["rgb"].shape[1], v["rgb"].shape[0]) for v in views]
+    tall = TALL_BOX
+    cube = (-1.0, -0.05, -1.0, 1.0, 1.95, 1.0)
+    setups = [("r5", (32, 64, 32), tall), ("r6", (64, 128, 64), tall), ("r7", (128, 256, 128), tall),
+              ("human256", (256, 256, 256), cube)]
+    out = {}
+    for name, grid, box in setups:
+        ctx = ftr.Context(grid, box)
+        ctx.reset()
+        for k in EVAL_RECON_CAMS:
+            s, n = fr["per_camera"][k]
+            ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+        ctx.solve()
+        m = ctx.extract_mesh()
+        nv, nt = int(m.n_vertices), int(m.n_tris)
+        h = max((box[3 + a] - box[a]) / grid[a] for a in range(3))
+        tol = float(np.float32(max(3.0 * h, 0.02)))
+        tw = torch.zeros((max(nv, 1), len(tviews)), dtype=torch.float32, device=dev)
+        tuv = torch.zeros((max(nv, 1), len(tviews), 2), dtype=torch.float32, device=dev)
+        trgb = torch.zeros((max(nv, 1), 3), dtype=torch.uint8, device=dev)
+        ftr.ftr_texture(ctx.h, tviews, tol, tw, tuv, trgb, None)
+        bufs = [(torch.zeros(v["depth"].shape, dtype=torch.float32, device=dev),
+                 torch.zeros(v["rgb"].shape[:2], dtype=torch.float32, device=dev),
+                 torch.zeros(v["rgb"].shape, dtype=torch.uint8, device=dev),
+                 torch.zeros(v["rgb"].shape, dtype=torch.uint8, device=dev)) for v in views]
+
+        def evaluate():
+            res = []
+            for i, v in enumerate(dviews):
+                dep, rdep, cpv, mtx = bufs[i]
+                ftr.ftr_render(ctx.h, m.vertices, m.tris, cams[i], dep, n_vertices=nv, n_tris=nt)
+                g = ftr.ftr_eval_geometry(ctx.h, cams[i], dep, v["depth"])
+                ftr.ftr_render(ctx.h, m.vertices, m.tris, rcams[i], rdep, cpv, vertex_rgb=trgb,
+                               n_vertices=nv, n_tris=nt)
+                a1 = ftr.ftr_eval_appearance(ctx.h, rdep, cpv, v["rgb"])
+                ftr.ftr_render(ctx.h, m.vertices, m.tris, rcams[i], rdep, mtx, tex_weights=tw, tex_uv=tuv,
+                               tex_views=tviews, n_vertices=nv, n_tris=nt)
+                a2 = ftr.ftr_eval_appearance(ctx.h, rdep, mtx, v["rgb"])
+                res.append((g, a1, a2))
+            return res
+        evaluate()
+        torch.cuda.synchronize()
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            res = evaluate()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+        ctx.close()
+        held = [i for i in range(len(views)) if i not in EVAL_RECON_CAMS]
+        out[name] = {
+            "grid": list(grid), "vertices": nv,
+            "hausdorff_px_mean": round(float(np.mean([r[0]["hausdorff_px"] for r in res])), 3),
+            "hausdorff_px_heldout": [round(float(res[i][0]["hausdorff_px"]), 3) for i in held],
+            "vre_mean": round(float(np.mean([r[0]["vre"] for r in res])), 4),
+            "cp_rmse_mm_mean": round(1e3 * float(np.mean([r[0]["cp_rmse"] for r in res])), 3),
+            "wms3im_vertex_colour_mean": round(float(np.mean([r[1]["wms3im"] for r in res])), 4),
+            "wms3im_multitexture_mean": round(float(np.mean([r[2]["wms3im"] for r in res])), 4),
+            "wms3im_multitexture_heldout": [round(float(res[i][2]["wms3im"]), 4) for i in held],
+            "eval_ms_6_views": round(ms, 3)}
+    out["config"] = ("6-camera synthetic human frame (512x424 depth, 1920x1080 RGB, ring 2.5 m), reconstruction "
+                     "from cameras 0,1,3,5 (texture from the same), evaluation in all 6 views (2 and 4 held out): "
+                     "VRE, 2D Hausdorff, CP-RMSE on the depth views, WMS3IM on the RGB views; means over the 6 "
+                     "views; eval_ms = 6 depth + 12 RGB renders and 18 metric evaluations, host-timed, synchronised")
+    return {"evaluation": out}
 
 
 def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
