@@ -275,6 +275,23 @@ def oracle_baseline(cfg, fr, steps=1):
 
 # ----------------------------------------------------------------------------- our arm
 
+def replica_max(seconds_or_ms, world, device):
+    """The timed region of the slowest replica: max over ranks (one
+    independent replica per rank, no data exchange besides this)."""
+    if world <= 1:
+        return float(seconds_or_ms)
+    import torch
+    t = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(steps, seconds, world):
+    """Whole-job frames/s: every rank processed ``steps`` frames within the
+    slowest rank's ``seconds``."""
+    return world * steps / seconds
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1712_03084_gb300 import build as pbuild
@@ -401,12 +418,8 @@ def run_ours(args, rank, world, local_rank):
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    total_ms = replica_max(float(sum(step_ms)), world, dev)
+    value = replica_rate(args.steps, total_ms / 1000.0, world)
 
     # dominant kernel and its roofline
     per_launch = {k: (ms / n if n else 0.0, n) for k, (ms, n) in prof.items()}
@@ -928,7 +941,50 @@ def run_evaluation(args, rank, dev):
                      "from cameras 0,1,3,5 (texture from the same), evaluation in all 6 views (2 and 4 held out): "
                      "VRE, 2D Hausdorff, CP-RMSE on the depth views, WMS3IM on the RGB views; means over the 6 "
                      "views; eval_ms = 6 depth + 12 RGB renders and 18 metric evaluations, host-timed, synchronised")
+    out["ablation"] = run_ablation(args, rank, dev)
     return {"evaluation": out}
+
+
+def run_ablation(args, rank, dev):
+    """Fig. 11 as numbers: the weighted splat of eq. (1)(2) with its
+    confidences against the simple splat (nearest node, no weights), on
+    input with 1x and 3x the sensor's depth noise, scored against the
+    noise-free depth maps of all six cameras (same body, same cameras)."""
+    import torch
+    from datagen import human_frame
+    from paper_1712_03084_gb300 import ftr
+    seed = args.seed + 91 + rank
+    clean = human_frame(seed=seed, K=6, noise_coef=0.0, with_rgb=False, device=dev)
+    gts = [torch.from_numpy(np.ascontiguousarray(v["depth"].astype(np.float32))).to(dev) for v in clean["views"]]
+    cams = [ftr.make_camera(v["K"], v["world_to_cam"], v["depth"].shape[1], v["depth"].shape[0])
+            for v in clean["views"]]
+    res = {}
+    for tag, noise in (("noise_1x", 0.0012), ("noise_3x", 0.0036)):
+        fr = human_frame(seed=seed, K=6, noise_coef=noise, with_rgb=False, device=dev)
+        P, N, W = (torch.from_numpy(np.ascontiguousarray(fr[k])).to(dev) for k in ("points", "normals", "weights"))
+        row = {}
+        for mode, name in ((ftr.FTR_SPLAT_SIMPLE, "simple"), (ftr.FTR_SPLAT_WEIGHTED, "weighted")):
+            ctx = ftr.Context((128, 256, 128), TALL_BOX, splat_mode=mode)
+            ctx.reset()
+            for k in EVAL_RECON_CAMS:
+                s0, n0 = fr["per_camera"][k]
+                ctx.splat(P[s0:s0 + n0], N[s0:s0 + n0], W[s0:s0 + n0])
+            ctx.solve()
+            m = ctx.extract_mesh()
+            gs = []
+            for i, cam in enumerate(cams):
+                dep = torch.zeros(gts[i].shape, dtype=torch.float32, device=dev)
+                ftr.ftr_render(ctx.h, m.vertices, m.tris, cam, dep, n_vertices=int(m.n_vertices),
+                               n_tris=int(m.n_tris))
+                gs.append(ftr.ftr_eval_geometry(ctx.h, cam, dep, gts[i]))
+            ctx.close()
+            row[name] = {"cp_rmse_mm": round(1e3 * float(np.mean([g["cp_rmse"] for g in gs])), 3),
+                         "hausdorff_px": round(float(np.mean([g["hausdorff_px"] for g in gs])), 3),
+                         "vre": round(float(np.mean([g["vre"] for g in gs])), 4)}
+        res[tag] = row
+    res["config"] = ("grid 128x256x128 over the 1.6 x 2 x 1.6 m box, cameras 0,1,3,5 reconstruct, the mesh scored "
+                     "in all 6 depth views against noise-free depth of the same frame; means over the views")
+    return res
 
 
 def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
@@ -985,12 +1041,8 @@ def run_e2e(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
         gc.enable()
-    total = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-    return {"value": round(world * args.steps / total, 2), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+    total = replica_max(float(sum(times)), world, dev)
+    return {"value": round(replica_rate(args.steps, total, world), 2), "unit": UNIT, "h2d_bytes_per_step": int(bi),
             "d2h_bytes_per_step": int(bo[0]), "ms_per_step": round(1000 * total / args.steps, 4),
             "timing": "host wall clock per step (synchronised), pinned host buffers"}
 
