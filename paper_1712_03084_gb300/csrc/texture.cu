@@ -10,9 +10,12 @@
 // for the paper's OpenGL multitexture blend is the weighted mean of bilinear
 // RGB samples, stored as floor(c + 1/2).  Every discrete decision (pixel
 // choice, z > 0, the depth test, the RGB bounds) must match a float64
-// evaluation of the same formulas: each camera is evaluated in float32 first
-// and redone in float64 when any decision quantity falls within a guard band
-// (2e-3 px, 1e-4 m) of its threshold, far wider than the float32 error.
+// evaluation of the same formulas: each camera is evaluated in float32, and a
+// decision whose quantity falls within a guard band (2e-3 px, 1e-4 m) of its
+// threshold -- far wider than the float32 error -- is re-decided from that
+// quantity recomputed in float64 (float64 is slow on this GPU, so nothing
+// else is redone); a vertex within 1e-4 m of a camera plane is evaluated
+// entirely in float64.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -35,12 +38,6 @@ __device__ __forceinline__ void project(const T* K, const T* RT, const T X[3], T
 }
 
 template <class T> struct Cams;
-template <> struct Cams<float> {
-    __device__ static const float* K(const ViewDev& v) { return v.Kf; }
-    __device__ static const float* RT(const ViewDev& v) { return v.RTf; }
-    __device__ static const float* Krgb(const ViewDev& v) { return v.Krgbf; }
-    __device__ static const float* RTrgb(const ViewDev& v) { return v.RTrgbf; }
-};
 template <> struct Cams<double> {
     __device__ static const double* K(const ViewDev& v) { return v.K; }
     __device__ static const double* RT(const ViewDev& v) { return v.RT; }
@@ -55,26 +52,21 @@ __device__ __forceinline__ bool near_half_int(T u, T band) {
     return d < band || d > (T)1 - band;
 }
 
-// One camera for one vertex in precision T.  With GUARD set, returns false
-// (and nothing else) when a decision lies inside the guard band.
-template <class T, bool GUARD>
-__device__ __forceinline__ bool eval_camera(const ViewDev& vw, const T X[3], T tau, T& wk, T& ur, T& vr, T rgb[3]) {
-    const T band_px = (T)2e-3, band_m = (T)1e-4;
+// One camera for one vertex, entirely in precision T.
+template <class T>
+__device__ __forceinline__ void eval_camera(const ViewDev& vw, const T X[3], T tau, T& wk, T& ur, T& vr, T rgb[3]) {
     T u, v, z;
     project<T>(Cams<T>::K(vw), Cams<T>::RT(vw), X, u, v, z);
     wk = 0;
     ur = -1;
     vr = -1;
-    if (GUARD && fabs(z) < band_m) return false;
     if (z > (T)0) {
-        if (GUARD && (near_half_int(u, band_px) || near_half_int(v, band_px))) return false;
         const T px = floor(u + (T)0.5), py = floor(v + (T)0.5);
         if (px >= (T)0 && px < (T)vw.w && py >= (T)0 && py < (T)vw.h) {
             const int64_t pi = (int64_t)py * vw.w + (int64_t)px;
             const T D = (T)vw.depth[pi];
             if (D > (T)0) {
                 const T dz = fabs(D - z);
-                if (GUARD && fabs(dz - tau) < band_m) return false;
                 if (dz <= tau) wk = (T)vw.conf[pi];
             }
         }
@@ -83,9 +75,6 @@ __device__ __forceinline__ bool eval_camera(const ViewDev& vw, const T X[3], T t
         T zr;
         project<T>(Cams<T>::Krgb(vw), Cams<T>::RTrgb(vw), X, ur, vr, zr);
         const T xmax = (T)(vw.rgb_w - 1), ymax = (T)(vw.rgb_h - 1);
-        if (GUARD && (fabs(zr) < band_m || fabs(ur) < band_px || fabs(ur - xmax) < band_px ||
-                      fabs(vr) < band_px || fabs(vr - ymax) < band_px))
-            return false;
         if (!(zr > (T)0 && ur >= (T)0 && ur <= xmax && vr >= (T)0 && vr <= ymax)) wk = 0;
     }
     if (wk > (T)0) {
@@ -105,6 +94,86 @@ __device__ __forceinline__ bool eval_camera(const ViewDev& vw, const T X[3], T t
     } else {
         ur = -1;
         vr = -1;
+    }
+}
+
+// One camera for one vertex: everything in float32, except that a decision
+// whose float32 quantity lies inside the guard band is re-decided from that
+// quantity alone in float64 (the depth camera's u, v for the pixel choice,
+// its z for the depth test, the RGB projection for the RGB bounds).  The
+// values that are not decisions (W, the UV, the colour) stay float32.
+// Returns false only for a vertex within band_m of a camera plane; the
+// caller then evaluates the whole camera in float64.
+__device__ __forceinline__ bool eval_camera_mixed(const ViewDev& vw, const float X[3], float tau, double taud,
+                                                  float& wk, float& ur, float& vr, float rgb[3]) {
+    const float band_px = 2e-3f, band_m = 1e-4f;
+    const double Xd[3] = {X[0], X[1], X[2]};
+    float u, v, z;
+    project<float>(vw.Kf, vw.RTf, X, u, v, z);
+    wk = 0.f;
+    ur = -1.f;
+    vr = -1.f;
+    if (fabsf(z) < band_m) return false;
+    if (z > 0.f) {
+        int64_t px, py;
+        if (near_half_int(u, band_px) || near_half_int(v, band_px)) {
+            double ud, vd, zd;
+            project<double>(vw.K, vw.RT, Xd, ud, vd, zd);
+            px = (int64_t)floor(ud + 0.5);
+            py = (int64_t)floor(vd + 0.5);
+        } else {
+            px = (int64_t)floorf(u + 0.5f);
+            py = (int64_t)floorf(v + 0.5f);
+        }
+        if (px >= 0 && px < vw.w && py >= 0 && py < vw.h) {
+            const int64_t pi = py * vw.w + px;
+            const float D = vw.depth[pi];
+            if (D > 0.f) {
+                const float dz = fabsf(D - z);
+                bool vis;
+                if (fabsf(dz - tau) < band_m) {
+                    const double* RT = vw.RT;
+                    const double zd = RT[8] * Xd[0] + RT[9] * Xd[1] + RT[10] * Xd[2] + RT[11];
+                    vis = fabs((double)D - zd) <= taud;
+                } else {
+                    vis = dz <= tau;
+                }
+                if (vis) wk = vw.conf[pi];
+            }
+        }
+    }
+    if (wk > 0.f) {
+        float zr;
+        project<float>(vw.Krgbf, vw.RTrgbf, X, ur, vr, zr);
+        const float xmax = (float)(vw.rgb_w - 1), ymax = (float)(vw.rgb_h - 1);
+        bool in;
+        if (fabsf(zr) < band_m || fabsf(ur) < band_px || fabsf(ur - xmax) < band_px || fabsf(vr) < band_px ||
+            fabsf(vr - ymax) < band_px) {
+            double ud, vd, zd;
+            project<double>(vw.Krgb, vw.RTrgb, Xd, ud, vd, zd);
+            in = zd > 0.0 && ud >= 0.0 && ud <= (double)xmax && vd >= 0.0 && vd <= (double)ymax;
+        } else {
+            in = zr > 0.f && ur >= 0.f && ur <= xmax && vr >= 0.f && vr <= ymax;
+        }
+        if (!in) wk = 0.f;
+    }
+    if (wk > 0.f) {
+        const float fx0 = floorf(ur), fy0 = floorf(vr);
+        const float fx = ur - fx0, fy = vr - fy0;
+        const int x0 = (int)fx0, y0 = (int)fy0;
+        const int xa = min(max(x0, 0), vw.rgb_w - 1), xb = min(max(x0 + 1, 0), vw.rgb_w - 1);
+        const int ya = min(max(y0, 0), vw.rgb_h - 1), yb = min(max(y0 + 1, 0), vw.rgb_h - 1);
+        const uint8_t* p00 = vw.rgb + 3 * ((int64_t)ya * vw.rgb_w + xa);
+        const uint8_t* p10 = vw.rgb + 3 * ((int64_t)ya * vw.rgb_w + xb);
+        const uint8_t* p01 = vw.rgb + 3 * ((int64_t)yb * vw.rgb_w + xa);
+        const uint8_t* p11 = vw.rgb + 3 * ((int64_t)yb * vw.rgb_w + xb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            rgb[c] = (1.f - fx) * (1.f - fy) * (float)p00[c] + fx * (1.f - fy) * (float)p10[c] +
+                     (1.f - fx) * fy * (float)p01[c] + fx * fy * (float)p11[c];
+    } else {
+        ur = -1.f;
+        vr = -1.f;
     }
     return true;
 }
@@ -127,10 +196,10 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
     if (live) {
         const ViewDev& vw = vs.v[k];
         const float Xf[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
-        if (!eval_camera<float, true>(vw, Xf, (float)tau, wk, ur, vr, rgb)) {
+        if (!eval_camera_mixed(vw, Xf, (float)tau, tau, wk, ur, vr, rgb)) {
             const double Xd[3] = {Xf[0], Xf[1], Xf[2]};
             double wd, ud, vd, cd[3];
-            eval_camera<double, false>(vw, Xd, tau, wd, ud, vd, cd);
+            eval_camera<double>(vw, Xd, tau, wd, ud, vd, cd);
             wk = (float)wd;
             ur = (float)ud;
             vr = (float)vd;
