@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
     __shared__ bool last;
     const int nx = g.n[0];
     const int64_t nxy = (int64_t)nx * g.n[1];
-    double sum = 0.0, cnt = 0.0;
+    double sum = 0.0;
+    int cnt = 0;
     const int64_t n = *npts;
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
         const int4 b = pbase[i];
@@ -56,10 +57,10 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
         const float c0 = fmaf(fy, c10 - c00, c00);
         const float c1 = fmaf(fy, c11 - c01, c01);
         sum += (double)fmaf(fz, c1 - c0, c0);
-        cnt += 1.0;
+        cnt += 1;
     }
     const double s = block_sum(sum, sh);
-    const double c = block_sum(cnt, sh);
+    const double c = block_sum((double)cnt, sh);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = s;
         part[2 * blockIdx.x + 1] = c;
@@ -67,20 +68,18 @@ __global__ void __launch_bounds__(kThreads) k_level_partial(GridDev g, const int
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last || threadIdx.x >= 32) return;
+    if (!last) return;
     __threadfence();
-    const int lane = threadIdx.x;
+    // the whole CTA reads the partials (one or two per thread, all loads in
+    // flight at once), then the fixed tree
     double ts = 0.0, tc = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
         ts += __ldcg(&part[2 * b]);
         tc += __ldcg(&part[2 * b + 1]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ts += __shfl_down_sync(0xffffffffu, ts, o);
-        tc += __shfl_down_sync(0xffffffffu, tc, o);
-    }
-    if (lane == 0) {
+    ts = block_sum(ts, sh);
+    tc = block_sum(tc, sh);
+    if (threadIdx.x == 0) {
         const double L = tc > 0.0 ? ts / tc : 0.0;
         level[0] = L;
         level[1] = tc;

@@ -234,7 +234,7 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
 }
 
 // Exclusive scan of the three row-count arrays (length nb) in tiles of
-// kScanTile: tile sums, one CTA over the tile sums, then each tile writes
+// kScanTile: tile sums, then each tile adds up the sums before it and writes
 // off[a * (nb + 1) + i]; totals go to off[a * (nb + 1) + nb].
 constexpr int kScanTile = 2048;
 
@@ -255,35 +255,36 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_tile_sums(const int* __restri
     if (threadIdx.x == 0) tile[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_tile_scan(int3* tile, int ntiles, int nb, int* off) {
-    pdl_wait();
-    __shared__ int3 sh[kMcThreads / 32];
-    int3 carry = make_int3(0, 0, 0);
-    for (int base = 0; base < ntiles; base += kMcThreads) {
-        const int i = base + threadIdx.x;
-        const int3 v = i < ntiles ? tile[i] : make_int3(0, 0, 0);
-        int3 tot;
-        const int3 ex = block_scan3(v, tot, sh);
-        if (i < ntiles) tile[i] = make_int3(carry.x + ex.x, carry.y + ex.y, carry.z + ex.z);
-        carry.x += tot.x;
-        carry.y += tot.y;
-        carry.z += tot.z;
-    }
-    if (threadIdx.x == 0) {
-        off[nb] = carry.x;
-        off[(nb + 1) + nb] = carry.y;
-        off[2 * (nb + 1) + nb] = carry.z;
-        off[3 * (nb + 1) + 0] = carry.x;     // totals for the host
-        off[3 * (nb + 1) + 1] = carry.y;
-        off[3 * (nb + 1) + 2] = carry.z;
-    }
-}
-
+// Per tile: the exclusive offset is the sum of the (few) tile sums before
+// it, summed by every CTA itself (no separate scan launch); CTA 0 also writes
+// the totals.  Then the tile's rows get their offsets.
 __global__ void __launch_bounds__(kMcThreads) k_mc_tile_write(const int* __restrict__ blk, int nb,
-                                                              const int3* __restrict__ tile, int* off) {
+                                                              const int3* __restrict__ tile, int ntiles, int* off) {
     pdl_wait();
     __shared__ int3 sh[kMcThreads / 32];
-    int3 run = tile[blockIdx.x];
+    int3 pre = make_int3(0, 0, 0), all = make_int3(0, 0, 0);
+    for (int i = threadIdx.x; i < ntiles; i += kMcThreads) {
+        const int3 v = tile[i];
+        if (i < (int)blockIdx.x) {
+            pre.x += v.x;
+            pre.y += v.y;
+            pre.z += v.z;
+        }
+        all.x += v.x;
+        all.y += v.y;
+        all.z += v.z;
+    }
+    int3 run, total;
+    block_scan3(pre, run, sh);
+    block_scan3(all, total, sh);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        off[nb] = total.x;
+        off[(nb + 1) + nb] = total.y;
+        off[2 * (nb + 1) + nb] = total.z;
+        off[3 * (nb + 1) + 0] = total.x;     // totals for the host
+        off[3 * (nb + 1) + 1] = total.y;
+        off[3 * (nb + 1) + 2] = total.z;
+    }
     for (int k = 0; k < kScanTile / kMcThreads; ++k) {
         const int i = blockIdx.x * kScanTile + k * kMcThreads + threadIdx.x;
         const int3 v = i < nb ? make_int3(blk[i], blk[nb + i], blk[2 * nb + i]) : make_int3(0, 0, 0);
@@ -541,9 +542,8 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
     prof_begin(c, ST_MC_SCAN);
     const int ntiles = (nr + kScanTile - 1) / kScanTile;
     launch_pdl(k_mc_tile_sums, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile);
-    launch_pdl(k_mc_tile_scan, 1, kMcThreads, 0, c->stream, c->d_mc_tile, ntiles, nr, c->d_mc_off);
-    launch_pdl(k_mc_tile_write, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile, c->d_mc_off);
-    c->launches += 3;
+    launch_pdl(k_mc_tile_write, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile, ntiles, c->d_mc_off);
+    c->launches += 2;
     e = cudaGetLastError();
     prof_end(c, ST_MC_SCAN);
     return e;

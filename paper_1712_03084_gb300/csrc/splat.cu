@@ -239,7 +239,8 @@ __device__ __forceinline__ int4 brick_counts(int c) {
     return make_int4(c, c > 0, ch, ch > 1);
 }
 
-__global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restrict__ cnt, int nb, int4* tile_sum) {
+__global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restrict__ cnt, int nb, int4* tile_sum,
+                                                            int* meta) {
     pdl_wait();
     __shared__ int4 sh[kScanT / 32];
     int4 v = make_int4(0, 0, 0, 0);
@@ -255,46 +256,50 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restric
     }
     int4 tot;
     block_scan4(v, tot, sh);
-    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
-}
-
-// One CTA: exclusive scan of the tile sums in place; totals into meta.
-__global__ void __launch_bounds__(kScanT) k_brick_tile_scan(int4* tile_sum, int ntiles, int nb, int* off,
-                                                            int* meta, int* unit_off) {
-    pdl_wait();
-    __shared__ int4 sh[kScanT / 32];
-    int4 carry = make_int4(0, 0, 0, 0);
-    for (int base = 0; base < ntiles; base += kScanT) {
-        const int i = base + threadIdx.x;
-        const int4 v = i < ntiles ? tile_sum[i] : make_int4(0, 0, 0, 0);
-        int4 tot;
-        const int4 ex = block_scan4(v, tot, sh);
-        if (i < ntiles) tile_sum[i] = make_int4(carry.x + ex.x, carry.y + ex.y, carry.z + ex.z, carry.w + ex.w);
-        carry.x += tot.x;
-        carry.y += tot.y;
-        carry.z += tot.z;
-        carry.w += tot.w;
-    }
     if (threadIdx.x == 0) {
-        off[nb] = carry.x;
-        unit_off[carry.y] = carry.z;   // end of the last touched brick's chunks
-        meta[0] = carry.y;
-        meta[1] = carry.x;
-        meta[2] = 0x7fffffff;
-        meta[3] = -1;
-        meta[4] = 0;                   // chunk ticket of the accumulation
-        meta[5] = carry.z;             // chunks in all
-        meta[6] = carry.w;             // heavy bricks
+        tile_sum[blockIdx.x] = tot;
+        if (blockIdx.x == 0) {       // the z range is min/max-reduced by the write kernel
+            meta[2] = 0x7fffffff;
+            meta[3] = -1;
+        }
     }
 }
 
+// Per tile: its exclusive offset is the sum of the (few) tile sums before it,
+// summed by every CTA itself (no separate scan launch); CTA 0 also writes the
+// totals.  Then the tile's bricks get their offsets, slots and chunk ranges.
 __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restrict__ cnt, int nb, int nbxy,
-                                                             const int4* __restrict__ tile_off, int* off,
+                                                             const int4* __restrict__ tile_sum, int ntiles, int* off,
                                                              int* cursor, int* slot, int* active, int* meta,
                                                              int* unit_off, int* heavy_idx) {
     pdl_wait();
     __shared__ int4 sh[kScanT / 32];
-    int4 run = tile_off[blockIdx.x];
+    int4 pre = make_int4(0, 0, 0, 0), all = make_int4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < ntiles; i += kScanT) {
+        const int4 v = tile_sum[i];
+        if (i < (int)blockIdx.x) {
+            pre.x += v.x;
+            pre.y += v.y;
+            pre.z += v.z;
+            pre.w += v.w;
+        }
+        all.x += v.x;
+        all.y += v.y;
+        all.z += v.z;
+        all.w += v.w;
+    }
+    int4 run, total;
+    block_scan4(pre, run, sh);
+    block_scan4(all, total, sh);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        off[nb] = total.x;
+        unit_off[total.y] = total.z;   // end of the last touched brick's chunks
+        meta[0] = total.y;
+        meta[1] = total.x;
+        meta[4] = 0;                   // chunk ticket of the accumulation
+        meta[5] = total.z;             // chunks in all
+        meta[6] = total.w;             // heavy bricks
+    }
     int zmin = 0x7fffffff, zmax = -1;
     for (int k = 0; k < kTile / kScanT; ++k) {
         const int b = blockIdx.x * kTile + k * kScanT + threadIdx.x;
@@ -606,13 +611,11 @@ cudaError_t launch_splat(ftr_ctx* c) {
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ntiles = (c->n_bricks + kTile - 1) / kTile;
-    launch_pdl(k_brick_tile_sums, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->d_tile);
-    launch_pdl(k_brick_tile_scan, 1, kScanT, 0, c->stream, c->d_tile, ntiles, c->n_bricks, c->d_brick_off, c->d_meta,
-               c->d_unit_off);
+    launch_pdl(k_brick_tile_sums, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->d_tile, c->d_meta);
     launch_pdl(k_brick_tile_write, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
-               c->d_tile, c->d_brick_off, c->d_brick_cursor, c->d_brick_slot, c->d_active, c->d_meta, c->d_unit_off,
-               c->d_heavy_idx);
-    c->launches += 3;
+               c->d_tile, ntiles, c->d_brick_off, c->d_brick_cursor, c->d_brick_slot, c->d_active, c->d_meta,
+               c->d_unit_off, c->d_heavy_idx);
+    c->launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     launch_pdl(k_brick_fill, sms * 2, 256, 0, c->stream, c->pts.base, c->d_npts, c->g, c->d_brick_cursor, c->d_entries);
     c->launches++;
