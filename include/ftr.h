@@ -134,6 +134,16 @@ int ftr_extract_mesh(ftr_ctx* ctx, ftr_mesh* out);
 /* Copy the extracted mesh into caller buffers (host or device, any may be NULL). */
 int ftr_mesh_copy(ftr_ctx* ctx, float* vertices, float* normals, int32_t* tris);
 
+/*
+ * The same copies, only enqueued on the context's stream: the data is in the
+ * caller's buffers once the stream has reached them (an event or a stream
+ * synchronisation).  Host destinations must be page-locked for the copies to
+ * overlap other work (pageable memory makes CUDA stage them synchronously).
+ * The buffers must hold n_vertices x 3 and n_tris x 3 elements of the mesh
+ * that ftr_extract_mesh / ftr_frame_finish last reported.
+ */
+int ftr_mesh_copy_async(ftr_ctx* ctx, float* vertices, float* normals, int32_t* tris);
+
 typedef struct {
     int w, h;                 /* depth image size                                         */
     float K[9];               /* depth intrinsics, row-major 3x3                          */

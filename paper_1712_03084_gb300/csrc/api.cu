@@ -714,6 +714,20 @@ int ftr_mesh_copy(ftr_ctx* c, float* vertices, float* normals, int32_t* tris) {
     return FTR_OK;
 }
 
+int ftr_mesh_copy_async(ftr_ctx* c, float* vertices, float* normals, int32_t* tris) {
+    if (!c) return FTR_EINVAL;
+    if (!c->meshed) return set_err(c, FTR_ESTATE, "ftr_mesh_copy_async: no mesh");
+    cudaError_t e = cudaSuccess;
+    if (vertices && c->n_verts)
+        e = cudaMemcpyAsync(vertices, c->d_verts, sizeof(float) * 3 * c->n_verts, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && normals && c->n_verts)
+        e = cudaMemcpyAsync(normals, c->d_vnrm, sizeof(float) * 3 * c->n_verts, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && tris && c->n_tris)
+        e = cudaMemcpyAsync(tris, c->d_tris, sizeof(int32_t) * 3 * c->n_tris, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_mesh_copy_async");
+    return FTR_OK;
+}
+
 int ftr_texture(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, ftr_tex* out) {
     if (!c || !out) return FTR_EINVAL;
     if (k < 0 || k > kMaxViews || (k > 0 && !views)) return set_err(c, FTR_EINVAL, "ftr_texture: 0 <= k <= 8");

@@ -95,6 +95,7 @@ _SIGNATURES = [
     ("ftr_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("ftr_extract_mesh", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_mesh)]),
     ("ftr_mesh_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_mesh_copy_async", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_texture", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_float,
                                    ctypes.POINTER(ftr_tex)]),
     ("ftr_texture_vertices", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int,
@@ -233,6 +234,11 @@ def ftr_extract_mesh(ctx):
 def ftr_mesh_copy(ctx, vertices=None, normals=None, tris=None):
     _check(load().ftr_mesh_copy(ctx, _ptr(vertices, np.float32), _ptr(normals, np.float32),
                                 _ptr(tris, np.int32)), ctx)
+
+
+def ftr_mesh_copy_async(ctx, vertices=None, normals=None, tris=None):
+    _check(load().ftr_mesh_copy_async(ctx, _ptr(vertices, np.float32), _ptr(normals, np.float32),
+                                      _ptr(tris, np.int32)), ctx)
 
 
 def make_view(view):

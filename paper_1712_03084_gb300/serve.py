@@ -107,6 +107,8 @@ class Slot:
         self.out_rgb = torch.empty((self.cap, 3), dtype=torch.uint8, device=self.dev)
         self.out_tex = torch.empty((self.cap,), dtype=torch.uint8, device=self.dev)
         self.done = torch.cuda.Event()
+        self.fetched = torch.cuda.Event()
+        self.nv = self.nt = 0
         self.busy = False
         self.tag = None
         tol_h = max((bbox[3 + a] - bbox[a]) / grid_n[a] for a in range(3))
@@ -162,7 +164,37 @@ class Slot:
         """Complete the frame; returns (n_vertices, n_tris)."""
         m = ftr.ftr_frame_finish(self.ctx.h)
         self.busy = False
-        return m.n_vertices, m.n_tris
+        self.nv, self.nt = int(m.n_vertices), int(m.n_tris)
+        return self.nv, self.nt
+
+    def host_buffers(self):
+        """Page-locked host buffers for ``fetch_async`` at this slot's capacity."""
+        torch = self.torch
+        K = len(self.views)
+
+        def pin(shape, dtype):
+            return torch.empty(shape, dtype=dtype).pin_memory()
+        return {"vertices": pin((self.cap, 3), torch.float32), "normals": pin((self.cap, 3), torch.float32),
+                "tris": pin((2 * self.cap, 3), torch.int32), "weights": pin((self.cap, K), torch.float32),
+                "uv": pin((self.cap, K, 2), torch.float32), "rgb": pin((self.cap, 3), torch.uint8),
+                "textured": pin((self.cap,), torch.uint8)}
+
+    def fetch_async(self, host):
+        """Enqueue, on the slot's stream, the copies of the last finished
+        frame's mesh and texture data into ``host`` (``host_buffers()``); they
+        are done when ``self.fetched`` has completed.  Returns the bytes."""
+        nv, nt = self.nv, self.nt
+        if nv > host["vertices"].shape[0] or nt > host["tris"].shape[0] or nv > self.cap:
+            raise ValueError("host buffers smaller than the frame's mesh")
+        torch = self.torch
+        ftr.ftr_mesh_copy_async(self.ctx.h, host["vertices"], host["normals"], host["tris"])
+        with torch.cuda.stream(self.stream):
+            for key, src in (("weights", self.out_w), ("uv", self.out_uv), ("rgb", self.out_rgb),
+                             ("textured", self.out_tex)):
+                host[key][:nv].copy_(src[:nv], non_blocking=True)
+            self.fetched.record(self.stream)
+        K = len(self.views)
+        return nv * (24 + 12 * K + 4) + nt * 12
 
     def mesh(self):
         m = ftr.ftr_frame_info(self.ctx.h)

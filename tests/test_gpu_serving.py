@@ -114,3 +114,30 @@ def test_rgbd_sessions_match_the_device_raw_path_alone(rt):
         ctx.close()
         assert np.array_equal(v, m["vertices"]) and np.array_equal(t, m["tris"])
     assert len(stats["meshes"]) == 2
+
+
+def test_fetch_async_reads_back_the_frame(rt):
+    """Slot.fetch_async (ftr_mesh_copy_async + texture copies, no host wait)
+    lands the same mesh and texture data as the waiting reads, also while the
+    other slot of a two-slot pipeline is busy."""
+    fins = [rt.FrameInput.from_frame(f) for f in _frames(130, 2)]
+    slots = [rt.Slot((96, 96, 96), BOX, fins[0], max(f.n_points for f in fins)) for _ in range(2)]
+    hosts = [s.host_buffers() for s in slots]
+    for s, f in zip(slots, fins):
+        s.submit(f)
+    for s, h, f in zip(slots, hosts, fins):
+        nv, nt = s.finish()
+        s.fetch_async(h)
+        s.submit(f)                       # the next frame queued behind the read-back
+        s.fetched.synchronize()
+        assert nv > 1000 and h["vertices"][:nv].abs().sum() > 0
+    for s, h in zip(slots, hosts):
+        s.finish()
+        v, t = s.mesh()
+        s.fetch_async(h)
+        s.fetched.synchronize()
+        nv, nt = len(v), len(t)
+        assert np.array_equal(h["vertices"][:nv].numpy(), v) and np.array_equal(h["tris"][:nt].numpy(), t)
+        assert np.array_equal(h["weights"][:nv].numpy(), s.out_w[:nv].cpu().numpy())
+        assert np.array_equal(h["rgb"][:nv].numpy(), s.out_rgb[:nv].cpu().numpy())
+        s.close()
