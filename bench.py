@@ -11,10 +11,13 @@ cubes and per-vertex texture (Sec. III-B, III-C), through the C ABI.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  ``value`` is frames/s of the whole job with
-inputs resident in HBM; ``e2e`` is the same metric through the C ABI with
-pinned host buffers (inputs copied in, mesh and texture copied out inside
-the timed region).  L2 is flushed (256 MiB write) between timed steps, outside
-the timed intervals.  Multi-GPU runs are independent replicas (frames do not
+inputs resident in HBM, one frame after another on one context; ``e2e`` is
+the same metric through the public API from page-locked host buffers (every
+frame's inputs copied in and its mesh and texture data copied out inside the
+timed region), frames streamed through two alternating resident slots so
+that one frame's copies overlap the other's kernels (``e2e.unpipelined``:
+the synchronous calls, one frame at a time).  L2 is flushed (256 MiB write)
+between the device-timed steps, outside the timed intervals.  Multi-GPU runs are independent replicas (frames do not
 shard), launched with torch.distributed.run; the max over ranks is taken.
 ``--impl reference`` times the FP64 CPU oracle on the same frame instead
 (rank 0 only), each step a bounded sample of one frame's work.
@@ -543,7 +546,8 @@ def run_multi(args, rank, dev, plain_frame=None):
     # served: 8 sessions at 30 fps (Poisson), grids {128,256,384}^3, HBM budget 120 GB
     sessions, rgbd_sessions = [], []
     for sid in range(8):
-        fr0, g = _mixed_frame(3000 + 8 * rank + sid, (128, 256, 384), rng, dev)
+        # every grid size of the configuration is served (sessions cycle through them)
+        fr0, g = _mixed_frame(3000 + 8 * rank + sid, ((128, 256, 384)[sid % 3],), rng, dev)
         fins = [serve.FrameInput.from_frame(fr0)]
         rgbd = [serve.FrameInput.from_frame(fr0, rgbd=True)]
         # continuous motion: the same body turning 4 degrees per frame

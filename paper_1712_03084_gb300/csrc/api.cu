@@ -179,6 +179,13 @@ cudaError_t grow_entries(ftr_ctx* c, int64_t need) {
     cudaError_t e = dalloc(&c->d_entries, cap);
     if (e != cudaSuccess) return e;
     c->cap_entries = cap;
+    // chunks: one per touched brick plus at most cap / chunk more
+    const int64_t units = (int64_t)c->n_bricks + cap / kSplatChunk + 2;
+    if (units > c->cap_units) {
+        dfree(c->d_unit_slot);
+        if ((e = dalloc(&c->d_unit_slot, (size_t)units)) != cudaSuccess) return e;
+        c->cap_units = units;
+    }
     // a heavy brick has more than one chunk of pairs: at most cap / chunk of them
     const int64_t heavy = cap / kSplatChunk + 1;
     if (heavy > c->cap_heavy) {
@@ -210,6 +217,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_meta);
     dfree(c->d_tile);
     dfree(c->d_unit_off);
+    dfree(c->d_unit_slot);
     dfree(c->d_heavy_idx);
     dfree(c->d_heavy_acc);
     dfree(c->d_heavy_done);
@@ -1223,6 +1231,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     b += (int64_t)c->stage_cap + (int64_t)c->tex_stage_cap;
     b += nb * (int64_t)sizeof(int) * 5 + (nb / 2048 + 1) * (int64_t)sizeof(int2) + 64;
     b += c->cap_entries * (int64_t)sizeof(int);
+    b += c->cap_units * (int64_t)sizeof(int);
     b += c->cap_heavy * (4 * kBrickVox * 8 + 4) + nb * 8;   // heavy-brick accumulators, chunk offsets
     b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
     b += 5 * c->Mh * (int64_t)sizeof(float2) + c->M * (int64_t)sizeof(float);

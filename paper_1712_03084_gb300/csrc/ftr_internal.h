@@ -114,6 +114,8 @@ struct ftr_ctx {
     int4* d_tile = nullptr;    // per-tile sums / offsets of the brick scan (pairs, touched, chunks, heavy)
     int* d_unit_off = nullptr; // per touched brick: first accumulation chunk; [touched] = all chunks
     int* d_heavy_idx = nullptr;  // per touched brick: index of its global accumulator, -1 for one chunk
+    int* d_unit_slot = nullptr;  // per accumulation chunk: its touched brick
+    int64_t cap_units = 0;
     unsigned long long* d_heavy_acc = nullptr;   // 4 x 512 int64 per heavy brick (zero between frames)
     int* d_heavy_done = nullptr; // chunks finished per heavy brick (zero between frames)
     int64_t cap_heavy = 0;

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_sums(const int* __restric
 __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restrict__ cnt, int nb, int nbxy,
                                                              const int4* __restrict__ tile_sum, int ntiles, int* off,
                                                              int* cursor, int* slot, int* active, int* meta,
-                                                             int* unit_off, int* heavy_idx) {
+                                                             int* unit_off, int* heavy_idx, int* unit_slot) {
     pdl_wait();
     __shared__ int4 sh[kScanT / 32];
     int4 pre = make_int4(0, 0, 0, 0), all = make_int4(0, 0, 0, 0);
@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kScanT) k_brick_tile_write(const int* __restri
                 slot[b] = s;
                 active[s] = b;
                 unit_off[s] = run.z + ex.z;
+                for (int j = 0; j < q.z; ++j) unit_slot[run.z + ex.z + j] = s;
                 heavy_idx[s] = q.w ? run.w + ex.w : -1;
                 const int bz = b / nbxy;
                 zmin = min(zmin, bz);
@@ -391,6 +392,7 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
                                                              const int* __restrict__ wild_weights,
                                                              float* __restrict__ vpool, int* __restrict__ ticket,
                                                              const int* __restrict__ unit_off,
+                                                             const int* __restrict__ unit_slot,
                                                              const int* __restrict__ heavy_idx,
                                                              unsigned long long* __restrict__ heavy_acc,
                                                              int* __restrict__ heavy_done) {
@@ -400,7 +402,6 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
     __shared__ float4 s_frac[kStage];
     __shared__ float4 s_nrm[kStage];
     unsigned long long* acc64 = reinterpret_cast<unsigned long long*>(&acc[0][0]);
-    const int nact = meta[0];
     const int tid = threadIdx.x;
     const int o = tid & 63;
     const int ox = o & 3, oy = (o >> 2) & 3, oz = o >> 4;
@@ -412,18 +413,8 @@ __global__ void __launch_bounds__(kAccThreads) k_splat_accum(GridDev g, const in
     for (;;) {
         if (tid == 0) {
             const int u = atomicAdd(ticket, 1);
-            int sl = 0;
-            if (u < nunits) {      // the touched brick whose chunks hold unit u
-                int lo = 0, hi = nact - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (unit_off[mid] <= u) lo = mid;
-                    else hi = mid - 1;
-                }
-                sl = lo;
-            }
             s_unit = u;
-            s_slot = sl;
+            s_slot = u < nunits ? unit_slot[u] : 0;   // the touched brick whose chunks hold unit u
         }
         __syncthreads();
         const int unit = s_unit, s = s_slot;
@@ -614,7 +605,7 @@ cudaError_t launch_splat(ftr_ctx* c) {
     launch_pdl(k_brick_tile_sums, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->d_tile, c->d_meta);
     launch_pdl(k_brick_tile_write, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
                c->d_tile, ntiles, c->d_brick_off, c->d_brick_cursor, c->d_brick_slot, c->d_active, c->d_meta,
-               c->d_unit_off, c->d_heavy_idx);
+               c->d_unit_off, c->d_heavy_idx, c->d_unit_slot);
     c->launches += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     launch_pdl(k_brick_fill, sms * 2, 256, 0, c->stream, c->pts.base, c->d_npts, c->g, c->d_brick_cursor, c->d_entries);
@@ -625,7 +616,7 @@ cudaError_t launch_splat(ftr_ctx* c) {
     const int grid = sms * 4;
     launch_pdl(k_splat_accum, grid, kAccThreads, 0, c->stream, c->g, c->d_active, c->d_meta, c->d_brick_off, c->d_entries,
                c->pts.base, c->pts.frac, c->pts.nrm, c->d_wild, c->d_vpool, c->d_meta + 4, c->d_unit_off,
-               c->d_heavy_idx, c->d_heavy_acc, c->d_heavy_done);
+               c->d_unit_slot, c->d_heavy_idx, c->d_heavy_acc, c->d_heavy_done);
     c->launches++;
     prof_end(c, ST_SPLAT_ACC);
     return cudaGetLastError();
