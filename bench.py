@@ -14,8 +14,8 @@ Prints one JSON line (rank 0).  ``value`` is frames/s of the whole job with
 inputs resident in HBM, one frame after another on one context; ``e2e`` is
 the same metric through the public API from page-locked host buffers (every
 frame's inputs copied in and its mesh and texture data copied out inside the
-timed region), frames streamed through two alternating resident slots so
-that one frame's copies overlap the other's kernels (``e2e.unpipelined``:
+timed region), frames streamed through four resident slots in turn so
+that one frame's copies overlap other frames' kernels (``e2e.unpipelined``:
 the synchronous calls, one frame at a time).  L2 is flushed (256 MiB write)
 between the device-timed steps, outside the timed intervals.  Multi-GPU runs are independent replicas (frames do not
 shard), launched with torch.distributed.run; the max over ranks is taken.
@@ -992,10 +992,14 @@ def run_ablation(args, rank, dev):
     return res
 
 
-def run_e2e(args, fr, grid, box, world, dev):
-    """End to end through the public API, frames streamed: two resident slots
-    (serve.Slot) alternate, so one frame's host->device copies and read-back
-    overlap the other frame's kernels.  Every step copies its inputs (points,
+E2E_SLOTS = 4          # resident slots the end-to-end stream rotates through
+E2E_MIN_STEPS = 120    # frames per timed end-to-end run (the stream fills and drains once)
+
+
+def run_e2e(args, fr, grid, box, world, dev, nslots=E2E_SLOTS):
+    """End to end through the public API, frames streamed: ``nslots``
+    resident slots (serve.Slot) take the frames in turn, so one frame's
+    host->device copies and read-back overlap other frames' kernels.  Every step copies its inputs (points,
     normals, weights, depth, W and RGB images) in from page-locked host memory
     and reads its result (mesh and per-vertex texture data) back into
     page-locked host memory; the clock stops when the last read-back has
@@ -1003,13 +1007,13 @@ def run_e2e(args, fr, grid, box, world, dev):
     import torch
     from paper_1712_03084_gb300 import serve
     fin = serve.FrameInput.from_frame(fr)
-    slots = [serve.Slot(grid, box, fin, fin.n_points) for _ in range(2)]
+    slots = [serve.Slot(grid, box, fin, fin.n_points) for _ in range(nslots)]
     hosts = [s.host_buffers() for s in slots]
     d2h = [0]
 
     def run(n):
         for i in range(n):
-            s, h = slots[i % 2], hosts[i % 2]
+            s, h = slots[i % nslots], hosts[i % nslots]
             if s.busy:
                 s.finish()
                 d2h[0] = s.fetch_async(h)
@@ -1025,20 +1029,21 @@ def run_e2e(args, fr, grid, box, world, dev):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    steps = max(args.steps, E2E_MIN_STEPS)
     gc.disable()
     t0 = time.perf_counter()
-    run(args.steps)
+    run(steps)
     total = time.perf_counter() - t0
     gc.enable()
     for s in slots:
         s.close()
     total = replica_max(total, world, dev)
-    return {"value": round(replica_rate(args.steps, total, world), 2), "unit": UNIT,
+    return {"value": round(replica_rate(steps, total, world), 2), "unit": UNIT,
             "h2d_bytes_per_step": int(fin.h2d_bytes()), "d2h_bytes_per_step": int(d2h[0]),
-            "ms_per_step": round(1000 * total / args.steps, 4),
-            "timing": "host wall clock over all steps; two resident slots alternate (copies of one frame overlap "
-                      "the other's kernels), page-locked host buffers in and out, no L2 flush (inputs arrive "
-                      "from host memory every step)"}
+            "ms_per_step": round(1000 * total / steps, 4), "steps": steps, "slots": nslots,
+            "timing": f"host wall clock over {steps} frames streamed through {nslots} resident slots in turn "
+                      "(one frame's copies overlap other frames' kernels), page-locked host buffers in and out, "
+                      "no L2 flush (inputs arrive from host memory every step)"}
 
 
 def run_e2e_sync(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
