@@ -421,6 +421,7 @@ void eval_free(ftr_ctx* c) {
     EvalScratch* ev = c->ev;
     if (!ev) return;
     if (ev->zkey) cudaFree(ev->zkey);
+    if (ev->big) cudaFree(ev->big);
     if (ev->col) cudaFree(ev->col);
     if (ev->pts) cudaFree(ev->pts);
     if (ev->d2) cudaFree(ev->d2);

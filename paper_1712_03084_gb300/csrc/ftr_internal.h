@@ -297,6 +297,8 @@ cudaError_t launch_texture_bounded(ftr_ctx* c, const ViewSet& vs, float depth_to
 struct EvalScratch {
     unsigned long long* zkey = nullptr;   // per pixel: (float32 z bits << 32) | triangle, ~0 = empty
     int64_t zkey_cap = 0;
+    int* big = nullptr;                   // large triangles for the shared-pixel pass, then their count
+    int64_t big_cap = 0;
     int* col = nullptr;                   // 2 x pixels: column distances to the sensor / rendered silhouette
     float4* pts = nullptr;                // 2 x pixels: compacted sensor and rendered points (.w = pixel)
     float* d2 = nullptr;                  // pixels: squared closest-point distance per sensor pixel

@@ -8,7 +8,10 @@
 //              pixel centres of the screen bounding box, test coverage with
 //              the three edge functions, intersect the pixel's ray with the
 //              triangle's plane and keep the nearest surface with a 64-bit
-//              atomicMin on (float32 z bits << 32 | triangle index);
+//              atomicMin on (float32 z bits << 32 | triangle index); a
+//              triangle with more than 1024 pixel centres in its box is
+//              listed instead and k_raster_big shares its pixels among the
+//              threads of a CTA (the same per-pixel code);
 //   k_resolve  one thread per pixel: depth from the key, colour from the
 //              winning triangle (perspective-correct barycentrics of the hit
 //              point; vertex colours or the weighted blend of the views).
@@ -32,6 +35,7 @@ namespace ftr {
 namespace {
 
 constexpr double kZNear = 0.01;     // metres: a triangle with a vertex nearer the camera plane is not drawn
+constexpr int kBigPx = 1024;        // bounding-box pixels above which a triangle is shared by a CTA
 
 struct CamDev {
     int w, h;
@@ -61,58 +65,104 @@ __device__ __forceinline__ double edge(double ua, double va, double ub, double v
     return ds(dm(ds(ub, ua), ds(py, va)), dm(ds(vb, va), ds(px, ua)));
 }
 
-__global__ void __launch_bounds__(128) k_raster(CamDev cam, const float* __restrict__ verts,
-                                                const int32_t* __restrict__ tris, int64_t nt, int64_t nv,
-                                                unsigned long long* __restrict__ zkey) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+// Everything a pixel test needs, set up once per triangle.
+struct TriSetup {
+    double u[3], v[3];
+    double nx, ny, nz, num;
+    double x0, x1, y0, y1;
+};
+
+// Projects the triangle and its plane; false if it is not drawn (an index
+// out of range, a vertex nearer than kZNear, zero area, or no pixel centre
+// in its clipped bounding box).
+__device__ __forceinline__ bool tri_setup(const CamDev& cam, const float* __restrict__ verts,
+                                          const int32_t* __restrict__ tris, int64_t t, int64_t nv, TriSetup& s) {
     const int i3[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
-    double xc[3][3], u[3], v[3];
+    double xc[3][3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        if (i3[m] < 0 || i3[m] >= nv) return;
+        if (i3[m] < 0 || i3[m] >= nv) return false;
         cam_point(cam, verts + 3 * (int64_t)i3[m], xc[m]);
-        if (!(xc[m][2] >= kZNear)) return;
+        if (!(xc[m][2] >= kZNear)) return false;
         const double a = dd(xc[m][0], xc[m][2]);
         const double b = dd(xc[m][1], xc[m][2]);
-        u[m] = da(da(dm(cam.K[0], a), dm(cam.K[1], b)), cam.K[2]);
-        v[m] = da(dm(cam.K[4], b), cam.K[5]);
+        s.u[m] = da(da(dm(cam.K[0], a), dm(cam.K[1], b)), cam.K[2]);
+        s.v[m] = da(dm(cam.K[4], b), cam.K[5]);
     }
-    const double area = ds(dm(ds(u[1], u[0]), ds(v[2], v[0])), dm(ds(v[1], v[0]), ds(u[2], u[0])));
-    if (!isfinite(area) || area == 0.0) return;
-    const double x0 = fmax(ceil(fmin(fmin(u[0], u[1]), u[2])), 0.0);
-    const double x1 = fmin(floor(fmax(fmax(u[0], u[1]), u[2])), (double)(cam.w - 1));
-    const double y0 = fmax(ceil(fmin(fmin(v[0], v[1]), v[2])), 0.0);
-    const double y1 = fmin(floor(fmax(fmax(v[0], v[1]), v[2])), (double)(cam.h - 1));
-    if (x1 < x0 || y1 < y0) return;
+    const double area = ds(dm(ds(s.u[1], s.u[0]), ds(s.v[2], s.v[0])), dm(ds(s.v[1], s.v[0]), ds(s.u[2], s.u[0])));
+    if (!isfinite(area) || area == 0.0) return false;
+    s.x0 = fmax(ceil(fmin(fmin(s.u[0], s.u[1]), s.u[2])), 0.0);
+    s.x1 = fmin(floor(fmax(fmax(s.u[0], s.u[1]), s.u[2])), (double)(cam.w - 1));
+    s.y0 = fmax(ceil(fmin(fmin(s.v[0], s.v[1]), s.v[2])), 0.0);
+    s.y1 = fmin(floor(fmax(fmax(s.v[0], s.v[1]), s.v[2])), (double)(cam.h - 1));
+    if (s.x1 < s.x0 || s.y1 < s.y0) return false;
     double e1v[3], e2v[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         e1v[r] = ds(xc[1][r], xc[0][r]);
         e2v[r] = ds(xc[2][r], xc[0][r]);
     }
-    const double nx = ds(dm(e1v[1], e2v[2]), dm(e1v[2], e2v[1]));
-    const double ny = ds(dm(e1v[2], e2v[0]), dm(e1v[0], e2v[2]));
-    const double nz = ds(dm(e1v[0], e2v[1]), dm(e1v[1], e2v[0]));
-    const double num = da(da(dm(nx, xc[0][0]), dm(ny, xc[0][1])), dm(nz, xc[0][2]));
-    const unsigned long long tid = (unsigned long long)t;
-    for (double py = y0; py <= y1; py += 1.0) {
+    s.nx = ds(dm(e1v[1], e2v[2]), dm(e1v[2], e2v[1]));
+    s.ny = ds(dm(e1v[2], e2v[0]), dm(e1v[0], e2v[2]));
+    s.nz = ds(dm(e1v[0], e2v[1]), dm(e1v[1], e2v[0]));
+    s.num = da(da(dm(s.nx, xc[0][0]), dm(s.ny, xc[0][1])), dm(s.nz, xc[0][2]));
+    return true;
+}
+
+// Coverage and depth of pixel (px, py) (dy = its ray's y slope); the key
+// goes to the z-buffer when the pixel is covered.
+__device__ __forceinline__ void tri_pixel(const CamDev& cam, const TriSetup& s, double px, double py, double dy,
+                                          unsigned long long tid, unsigned long long* __restrict__ zkey) {
+    const double e0 = edge(s.u[0], s.v[0], s.u[1], s.v[1], px, py);
+    const double e1 = edge(s.u[1], s.v[1], s.u[2], s.v[2], px, py);
+    const double e2 = edge(s.u[2], s.v[2], s.u[0], s.v[0], px, py);
+    const bool in = (e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0) || (e0 <= 0.0 && e1 <= 0.0 && e2 <= 0.0);
+    if (!in) return;
+    const double dx = dd(ds(ds(px, cam.K[2]), dm(cam.K[1], dy)), cam.K[0]);
+    const double den = da(da(dm(s.nx, dx), dm(s.ny, dy)), s.nz);
+    if (den == 0.0) return;
+    const double z = dd(s.num, den);
+    if (!(z > 0.0) || !isfinite(z)) return;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(__double2float_rn(z)) << 32) | tid;
+    atomicMin(zkey + (int64_t)py * cam.w + (int64_t)px, key);
+}
+
+// One thread per triangle; a triangle whose bounding box holds more than
+// kBigPx pixel centres is listed for k_raster_big instead.
+__global__ void __launch_bounds__(128) k_raster(CamDev cam, const float* __restrict__ verts,
+                                                const int32_t* __restrict__ tris, int64_t nt, int64_t nv,
+                                                unsigned long long* __restrict__ zkey, int* __restrict__ big,
+                                                int* __restrict__ nbig) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    TriSetup s;
+    if (!tri_setup(cam, verts, tris, t, nv, s)) return;
+    if ((s.x1 - s.x0 + 1.0) * (s.y1 - s.y0 + 1.0) > (double)kBigPx) {
+        big[atomicAdd(nbig, 1)] = (int)t;          // at most nt entries
+        return;
+    }
+    for (double py = s.y0; py <= s.y1; py += 1.0) {
         const double dy = dd(ds(py, cam.K[5]), cam.K[4]);
-        const int64_t row = (int64_t)py * cam.w;
-        for (double px = x0; px <= x1; px += 1.0) {
-            const double e0 = edge(u[0], v[0], u[1], v[1], px, py);
-            const double e1 = edge(u[1], v[1], u[2], v[2], px, py);
-            const double e2 = edge(u[2], v[2], u[0], v[0], px, py);
-            const bool in = (e0 >= 0.0 && e1 >= 0.0 && e2 >= 0.0) || (e0 <= 0.0 && e1 <= 0.0 && e2 <= 0.0);
-            if (!in) continue;
-            const double dx = dd(ds(ds(px, cam.K[2]), dm(cam.K[1], dy)), cam.K[0]);
-            const double den = da(da(dm(nx, dx), dm(ny, dy)), nz);
-            if (den == 0.0) continue;
-            const double z = dd(num, den);
-            if (!(z > 0.0) || !isfinite(z)) continue;
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(__double2float_rn(z)) << 32) | tid;
-            atomicMin(zkey + row + (int64_t)px, key);
+        for (double px = s.x0; px <= s.x1; px += 1.0) tri_pixel(cam, s, px, py, dy, (unsigned long long)t, zkey);
+    }
+}
+
+// The listed large triangles, one CTA each (grid-stride over the list): the
+// CTA's threads share the triangle's pixel centres.
+__global__ void __launch_bounds__(256) k_raster_big(CamDev cam, const float* __restrict__ verts,
+                                                    const int32_t* __restrict__ tris, int64_t nv,
+                                                    unsigned long long* __restrict__ zkey,
+                                                    const int* __restrict__ big, const int* __restrict__ nbig) {
+    const int n = *nbig;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const int64_t t = big[j];
+        TriSetup s;
+        if (!tri_setup(cam, verts, tris, t, nv, s)) continue;    // always drawn: listed by k_raster
+        const int64_t wx = (int64_t)(s.x1 - s.x0) + 1, hy = (int64_t)(s.y1 - s.y0) + 1;
+        for (int64_t k = threadIdx.x; k < wx * hy; k += blockDim.x) {
+            const double py = s.y0 + (double)(k / wx), px = s.x0 + (double)(k % wx);
+            const double dy = dd(ds(py, cam.K[5]), cam.K[4]);
+            tri_pixel(cam, s, px, py, dy, (unsigned long long)t, zkey);
         }
     }
 }
@@ -294,13 +344,27 @@ int ftr_render(ftr_ctx* c, const ftr_render_src* src, const ftr_camera* cam, flo
             return cuda_fail(c, e, "ftr_render: z-buffer");
         ev->zkey_cap = npx;
     }
+    if (src->n_tris + 1 > ev->big_cap) {
+        cudaStreamSynchronize(c->stream);
+        if (ev->big) cudaFree(ev->big);
+        ev->big = nullptr;
+        ev->big_cap = 0;
+        if ((e = cudaMalloc((void**)&ev->big, (size_t)(src->n_tris + 1) * sizeof(int))) != cudaSuccess)
+            return cuda_fail(c, e, "ftr_render: triangle list");
+        ev->big_cap = src->n_tris + 1;
+    }
     const CamDev cd = make_cam(*cam);
     if ((e = cudaMemsetAsync(ev->zkey, 0xff, (size_t)npx * sizeof(unsigned long long), c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "ftr_render: clear");
     if (src->n_tris > 0) {
-        k_raster<<<(unsigned)((src->n_tris + 127) / 128), 128, 0, c->stream>>>(cd, src->vertices, src->tris,
-                                                                             src->n_tris, src->n_vertices, ev->zkey);
-        c->launches++;
+        int* nbig = ev->big + src->n_tris;
+        if ((e = cudaMemsetAsync(nbig, 0, sizeof(int), c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "ftr_render: clear");
+        k_raster<<<(unsigned)((src->n_tris + 127) / 128), 128, 0, c->stream>>>(
+            cd, src->vertices, src->tris, src->n_tris, src->n_vertices, ev->zkey, ev->big, nbig);
+        k_raster_big<<<2 * 152, 256, 0, c->stream>>>(cd, src->vertices, src->tris, src->n_vertices, ev->zkey, ev->big,
+                                                     nbig);
+        c->launches += 2;
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ftr_render: raster");
     }
     k_resolve<<<(unsigned)((npx + 255) / 256), 256, 0, c->stream>>>(

@@ -180,6 +180,27 @@ def test_edge_cases(ftr):
     ctx.close()
 
 
+def test_large_triangles_share_their_pixels(ftr):
+    """Triangles with more than 1024 pixel centres in their box go to the
+    CTA-shared pass; the depth stays bit-exact, including where they meet
+    small triangles in front of them."""
+    import torch
+    ctx = ftr.Context((32, 32, 32), (-1.0, -1.0, -1.0, 1.0, 1.0, 1.0))
+    RT = np.concatenate([np.eye(3), np.zeros((3, 1))], axis=1).astype(np.float32)
+    K = np.array([[1060.0, 0, 960.0], [0, 1060.0, 540.0], [0, 0, 1.0]], np.float32)
+    # a tilted quad filling the view, one mid-size triangle and a small one in front
+    quad = [[-2.0, -1.2, 2.5], [2.0, -1.2, 3.5], [2.0, 1.2, 3.5], [-2.0, 1.2, 2.5]]
+    mid = [[-0.3, -0.2, 2.0], [0.2, -0.25, 2.1], [0.0, 0.3, 2.05]]
+    small = [[0.01, 0.01, 1.5], [0.02, 0.01, 1.5], [0.01, 0.02, 1.5]]
+    verts = np.array(quad + mid + small, np.float32)
+    tris = np.array([[0, 1, 2], [0, 2, 3], [4, 5, 6], [7, 8, 9]], np.int32)
+    _, depth, _ = _render(ftr, torch, ctx, verts, tris, K, RT, 1920, 1080)
+    ref, win = orender.rasterise(verts, tris, K, RT, 1920, 1080)
+    assert (win == 0).sum() > 500000 and (win == 2).sum() > 10000 and (win == 3).sum() > 0
+    assert np.array_equal(depth.cpu().numpy(), ref)
+    ctx.close()
+
+
 def _uv_sphere(r, centre, n_th=181, n_ph=361):
     th, ph = np.meshgrid(np.linspace(0, np.pi, n_th), np.linspace(0, 2 * np.pi, n_ph), indexing="ij")
     P = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], -1).reshape(-1, 3) * r + centre
