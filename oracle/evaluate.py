@@ -70,7 +70,7 @@ def vre(rendered_depth, sensor_depth):
     return (x / o if o else 0.0), x, o, int(r.sum()), int(g.sum())
 
 
-def _directed_sq(p, q, chunk=2048):
+def _directed_sq(p, q, chunk=256):
     """max over p of the squared distance to the nearest of q (brute force)."""
     worst = 0
     for s in range(0, len(p), chunk):
@@ -98,7 +98,7 @@ def backproject(K, depth):
     return np.stack([z * dx, z * dy, z], axis=1)
 
 
-def closest_sq(P, Q, chunk=1024):
+def closest_sq(P, Q, chunk=128):
     """Squared distance from each point of P to the closest point of Q (brute force)."""
     out = np.empty(len(P))
     for s in range(0, len(P), chunk):
