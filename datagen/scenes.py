@@ -388,7 +388,7 @@ def frame_config(name):
 
 def human_frame(seed=0, K=4, ring=2.5, height=1.2, depth_wh=(512, 424), fxy=365.0,
                 rgb_wh=(1920, 1080), rgb_f=1060.0, angle_range=40.0, with_rgb=True,
-                noise_coef=0.0012, pixel_stride=1, device=None, yaw_deg=None):
+                noise_coef=0.0012, pixel_stride=1, device=None, yaw_deg=None, pose_seed=None):
     """One synthetic multi-camera frame of the capsule human.
 
     Returns dict(points [P,3] f32, normals [P,3] f32, weights [P] f32,
@@ -396,7 +396,8 @@ def human_frame(seed=0, K=4, ring=2.5, height=1.2, depth_wh=(512, 424), fxy=365.
     K_rgb, world_to_rgb)], prims, cams).
     """
     rng = np.random.default_rng(seed)
-    prims = human_primitives(seed, angle_range, yaw_deg)
+    # pose_seed: another body pose seen by the same rig (cameras, texture, noise stream of ``seed``)
+    prims = human_primitives(seed if pose_seed is None else pose_seed, angle_range, yaw_deg)
     cams = ring_cameras(K, ring, height, (0.0, 0.95, 0.0), depth_wh[0], depth_wh[1], fxy, fxy,
                         phase_deg=float(rng.uniform(0, 360.0 / K)))
     params = texture_params(seed)

@@ -29,3 +29,14 @@ def test_human_frame_is_seeded_and_sane():
     for (s, n), cam in zip(a["per_camera"], a["cams"]):
         d = cam.pos - P[s:s + n]
         assert np.mean(np.einsum("ij,ij->i", d, a["normals"][s:s + n]) > 0) > 0.99
+
+
+def test_pose_seed_moves_the_body_not_the_rig():
+    from datagen import human_frame
+    kw = dict(K=2, depth_wh=(64, 53), fxy=45.6, rgb_wh=(32, 18), rgb_f=35.0)
+    a = human_frame(seed=5, **kw)
+    b = human_frame(seed=5, pose_seed=99, **kw)
+    for va, vb in zip(a["views"], b["views"]):
+        assert np.array_equal(va["K"], vb["K"]) and np.array_equal(va["world_to_cam"], vb["world_to_cam"])
+        assert np.array_equal(va["world_to_rgb"], vb["world_to_rgb"])
+    assert not np.array_equal(a["views"][0]["depth"], b["views"][0]["depth"])
