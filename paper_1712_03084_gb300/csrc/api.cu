@@ -348,7 +348,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_active, c->n_bricks);
     ALLOC(c->d_meta, 8);
     ALLOC(c->d_kerr, 1);
-    ALLOC(c->d_tile, (c->n_bricks + 2047) / 2048 + 1);
+    ALLOC(c->d_tile, (c->n_bricks + kBrickScanTile - 1) / kBrickScanTile + 1);
     ALLOC(c->d_unit_off, c->n_bricks + 1);
     ALLOC(c->d_heavy_idx, c->n_bricks);
     ALLOC(c->d_vpool, (size_t)c->n_bricks * 3 * kBrickVox);
@@ -363,7 +363,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_ticket, 1);
     c->mc_blocks = grid_n[1] * grid_n[2];      // marching cubes counts per grid row
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
-    ALLOC(c->d_mc_tile, (c->mc_blocks + 2047) / 2048 + 1);
+    ALLOC(c->d_mc_tile, (c->mc_blocks + kMcScanTile - 1) / kMcScanTile + 1);
     {
         int wp = 1;
         while (wp < (grid_n[0] + 31) / 32) wp <<= 1;
@@ -1229,7 +1229,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     int64_t b = 0;
     b += c->pts.cap * (int64_t)(sizeof(int4) + 2 * sizeof(float4));
     b += (int64_t)c->stage_cap + (int64_t)c->tex_stage_cap;
-    b += nb * (int64_t)sizeof(int) * 5 + (nb / 2048 + 1) * (int64_t)sizeof(int2) + 64;
+    b += nb * (int64_t)sizeof(int) * 5 + (nb / kBrickScanTile + 1) * (int64_t)sizeof(int4) + 64;
     b += c->cap_entries * (int64_t)sizeof(int);
     b += c->cap_units * (int64_t)sizeof(int);
     b += c->cap_heavy * (4 * kBrickVox * 8 + 4) + nb * 8;   // heavy-brick accumulators, chunk offsets

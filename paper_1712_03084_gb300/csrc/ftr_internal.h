@@ -15,6 +15,8 @@ namespace ftr {
 constexpr int kBrick = 8;                 // splat accumulation brick edge (nodes)
 constexpr int kBrickVox = kBrick * kBrick * kBrick;
 constexpr int kMaxViews = 8;
+constexpr int kBrickScanTile = 256;   // bricks per tile of the brick-count scan (one block scan per CTA)
+constexpr int kMcScanTile = 256;      // grid rows per tile of the marching-cubes row scan
 constexpr int kMcThreads = 256;           // marching-cubes CTA size (chunks of 8 grid rows)
 constexpr int kMaxTrisPerCase = 5;
 constexpr int kSplatChunk = 1024;          // (point, brick) pairs per accumulation work unit

@@ -236,7 +236,8 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
 // Exclusive scan of the three row-count arrays (length nb) in tiles of
 // kScanTile: tile sums, then each tile adds up the sums before it and writes
 // off[a * (nb + 1) + i]; totals go to off[a * (nb + 1) + nb].
-constexpr int kScanTile = 2048;
+constexpr int kScanTile = kMcScanTile;
+static_assert(kScanTile % kMcThreads == 0, "a tile is a whole number of block scans");
 
 __global__ void __launch_bounds__(kMcThreads) k_mc_tile_sums(const int* __restrict__ blk, int nb, int3* tile) {
     pdl_wait();

@@ -178,11 +178,12 @@ __global__ void k_brick_fill(const int4* __restrict__ pbase, const int64_t* __re
 
 // Exclusive scan of the brick counts in three coalesced launches over tiles
 // of kTile bricks: (1) per-tile sums of the counts and of the touched
-// bricks, (2) one CTA scans the tile sums, (3) each tile rescans itself
-// with its offset and writes the brick offsets, the dense slot of every
+// bricks, (2) each tile adds up the sums before it, rescans itself with
+// that offset and writes the brick offsets, the dense slot of every
 // touched brick (-1 otherwise), the list of touched bricks and the z-range.
 constexpr int kScanT = 256;
-constexpr int kTile = 2048;
+constexpr int kTile = kBrickScanTile;
+static_assert(kTile % kScanT == 0, "a tile is a whole number of block scans");
 // A brick's pairs are accumulated in chunks of at most kChunk (point, brick)
 // pairs, one chunk per CTA at a time; the 32-bit hi/lo accumulators stay exact
 // for up to 2047 contributions per voxel.
