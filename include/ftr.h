@@ -342,7 +342,7 @@ int64_t ftr_launch_count(const ftr_ctx* ctx);
 
 /* ---- rendering and objective evaluation (Sec. III-C, III-E) ------------------
  *
- * Sec. III-E judges a reconstruction by projecting the mesh into the K + K'
+ * Sec. III-E scores a reconstruction by projecting the mesh into the K + K'
  * sensor views (K used by the reconstruction, K' held out) and comparing the
  * rendered depth and colour with what each sensor captured.  Every pointer
  * in this section is DEVICE memory; the render only enqueues, the two
