@@ -282,6 +282,21 @@ def oracle_setup(cfg, fr):
     return {"cfg": cfg, "fr": fr, "A": r["A"], "L": r["L"], "verts": r["mesh"]["vertices"]}
 
 
+def oracle_sphere64(reps=2):
+    """The whole oracle path on the 64^3 sphere (20,000 points), seconds per
+    frame: the small configuration, timed in full (no sampling)."""
+    from datagen import f32_box, frame_config, sphere_points
+    from oracle import pipeline
+    cfg = frame_config("sphere64")
+    P, N, W = sphere_points(20000, 0.005, seed=0)
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        pipeline.reconstruct(P, N, W, cfg["grid_n"], f32_box(cfg["bbox"]))
+        t.append(time.perf_counter() - t0)
+    return float(min(t))
+
+
 def oracle_baseline(cfg, fr, steps=1):
     ctx_o = oracle_setup(cfg, fr)
     w0, c0 = time.perf_counter(), time.process_time()
@@ -492,10 +507,16 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, est = oracle_baseline(cfg, fr, steps=1)
+        s64 = oracle_sphere64()
+        host_cores = os.cpu_count() or 1
         cpu = {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"FP64 NumPy oracle on the same frame: full splat, level and texture, 1/{SAMPLE_S} of "
                          f"the 12 axis passes of the 3D transforms, of the filter and of the marching-cubes slabs, "
-                         f"scaled to one frame ({est[0]:.1f} s/frame estimated)"}
+                         f"scaled to one frame ({est[0]:.1f} s/frame estimated)",
+               "host_cores": host_cores,
+               "all_cores_bound": round(v * host_cores, 4),
+               "sphere64": {"seconds_per_frame": round(s64, 3), "frames_per_s": round(1.0 / s64, 3),
+                            "note": "the whole oracle path on the 64^3 sphere (20,000 points), one process"}}
     if ctx is not None:
         ctx.close()
     if rank != 0:
