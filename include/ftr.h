@@ -243,13 +243,12 @@ int ftr_frame_finish(ftr_ctx* ctx, ftr_mesh* out);
  * ftr_solve + ftr_extract_mesh_async + ftr_texture_async (k = 0: no texture)
  * as one CUDA graph replay on the context stream, for the points added since
  * ftr_reset; complete it with ftr_frame_finish.  The graph is captured on the
- * first call and again whenever the views (their image pointers, sizes or
- * calibrations), depth_tol, the outputs, the output capacity or a context
- * buffer changed (a buffer grows when a frame has more points or a larger
- * mesh than any before).  A capture costs host time in the order of a frame,
- * so a stream of frames should land its images in the same device buffers
- * every frame.  Same results as the separate calls; does not return L (see
- * ftr_frame_info / ftr_solve).
+ * first call and again whenever depth_tol, the outputs, the output capacity,
+ * the number of views or a context buffer changed (a buffer grows when a
+ * frame has more points or a larger mesh than any before).  When only the
+ * views' image pointers or calibrations changed, the graph's texture node is
+ * given the new views in place (no capture).  Same results as the separate
+ * calls; does not return L (see ftr_frame_info / ftr_solve).
  */
 int ftr_frame_launch(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out,
                      int64_t out_capacity);

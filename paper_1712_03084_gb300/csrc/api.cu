@@ -255,6 +255,7 @@ void free_all(ftr_ctx* c) {
         if (c->ev_stop[s]) cudaEventDestroy(c->ev_stop[s]);
     }
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -909,14 +910,38 @@ int ftr_frame_launch(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, 
         if ((e = grow_mesh(c, guess, guess, 2 * guess)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
         c->graph_valid = false;
     }
-    const bool same = c->graph_valid && c->graph_tol == depth_tol && c->graph_cap == out_capacity &&
-                      memcmp(&c->graph_vs, &vs, sizeof(vs)) == 0 &&
-                      memcmp(c->graph_outs, outs, sizeof(outs)) == 0;
+    const bool same_but_views = c->graph_valid && c->graph_tol == depth_tol && c->graph_cap == out_capacity &&
+                                memcmp(c->graph_outs, outs, sizeof(outs)) == 0;
+    bool same = same_but_views && memcmp(&c->graph_vs, &vs, sizeof(vs)) == 0;
+    if (same_but_views && !same && c->graph_tex_node && vs.k == c->graph_vs.k && vs.k > 0) {
+        // only the images or calibrations changed: give the graph's texture
+        // node the new view set instead of capturing the frame again
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(c->graph_tex_node, &kp) == cudaSuccess && kp.kernelParams &&
+            kp.func == texture_kernel(vs.k)) {
+            void* args[9];
+            for (int i = 0; i < 9; ++i) args[i] = kp.kernelParams[i];
+            ViewSet vs_arg = vs;
+            args[0] = &vs_arg;
+            kp.kernelParams = args;
+            if (cudaGraphExecKernelNodeSetParams(c->graph_exec, c->graph_tex_node, &kp) == cudaSuccess &&
+                cudaGraphKernelNodeSetParams(c->graph_tex_node, &kp) == cudaSuccess) {
+                c->graph_vs = vs;
+                same = true;
+            }
+        }
+        cudaGetLastError();
+    }
     if (!same) {
         if (c->graph_exec) {
             cudaGraphExecDestroy(c->graph_exec);
             c->graph_exec = nullptr;
         }
+        if (c->graph) {
+            cudaGraphDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        c->graph_tex_node = nullptr;
         const bool prof = c->prof;
         c->prof = false;                 // no event records inside the capture
         const int64_t l0 = c->launches;
@@ -929,7 +954,31 @@ int ftr_frame_launch(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, 
         }
         c->prof = prof;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess && vs.k > 0) {
+            // remember the texture kernel node for views-only updates
+            size_t n = 0;
+            if (cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess && n > 0) {
+                std::vector<cudaGraphNode_t> nodes(n);
+                if (cudaGraphGetNodes(graph, nodes.data(), &n) == cudaSuccess) {
+                    const void* tex_fn = texture_kernel(vs.k);
+                    for (size_t i = 0; i < n; ++i) {
+                        cudaGraphNodeType t;
+                        cudaKernelNodeParams kp;
+                        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel &&
+                            cudaGraphKernelNodeGetParams(nodes[i], &kp) == cudaSuccess && kp.func == tex_fn) {
+                            c->graph_tex_node = nodes[i];
+                            break;
+                        }
+                    }
+                }
+            }
+            cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            c->graph = graph;                 // kept: its texture node is updated in place
+        } else if (graph) {
+            cudaGraphDestroy(graph);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch: graph capture");
         c->graph_launches = c->launches - l0;
         c->launches = l0;

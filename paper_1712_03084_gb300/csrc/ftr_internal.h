@@ -187,6 +187,8 @@ struct ftr_ctx {
 
     // whole-frame CUDA graph (ftr_frame_launch)
     cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;           // the captured graph graph_exec was instantiated from
+    cudaGraphNode_t graph_tex_node = nullptr;   // its texture kernel node (views-only updates)
     int64_t graph_launches = 0;       // kernels per replay
     bool graph_valid = false;
     ftr::ViewSet graph_vs{};
@@ -285,6 +287,8 @@ cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);
 cudaError_t launch_dense_V(ftr_ctx* c, float* out_dev);
 cudaError_t launch_load_dense_V(ftr_ctx* c, const float* V_dev);
 
+// The texture kernel instantiated for k views (the function a graph node launches).
+const void* texture_kernel(int k);
 cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv,
                            uint8_t* rgb, uint8_t* textured);
 // Same, for nv caller-given vertices (device, nv x 3).

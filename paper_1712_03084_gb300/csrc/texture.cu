@@ -259,6 +259,16 @@ cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, const fl
 
 }  // namespace
 
+const void* texture_kernel(int k) {
+    const int G = k <= 1 ? 1 : (k <= 2 ? 2 : (k <= 4 ? 4 : 8));
+    switch (G) {
+        case 1: return reinterpret_cast<const void*>(k_texture<1>);
+        case 2: return reinterpret_cast<const void*>(k_texture<2>);
+        case 4: return reinterpret_cast<const void*>(k_texture<4>);
+        default: return reinterpret_cast<const void*>(k_texture<8>);
+    }
+}
+
 cudaError_t launch_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, float* w, float* uv, uint8_t* rgb,
                            uint8_t* textured) {
     return run_texture(c, vs, depth_tol, c->d_verts, c->n_verts, nullptr, w, uv, rgb, textured);

@@ -313,6 +313,48 @@ def test_graph_frame_equals_separate_calls(ftr):
     g.close()
 
 
+def test_graph_frame_follows_new_view_buffers(ftr):
+    """Frames whose views live in other device buffers (other images, other
+    calibrations) give the texture data of those views: the graph's texture
+    node takes the new view set (or the frame is captured again)."""
+    import torch
+    name = "human96"
+    c = G.CASES[name]
+    P, N, W, views = G.case_inputs(name)
+    other = G.case_inputs("human128")[3]            # another rig and other images, same sizes
+    tol = float(np.float32(0.03))
+
+    def dev(vs, invert):
+        out = []
+        for v in vs:
+            d = dict(v)
+            for key in ("depth", "conf", "rgb"):
+                a = v[key]
+                if key == "rgb" and invert:
+                    a = (255 - a).astype(np.uint8)
+                d[key] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            out.append(d)
+        return out
+    sets = [dev(views, False), dev(views, True), dev(other, False)]
+    K = len(views)
+    cap = 200000
+    outs = [torch.zeros((cap, K), dtype=torch.float32, device="cuda"),
+            torch.zeros((cap, K, 2), dtype=torch.float32, device="cuda"),
+            torch.zeros((cap, 3), dtype=torch.uint8, device="cuda"),
+            torch.zeros((cap,), dtype=torch.uint8, device="cuda")]
+    g = ftr.Context(c["grid"], c["bbox"])
+    for j in (0, 1, 2, 0, 2, 1):
+        g.reset()
+        g.splat(P, N, W)
+        ftr.ftr_frame_launch(g.h, sets[j], tol, *outs, out_capacity=cap)
+        m = ftr.ftr_frame_finish(g.h)
+        nv = m.n_vertices
+        ref = g.texture_numpy(sets[j], tol, nv)
+        assert np.array_equal(outs[0][:nv].cpu().numpy(), ref["weights"])
+        assert np.array_equal(outs[2][:nv].cpu().numpy(), ref["rgb"])
+    g.close()
+
+
 @pytest.mark.parametrize("name", ["sphere64", "human_aniso"])
 def test_inside_mask_is_the_binarised_volume(ftr, name):
     """The exported binarised volume (Sec. IV's input) is exactly A >= L of
