@@ -140,7 +140,7 @@ class Slot:
                 self.W[:n].copy_(fin.weights, non_blocking=True)
             for d, v in zip(self.views, fin.views):
                 for k in ("K", "world_to_cam", "K_rgb", "world_to_rgb"):
-                    d[k] = v[k]          # the frame's calibration (a change re-captures the graph)
+                    d[k] = v[k]          # the frame's calibration (updated in the frame graph)
                 d["depth"].copy_(v["depth"], non_blocking=True)
                 if not fin.rgbd:
                     d["conf"].copy_(v["conf"], non_blocking=True)
