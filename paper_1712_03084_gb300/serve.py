@@ -257,15 +257,22 @@ class Session:
 class Server:
     """Continuous-batching request loop over resident per-session slots."""
 
-    def __init__(self, hbm_budget_bytes):
+    def __init__(self, hbm_budget_bytes, slot_factory=None, sync=None):
+        """``slot_factory(session)`` makes a session's slot (default: a
+        resident ``Slot``); ``sync()`` waits for the device (default:
+        ``torch.cuda.synchronize``).  Both exist so that the scheduling can
+        be exercised without a device."""
         self.budget = int(hbm_budget_bytes)
         self.used = 0
         self.sessions = []
         self.rejected = []
+        self.slot_factory = slot_factory or (
+            lambda sess: Slot(sess.grid_n, sess.bbox, sess.frames[0], max(f.n_points for f in sess.frames)))
+        self.sync = sync
 
     def admit(self, sess):
         """Create the session's slot if its device memory fits the budget."""
-        slot = Slot(sess.grid_n, sess.bbox, sess.frames[0], max(f.n_points for f in sess.frames))
+        slot = self.slot_factory(sess)
         need = slot.device_bytes()
         if self.used + need > self.budget:
             slot.close()
@@ -280,7 +287,7 @@ class Server:
         """Serve every admitted session for ``duration_s`` seconds of arrivals
         (Poisson, rate_hz each; ``saturate`` makes every frame available at
         t = 0).  Returns latency and throughput statistics."""
-        torch = _torch()
+        sync = self.sync or _torch().cuda.synchronize
         rng = np.random.default_rng(seed)
         arrivals = []
         for s in self.sessions:
@@ -304,7 +311,7 @@ class Server:
                     s.slot.submit(s.frames[j % len(s.frames)])
                 for s in self.sessions:
                     s.slot.finish()
-        torch.cuda.synchronize()
+        sync()
         lat, done_frames, meshes = [], 0, {}
         nxt = 0
         pending = len(arrivals)
