@@ -14,6 +14,10 @@
  *   marching cubes on A = L -> mesh                       (Sec. III-B, [35])
  *   per-vertex visibility, weights W_k, UVs               (Sec. III-C)
  *
+ * and, around it, the raw reconstruction of depth maps into oriented,
+ * weighted points (Sec. III-A) and the rendering and objective evaluation
+ * of a mesh against sensor views (Sec. III-E, eq. 3-7).
+ *
  * Conventions shared by every entry point
  *   - Pointers marked "host or device" may point to device memory (cudaMalloc,
  *     torch CUDA tensors, managed memory) or to host memory (pinned or
