@@ -1,7 +1,8 @@
-"""Full-size parity: the benchmark's 256^3 human frame, through the same
-whole-frame CUDA-graph call the benchmark times, against the FP64 oracle run
-on the whole frame; and the splat of the 384^3 frame (the split-precision
-study's largest grid) against the oracle's splat.
+"""Full-size parity: the benchmark's 256^3 human frame and the same frame on
+the 384^3 grid (the split-precision study's and the serving sessions'
+largest grid), through the same whole-frame CUDA-graph call the benchmark
+times, against the FP64 oracle run on the whole frame; and the splat of the
+384^3 frame against the oracle's splat.
 
 Bars as in the small-grid parity tests: A relative L2 <= 1e-5, |dL| / (max A
 - min A) <= 1e-5, vertex Hausdorff <= 0.5 voxel, max |V_gpu - V_oracle| <=
@@ -26,9 +27,10 @@ def ftr():
     return F
 
 
-def test_bench_frame_human256_graph_path(ftr):
+@pytest.mark.parametrize("name", ["human256", "human384"])
+def test_bench_frame_graph_path(ftr, name):
     import torch
-    cfg = frame_config("human256")
+    cfg = frame_config(name)
     grid, box = cfg["grid_n"], cfg["bbox"]
     fr = human_frame(seed=1, K=cfg["K"], ring=cfg["ring"], height=cfg["height"])
     dev = torch.device("cuda", 0)

@@ -207,6 +207,44 @@ def test_texture_matches_oracle_on_the_same_mesh(ftr):
     ctx.close()
 
 
+def test_texture_matches_oracle_on_full_size_views(ftr):
+    """The texture stage at the benchmark frame's image sizes (four 512 x 424
+    depth maps, four 1920 x 1080 RGB views, Sec. III-C): the oracle's 128^3
+    mesh of that frame textured by ftr_texture_vertices and by the oracle.
+    Weights bit-equal, UVs within 1e-3 px, colours within 1 LSB."""
+    import torch
+    from datagen import f32_box, frame_config, human_frame
+    from oracle import pipeline
+    from oracle import texture as otex
+    cfg = frame_config("human128")
+    fr = human_frame(seed=1, K=cfg["K"], ring=cfg["ring"], height=cfg["height"])
+    views = fr["views"]
+    assert views[0]["depth"].shape == (424, 512) and views[0]["rgb"].shape == (1080, 1920, 3)
+    ref_mesh = pipeline.reconstruct(fr["points"], fr["normals"], fr["weights"], cfg["grid_n"],
+                                    f32_box(cfg["bbox"]))["mesh"]
+    verts = ref_mesh["vertices"].astype(np.float32)
+    nv, k = len(verts), len(views)
+    dev = torch.device("cuda", 0)
+    dviews = [{key: (torch.from_numpy(np.ascontiguousarray(v[key])).to(dev) if key in ("depth", "conf", "rgb")
+                     else v[key]) for key in v} for v in views]
+    w = torch.zeros((nv, k), dtype=torch.float32, device=dev)
+    uv = torch.zeros((nv, k, 2), dtype=torch.float32, device=dev)
+    rgb = torch.zeros((nv, 3), dtype=torch.uint8, device=dev)
+    tx = torch.zeros((nv,), dtype=torch.uint8, device=dev)
+    ctx = ftr.Context(cfg["grid_n"], cfg["bbox"])
+    tol = float(np.float32(0.03))
+    ftr.ftr_texture_vertices(ctx.h, dviews, tol, torch.from_numpy(verts).to(dev), w, uv, rgb, tx)
+    ctx.close()
+    ref = otex.texture(verts.astype(np.float64), views, tol)
+    assert np.array_equal(w.cpu().numpy(), ref["weights"].astype(np.float32))
+    vis = ref["weights"] > 0
+    assert vis.mean() > 0.3
+    assert np.max(np.abs(uv.cpu().numpy()[vis] - ref["uv"][vis])) <= 1e-3
+    assert np.all(uv.cpu().numpy()[~vis] == -1)
+    assert np.array_equal(tx.cpu().numpy(), ref["textured"])
+    assert np.max(np.abs(rgb.cpu().numpy().astype(int) - ref["rgb"].astype(int))) <= 1
+
+
 def test_async_frame_equals_sync_frame(ftr):
     """Queued frame (extract/texture async, one wait) = the waiting calls."""
     import torch

@@ -48,6 +48,33 @@ def _oracle_raw(views):
     return np.concatenate(P), np.concatenate(N), np.concatenate(W), maps
 
 
+def test_device_points_equal_the_oracle_points(ftr):
+    """Points, normals and W written by the raw reconstruction, one by one
+    against oracle.raw.raw_points on the same depth maps (Sec. III-A): same
+    count and pixel order, positions within 4e-6 m (the kernel works in
+    float32 on coordinates up to ~3 m, whose ulp is 2.4e-7 m: about a dozen
+    roundings), unit normals within 1e-5, W within 1e-5."""
+    import torch
+    fr_views = G.case_inputs("human96")[3]
+    dviews = _device_views(torch, fr_views)
+    ctx = ftr.Context(G.CASES["human96"]["grid"], G.CASES["human96"]["bbox"])
+    ctx.reset()
+    ftr.ftr_splat_depth(ctx.h, dviews)
+    n_in, _ = ctx.stats()
+    pixels = sum(int(v["depth"].numel()) for v in dviews)
+    buf = np.zeros(7 * pixels, np.float32)
+    ftr.ftr_debug_buffer(ctx.h, 2, buf)
+    ctx.close()
+    P, N, W, _ = _oracle_raw(fr_views)
+    assert n_in == len(P) > 1000
+    gp = buf[:3 * pixels].reshape(pixels, 3)[:n_in]
+    gn = buf[3 * pixels:6 * pixels].reshape(pixels, 3)[:n_in]
+    gw = buf[6 * pixels:][:n_in]
+    assert np.abs(gp - P).max() <= 4e-6
+    assert np.abs(gn - N).max() <= 1e-5
+    assert np.abs(gw - W).max() <= 1e-5
+
+
 @pytest.mark.parametrize("name", ["human96", "human128"])
 def test_depth_maps_to_field_and_mesh(ftr, name):
     import torch
