@@ -206,7 +206,10 @@ typedef struct {
  * pixel floor(u + 1/2), floor(v + 1/2) is inside the image and foreground
  * (D > 0), and |D - x_cam.z| <= depth_tol; its weight is W_k at that pixel,
  * set to 0 when the RGB projection falls outside the RGB image.  Projections
- * and the blend are evaluated in float64; the colour is floor(c + 1/2).
+ * run in float32; a decision that falls inside its float32 error guard band
+ * (the pixel choice, the depth test, the RGB bounds) is taken again from that
+ * quantity in float64, so every decision equals the float64 one.  The blend
+ * accumulates in float32; the colour is floor(c + 1/2).
  */
 int ftr_texture(ftr_ctx* ctx, const ftr_view* views, int k, float depth_tol, ftr_tex* out);
 
@@ -273,6 +276,17 @@ int ftr_frame_info(ftr_ctx* ctx, int64_t* info, int n);
  * brick tables, point store, mesh buffers and staging). */
 int64_t ftr_device_bytes(const ftr_ctx* ctx);
 
+/* The device bytes a context on grid_n will hold once it has run frames of
+ * at most `points` oriented points (or `depth_pixels` depth pixels through
+ * ftr_splat_depth*) and meshes of at most `vertices` / `tris`, with device
+ * inputs (no staging), at `precision` (an FTR_PREC_* code): the same
+ * accounting as ftr_device_bytes, applied to the capacities the library's
+ * growth rules give at those sizes.  Allocates nothing and needs no device,
+ * so a server can refuse a session before creating anything for it.
+ * Returns -1 for an unsupported grid or a negative size. */
+int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pixels, int64_t vertices,
+                           int64_t tris, int precision);
+
 /*
  * Tile plans (no counterpart in the paper, which gives no kernel design).
  * The y, z and inverse-y FFT passes each move F lines per CTA, F in
@@ -329,9 +343,13 @@ int ftr_set_indicator(ftr_ctx* ctx, const float* A, double level);
 int ftr_get_inside_mask(ftr_ctx* ctx, uint32_t* out);
 /* Cube class (uint8) per cell, (n_z-1) x (n_y-1) x (n_x-1), of the current A, L. */
 int ftr_get_cube_classes(ftr_ctx* ctx, uint8_t* out);
-/* Raw copy of an internal spectrum buffer after ftr_solve: which = 0 the
+/* Raw copy of an internal buffer (first `bytes` bytes; waits): which = 0 the
  * x-pass / inverse-y buffer (3 x (n_x/2+1) n_y n_z complex64), which = 1 the
- * y-pass / z-pass buffer (2 x (n_x/2+1) n_y n_z complex64). */
+ * y-pass / z-pass buffer (2 x (n_x/2+1) n_y n_z complex64), both after
+ * ftr_solve; which = 2 the output of the last ftr_splat_depth call over P
+ * depth pixels in all: points (3 P float32), normals (3 P) and W (P), each
+ * array's first (point count) entries valid, in pixel order (FTR_ESTATE
+ * before the first such call). */
 int ftr_debug_buffer(ftr_ctx* ctx, int which, void* out, int64_t bytes);
 /* The generated marching-cubes table: ntri[256] and tris[256 * 5 * 3] (-1 padded). */
 int ftr_mc_table(int32_t* ntri, int32_t* tris);
@@ -445,8 +463,13 @@ int ftr_eval_appearance(ftr_ctx* ctx, int w, int h, const float* rendered_depth,
 /* ---- allocation-free variant ------------------------------------------------ */
 
 /*
- * Iso-level L = mean over the accepted points of trilinear A (the same value
- * ftr_solve computes), without any device allocation.  The paper has no
+ * Iso-level L = mean over the accepted points of trilinear A, without any
+ * device allocation.  Every point gets the same accept / reject decision as
+ * in ftr_solve (both follow the float64 quotient (X - b_min) / h - 1/2), and
+ * the value matches ftr_solve's level within |dL| / (max A - min A) <= 1e-5,
+ * but it is not bit-identical: the fractions are rounded from float64 rather
+ * than through the ingest's float pair, and the partial sums are reduced in
+ * a different tree (1024 points per CTA, then one warp).  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory where they need the level -- a per-frame loop with a hard
  * latency budget (cudaMalloc/cudaFree may synchronise the device), or a host
@@ -454,8 +477,10 @@ int ftr_eval_appearance(ftr_ctx* ctx, int w, int h, const float* rendered_depth,
  *
  * A: n_z x n_y x n_x float32 indicator (device); grid_n, bbox as in
  * ftr_create; points: n x 3 float32 (device); level_out: one double, host or
- * device (a host pointer makes the call wait for the stream); stream: the
- * cudaStream_t to use, NULL = the default stream.  Needs no context.
+ * device (a host pointer makes the call wait for the stream, so with a host
+ * level_out on a stream that is being captured the call returns FTR_EINVAL
+ * and enqueues nothing); stream: the cudaStream_t to use, NULL = the default
+ * stream.  Needs no context.
  *
  * Scratch: a static 64 KB device array inside the library (one per device
  * that loads it, kept until the process exits), so n is limited to

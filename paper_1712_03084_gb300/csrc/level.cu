@@ -242,6 +242,13 @@ extern "C" int ftr_iso_level_noalloc(const float* A, const int grid_n[3], const 
     else
         cudaGetLastError();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!out_on_device) {
+        // a host level_out needs a wait for the stream, which a stream under
+        // capture cannot do: refuse before anything is enqueued
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FTR_ECUDA;
+        if (cs != cudaStreamCaptureStatusNone) return FTR_EINVAL;
+    }
     const int nblocks = n > 0 ? (int)((n + kNoAllocPointsPerCta - 1) / kNoAllocPointsPerCta) : 1;
     k_level_noalloc_partial<<<nblocks, kThreads, 0, st>>>(g, points, n, A, scratch);
     if (cudaGetLastError() != cudaSuccess) return FTR_ECUDA;

@@ -9,13 +9,18 @@
 //   ingest  point -> (floor t, t - floor t, W, N); t as a float pair, the
 //           float64 path only within 1e-5 of a decision
 //   count   per point, +1 on every brick its stencil overlaps
-//   scan    one CTA: brick offsets, dense slot per touched brick
+//   scan    256-brick tiles: per-tile sums, then each tile adds the sums
+//           before it and writes brick offsets, a dense slot per touched
+//           brick and the accumulation chunks (no single-CTA scan)
 //   fill    per point, append its index to each overlapped brick's list
-//   accum   one CTA per touched brick: 64 lanes per point evaluate the stencil
-//           nodes inside the brick and add the contributions to shared-memory
-//           fixed-point accumulators (value * 2^40 as 32-bit hi/lo halves,
-//           exact and order-independent, so the result is bit-reproducible);
-//           then V = (sigma2 / sigma1) U / d is written to the brick's slot.
+//   accum   persistent CTAs take work units (up to 1024 (point, brick) pairs
+//           of one touched brick) from a per-frame ticket: 64 lanes per point
+//           evaluate the stencil nodes inside the brick and add the
+//           contributions to shared-memory fixed-point accumulators (value *
+//           2^40 as 32-bit hi/lo halves, exact and order-independent, so the
+//           result is bit-reproducible); a brick of several units adds each
+//           unit's exact sums into an int64 global accumulator and its last
+//           unit writes V = (sigma2 / sigma1) U / d to the brick's slot.
 // The simple variant (nearest node floor(t + 1/2), V = mean N) uses the same
 // bricks with one node per point and d counting points.
 #include <cuda_runtime.h>

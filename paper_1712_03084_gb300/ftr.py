@@ -111,6 +111,8 @@ _SIGNATURES = [
     ("ftr_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
     ("ftr_frame_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("ftr_device_bytes", ctypes.c_int64, [ctypes.c_void_p]),
+    ("ftr_estimate_bytes", ctypes.c_int64, [ctypes.POINTER(ctypes.c_int), ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int]),
     ("ftr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -376,6 +378,15 @@ def ftr_device_bytes(ctx):
     return int(load().ftr_device_bytes(ctx))
 
 
+def ftr_estimate_bytes(grid_n, points, depth_pixels, vertices, tris, precision=FTR_PREC_FP32):
+    """Device bytes of a context at these sizes (allocates nothing)."""
+    g = (ctypes.c_int * 3)(*[int(v) for v in grid_n])
+    b = load().ftr_estimate_bytes(g, int(points), int(depth_pixels), int(vertices), int(tris), int(precision))
+    if b < 0:
+        raise FtrError(-1, "ftr_estimate_bytes: unsupported grid or negative size")
+    return int(b)
+
+
 def ftr_autotune(ctx):
     """Time the tile plans; returns the 3 x 4 microseconds per launch (rows: y,
     z, inverse-y passes; columns: 8, 16, 32 lines per CTA and the bulk-copied
@@ -453,12 +464,42 @@ def ftr_launch_count(ctx):
 
 
 def ftr_iso_level_noalloc(A, grid_n, bbox, points, n=None, level_out=None, stream=None):
-    """Level without device allocation (see include/ftr.h); returns L when level_out is None."""
-    g = (ctypes.c_int * 3)(*[int(v) for v in grid_n])
-    b = (ctypes.c_float * 6)(*[float(v) for v in bbox])
+    """Level without device allocation (see include/ftr.h); returns L when level_out is None.
+
+    The kernel reads ``A`` and ``points`` on the device, so both must be CUDA
+    float32 tensors on one device, ``A`` with n_x n_y n_z elements and
+    ``points`` with at least ``n`` rows of 3; ``level_out`` (optional) is a
+    float64 numpy array or tensor with at least one element.  Anything else
+    raises ValueError before the library is called."""
+    g = [int(v) for v in grid_n]
+    if len(g) != 3 or len(bbox) != 6:
+        raise ValueError("grid_n needs 3 sizes and bbox 6 coordinates")
+    for name, t in (("A", A), ("points", points)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and str(t.dtype) == "torch.float32" and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+    if A.device != points.device:
+        raise ValueError("A and points must be on the same device")
+    if A.numel() != g[0] * g[1] * g[2]:
+        raise ValueError(f"A has {A.numel()} elements, the grid {g[0] * g[1] * g[2]}")
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must be n x 3")
     n = int(points.shape[0]) if n is None else int(n)
-    out = np.zeros(1, np.float64) if level_out is None else level_out
-    code = load().ftr_iso_level_noalloc(_ptr(A, np.float32), g, b, _ptr(points, np.float32), n, _ptr(out), stream)
+    if not 0 <= n <= int(points.shape[0]):
+        raise ValueError(f"n = {n} outside [0, {int(points.shape[0])}]")
+    if level_out is None:
+        out = np.zeros(1, np.float64)
+    else:
+        out = level_out
+        if isinstance(out, np.ndarray):
+            ok = out.dtype == np.float64 and out.size >= 1 and out.flags["C_CONTIGUOUS"]
+        else:
+            ok = (hasattr(out, "data_ptr") and str(out.dtype) == "torch.float64" and out.numel() >= 1
+                  and (not out.is_cuda or out.device == A.device))
+        if not ok:
+            raise ValueError("level_out must hold at least one float64 (host, or on the device of A)")
+    gc = (ctypes.c_int * 3)(*g)
+    b = (ctypes.c_float * 6)(*[float(v) for v in bbox])
+    code = load().ftr_iso_level_noalloc(A.data_ptr(), gc, b, points.data_ptr(), n, _ptr(out), stream)
     if code != FTR_OK:
         raise FtrError(code, "ftr_iso_level_noalloc failed")
     return float(out[0]) if level_out is None else None
