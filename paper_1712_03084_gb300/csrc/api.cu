@@ -1272,27 +1272,87 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     return FTR_OK;
 }
 
+namespace {
+// Capacities that decide a context's device memory besides its grid.
+struct Caps {
+    int64_t pts = 0, stage = 0, tex_stage = 0, entries = 0, units = 0, heavy = 0, raw = 0, raw_tiles = 0;
+    int64_t mc_nodes = 0, verts = 0, tris = 0;
+    bool tc = false;
+};
+
+int64_t context_bytes(const int n[3], const Caps& k) {
+    const int64_t M = (int64_t)n[0] * n[1] * n[2];
+    const int64_t Mh = (int64_t)(n[0] / 2 + 1) * n[1] * n[2];
+    const int64_t nb = (int64_t)(n[0] / kBrick) * (n[1] / kBrick) * (n[2] / kBrick);
+    const int64_t mc_blocks = (int64_t)n[1] * n[2];
+    const int64_t level_blocks = 304;
+    int64_t b = 0;
+    b += k.pts * (int64_t)(sizeof(int4) + 2 * sizeof(float4));
+    b += k.stage + k.tex_stage;
+    b += nb * (int64_t)sizeof(int) * 5 + (nb / kBrickScanTile + 1) * (int64_t)sizeof(int4) + 64;
+    b += k.entries * (int64_t)sizeof(int);
+    b += k.units * (int64_t)sizeof(int);
+    b += k.heavy * (4 * kBrickVox * 8 + 4) + nb * 8;   // heavy-brick accumulators, chunk offsets
+    b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
+    b += 5 * Mh * (int64_t)sizeof(float2) + M * (int64_t)sizeof(float);
+    b += (int64_t)(n[0] + n[1] + n[2]) * (int64_t)sizeof(float2);
+    if (k.tc) b += (int64_t)tc_table_bytes() + 16;
+    b += k.raw * 7 * (int64_t)sizeof(float) + k.raw_tiles * (int64_t)sizeof(int);
+    b += (2 * level_blocks + 8) * (int64_t)sizeof(double);
+    b += (6 * mc_blocks + 16) * (int64_t)sizeof(int);
+    b += mc_blocks * 16 * (int64_t)sizeof(unsigned);   // inside bits (upper bound)
+    b += k.mc_nodes * (int64_t)sizeof(int4) + k.verts * 6 * (int64_t)sizeof(float) +
+         k.tris * 3 * (int64_t)sizeof(int32_t);
+    return b;
+}
+
+int64_t pow2_cap(int64_t need, int64_t first) {
+    int64_t cap = first;
+    while (cap < need) cap *= 2;
+    return cap;
+}
+}  // namespace
+
 int64_t ftr_device_bytes(const ftr_ctx* c) {
     if (!c) return 0;
-    const int64_t nb = c->n_bricks;
-    int64_t b = 0;
-    b += c->pts.cap * (int64_t)(sizeof(int4) + 2 * sizeof(float4));
-    b += (int64_t)c->stage_cap + (int64_t)c->tex_stage_cap;
-    b += nb * (int64_t)sizeof(int) * 5 + (nb / kBrickScanTile + 1) * (int64_t)sizeof(int4) + 64;
-    b += c->cap_entries * (int64_t)sizeof(int);
-    b += c->cap_units * (int64_t)sizeof(int);
-    b += c->cap_heavy * (4 * kBrickVox * 8 + 4) + nb * 8;   // heavy-brick accumulators, chunk offsets
-    b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
-    b += 5 * c->Mh * (int64_t)sizeof(float2) + c->M * (int64_t)sizeof(float);
-    b += (int64_t)(c->g.n[0] + c->g.n[1] + c->g.n[2]) * (int64_t)sizeof(float2);
-    if (c->d_tc_table) b += (int64_t)tc_table_bytes() + 16;
-    b += c->raw_cap * 7 * (int64_t)sizeof(float) + c->raw_tiles_cap * (int64_t)sizeof(int);
-    b += (2 * c->level_blocks + 8) * (int64_t)sizeof(double);
-    b += (6 * (int64_t)c->mc_blocks + 16) * (int64_t)sizeof(int);
-    b += (int64_t)c->mc_blocks * 16 * (int64_t)sizeof(unsigned);   // inside bits (upper bound)
-    b += c->cap_mc_nodes * (int64_t)sizeof(int4) + c->cap_verts * 6 * (int64_t)sizeof(float) +
-         c->cap_tris * 3 * (int64_t)sizeof(int32_t);
-    return b;
+    Caps k;
+    k.pts = c->pts.cap;
+    k.stage = (int64_t)c->stage_cap;
+    k.tex_stage = (int64_t)c->tex_stage_cap;
+    k.entries = c->cap_entries;
+    k.units = c->cap_units;
+    k.heavy = c->cap_heavy;
+    k.raw = c->raw_cap;
+    k.raw_tiles = c->raw_tiles_cap;
+    k.mc_nodes = c->cap_mc_nodes;
+    k.verts = c->cap_verts;
+    k.tris = c->cap_tris;
+    k.tc = c->d_tc_table != nullptr;
+    return context_bytes(c->g.n, k);
+}
+
+int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pixels, int64_t vertices,
+                           int64_t tris, int precision) {
+    if (!grid_n || points < 0 || depth_pixels < 0 || vertices < 0 || tris < 0) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (!supported_n(grid_n[a])) return -1;
+    Caps k;
+    // the growth rules of the point store, the (point, brick) pairs and the
+    // accumulation chunks, at these sizes; device inputs need no staging
+    const int64_t pts = points > depth_pixels ? points : depth_pixels;
+    k.pts = pts > 0 ? pow2_cap(pts, 1 << 16) : 0;
+    k.entries = pow2_cap(8 * pts + 1, 1 << 18);
+    const int64_t nb = (int64_t)(grid_n[0] / kBrick) * (grid_n[1] / kBrick) * (grid_n[2] / kBrick);
+    k.units = nb + k.entries / kSplatChunk + 2;
+    k.heavy = k.entries / kSplatChunk + 1;
+    k.raw = depth_pixels;
+    k.raw_tiles = depth_pixels > 0 ? depth_pixels / 128 + 16 * 1024 : 0;
+    // mesh buffers grow to 1.5 x what a frame needs (+1024); active nodes <= vertices
+    k.mc_nodes = vertices + vertices / 2 + 1024;
+    k.verts = vertices + vertices / 2 + 1024;
+    k.tris = tris + tris / 2 + 1024;
+    k.tc = precision != FTR_PREC_FP32;
+    return context_bytes(grid_n, k);
 }
 
 const char* ftr_last_error(const ftr_ctx* c) {
@@ -1431,8 +1491,10 @@ int ftr_debug_buffer(ftr_ctx* c, int which, void* out, int64_t bytes) {
     switch (which) {
         case 0: src = c->d_s0; have = (int64_t)sizeof(float2) * 3 * c->Mh; break;
         case 1: src = c->d_s1; have = (int64_t)sizeof(float2) * 2 * c->Mh; break;
+        case 2: src = c->d_raw; have = (int64_t)sizeof(float) * 7 * c->raw_cap; break;
         default: return set_err(c, FTR_EINVAL, "ftr_debug_buffer: unknown buffer %d", which);
     }
+    if (!src) return set_err(c, FTR_ESTATE, "ftr_debug_buffer: buffer %d does not exist yet", which);
     if (bytes > have) return set_err(c, FTR_EINVAL, "ftr_debug_buffer: %lld > %lld bytes", (long long)bytes,
                                      (long long)have);
     cudaError_t e = cudaMemcpyAsync(out, src, (size_t)bytes, cudaMemcpyDefault, c->stream);
