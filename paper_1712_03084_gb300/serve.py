@@ -203,14 +203,24 @@ class Slot:
         ftr.ftr_mesh_copy(self.ctx.h, v, None, t)
         return v, t
 
+    def results(self):
+        """The last finished frame's mesh and texture data as host arrays:
+        dict(vertices, tris, weights, uv, rgb, textured)."""
+        v, t = self.mesh()
+        nv = len(v)
+        return {"vertices": v, "tris": t, "weights": self.out_w[:nv].cpu().numpy(),
+                "uv": self.out_uv[:nv].cpu().numpy(), "rgb": self.out_rgb[:nv].cpu().numpy(),
+                "textured": self.out_tex[:nv].cpu().numpy()}
+
     def close(self):
         self.ctx.close()
 
 
-def run_batch(frames, grids, bboxes, sequential=False, rounds=3):
+def run_batch(frames, grids, bboxes, sequential=False, rounds=3, results=False):
     """Reconstruct ``frames`` (FrameInput list) on one slot each, all queued at
     once (or one after another), ``rounds`` times; returns (median seconds per
-    round, [(n_vertices, n_tris)])."""
+    round, [(n_vertices, n_tris)]), or with ``results`` (median seconds, per
+    frame ``Slot.results()`` of the last round: mesh and texture data)."""
     torch = _torch()
     slots = [Slot(g, b, f, f.n_points) for f, g, b in zip(frames, grids, bboxes)]
     # warm-up, twice: the first round sizes every slot's buffers (growing them
@@ -237,6 +247,8 @@ def run_batch(frames, grids, bboxes, sequential=False, rounds=3):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     gc.enable()
+    if results:
+        out = [s.results() for s in slots]
     for s in slots:
         s.close()
     return float(np.median(times)), out
@@ -244,7 +256,12 @@ def run_batch(frames, grids, bboxes, sequential=False, rounds=3):
 
 @dataclass
 class Session:
-    """A live capture rig: grid, bbox and a cycle of frames (continuous motion)."""
+    """A live capture rig: grid, bbox and a cycle of frames (continuous motion).
+
+    ``start_s`` / ``stop_s``: when the session joins and leaves the serving
+    loop (seconds after its start; ``stop_s`` None = until the end);
+    ``n_slots``: resident slots of the session, so that up to that many of
+    its frames can be on the device at once."""
     sid: int
     grid_n: tuple
     bbox: tuple
@@ -252,99 +269,203 @@ class Session:
     rate_hz: float = 30.0
     slot: object = None
     queue: list = field(default_factory=list)
+    start_s: float = 0.0
+    stop_s: object = None
+    n_slots: int = 1
+    slots: list = field(default_factory=list)
+    nbytes: int = 0
+
+
+def slot_estimate_bytes(sess):
+    """Device bytes a session's slots will hold, from its grid, frames and
+    cameras alone (nothing is allocated): the library's estimate of a
+    context at the largest frame's point count and the mesh capacity, plus
+    the slot's staging and texture outputs."""
+    nx, ny, nz = sess.grid_n
+    pts = max(int(f.n_points) for f in sess.frames)
+    t = sess.frames[0]
+    pixels = sum(int(v["depth"].numel()) for v in t.views)
+    rgb = sum(int(v["rgb"].numel()) for v in t.views)
+    cap = max(1 << 16, (nx * ny * nz) // 64)
+    K = len(t.views)
+    ctx = ftr.ftr_estimate_bytes(sess.grid_n, pts, pixels if t.rgbd else 0, cap, 2 * cap)
+    staged = 28 * max(1, pts) + 8 * pixels + rgb + cap * (12 * K + 4)
+    return sess.n_slots * (ctx + staged)
 
 
 class Server:
-    """Continuous-batching request loop over resident per-session slots."""
+    """Continuous-batching request loop over resident per-session slots.
 
-    def __init__(self, hbm_budget_bytes, slot_factory=None, sync=None):
-        """``slot_factory(session)`` makes a session's slot (default: a
-        resident ``Slot``); ``sync()`` waits for the device (default:
-        ``torch.cuda.synchronize``).  Both exist so that the scheduling can
-        be exercised without a device."""
+    Sessions join and leave while the loop runs: a session is admitted when
+    its device memory fits the HBM budget (checked on an estimate before
+    anything is allocated, then on the slots' real size after they have run
+    each of the session's frames once); one that does not fit waits and is
+    admitted when a departing session has freed enough.  A frame is
+    dispatched as soon as one of its session's slots is free, so frames that
+    arrive while others are on the GPU join the work in flight."""
+
+    def __init__(self, hbm_budget_bytes, slot_factory=None, sync=None, estimate=None):
+        """``slot_factory(session)`` makes one of a session's slots (default:
+        a resident ``Slot``); ``estimate(session)`` its bytes before any
+        allocation (default ``slot_estimate_bytes``); ``sync()`` waits for
+        the device (default ``torch.cuda.synchronize``).  They exist so that
+        the scheduling can be exercised without a device."""
         self.budget = int(hbm_budget_bytes)
         self.used = 0
         self.sessions = []
         self.rejected = []
+        self.waiting = []
+        self.events = []
         self.slot_factory = slot_factory or (
             lambda sess: Slot(sess.grid_n, sess.bbox, sess.frames[0], max(f.n_points for f in sess.frames)))
+        self.estimate = estimate or slot_estimate_bytes
         self.sync = sync
 
     def admit(self, sess):
-        """Create the session's slot if its device memory fits the budget."""
-        slot = self.slot_factory(sess)
-        need = slot.device_bytes()
+        """Make the session's slots if they fit the budget; False if not."""
+        if self.used + self.estimate(sess) > self.budget:
+            self.rejected.append(sess.sid)
+            return False
+        slots = [self.slot_factory(sess) for _ in range(max(1, sess.n_slots))]
+        # every frame once per slot: the buffers reach their final size (and
+        # the frame graphs are captured) before the memory is counted
+        for sl in slots:
+            for f in sess.frames:
+                sl.submit(f)
+                sl.finish()
+        need = sum(sl.device_bytes() for sl in slots)
         if self.used + need > self.budget:
-            slot.close()
+            for sl in slots:
+                sl.close()
             self.rejected.append(sess.sid)
             return False
         self.used += need
-        sess.slot = slot
+        sess.nbytes = need
+        sess.slots = slots
+        sess.slot = slots[0]
         self.sessions.append(sess)
         return True
 
-    def run(self, duration_s, seed=0, saturate=False, keep_meshes=None):
-        """Serve every admitted session for ``duration_s`` seconds of arrivals
-        (Poisson, rate_hz each; ``saturate`` makes every frame available at
-        t = 0).  Returns latency and throughput statistics."""
+    def _depart(self, sess):
+        for sl in sess.slots:
+            sl.close()
+        self.used -= sess.nbytes
+        sess.nbytes = 0
+        sess.slots = []
+        sess.slot = None
+        self.sessions.remove(sess)
+
+    def run(self, duration_s, seed=0, saturate=False, keep_meshes=None, late=()):
+        """Serve the admitted sessions, and the ``late`` ones from their
+        ``start_s``, for ``duration_s`` seconds of arrivals (Poisson, rate_hz
+        each, within [start_s, stop_s); ``saturate`` makes every frame of the
+        admitted sessions available at t = 0).  Returns latency and
+        throughput statistics, overall and per grid size."""
         sync = self.sync or _torch().cuda.synchronize
         rng = np.random.default_rng(seed)
+        everyone = list(self.sessions) + [s for s in late if s not in self.sessions]
         arrivals = []
-        for s in self.sessions:
-            t = 0.0
+        for s in everyone:
+            t = 0.0 if saturate else float(s.start_s)
+            end = duration_s if s.stop_s is None else min(duration_s, float(s.stop_s))
             k = 0
             while True:
                 t += 0.0 if saturate else rng.exponential(1.0 / s.rate_hz)
-                if (not saturate and t > duration_s) or (saturate and k >= int(duration_s * s.rate_hz)):
+                if (not saturate and t > end) or (saturate and k >= int(duration_s * s.rate_hz)):
                     break
                 arrivals.append((t, s.sid, k))
                 k += 1
         arrivals.sort()
-        by_id = {s.sid: s for s in self.sessions}
-        # warm-up: every frame of every session, twice: the first pass sizes
-        # each slot's buffers (growing them frees memory, which waits for the
-        # whole device, and invalidates the slot's graph), the second captures
-        # the final graphs before arrivals start
+        by_id = {s.sid: s for s in everyone}
+        # warm-up of the admitted sessions: every frame on every slot, twice
+        # (the first pass sizes the buffers, which frees memory and waits for
+        # the whole device, and invalidates the frame graphs; the second
+        # captures the final graphs before arrivals start)
         for _ in range(2):
-            for j in range(max(len(s.frames) for s in self.sessions)):
-                for s in self.sessions:
-                    s.slot.submit(s.frames[j % len(s.frames)])
-                for s in self.sessions:
-                    s.slot.finish()
+            for s in self.sessions:
+                for sl in s.slots:
+                    for f in s.frames:
+                        sl.submit(f)
+                        sl.finish()
         sync()
-        lat, done_frames, meshes = [], 0, {}
+        pending_join = sorted((s for s in everyone if s not in self.sessions), key=lambda s: s.start_s)
+        self.events = []
+        lat, qwait, grid_of, done_frames, meshes = [], [], [], 0, {}
+        dropped = 0
         nxt = 0
         pending = len(arrivals)
         gc.disable()                  # no collector pauses inside the loop
         t0 = time.perf_counter()
         while pending:
             now = time.perf_counter() - t0
+            # joins: admitted now if the budget allows, else they wait for a departure
+            while pending_join and pending_join[0].start_s <= now:
+                s = pending_join.pop(0)
+                ta = time.perf_counter()
+                ok = self.admit(s)
+                self.events.append(("join", s.sid, round(now, 4), ok, round(1e3 * (time.perf_counter() - ta), 2)))
+                if not ok:
+                    self.waiting.append(s)
             while nxt < len(arrivals) and arrivals[nxt][0] <= now:
                 ta, sid, k = arrivals[nxt]
                 by_id[sid].queue.append((ta, k))
                 nxt += 1
-            for s in self.sessions:
-                sl = s.slot
-                if sl.busy and sl.ready():
-                    nv, nt = sl.finish()
-                    ta, k = sl.tag
-                    lat.append(time.perf_counter() - t0 - ta)
-                    done_frames += 1
-                    pending -= 1
-                    if keep_meshes is not None and (s.sid, k) in keep_meshes:
-                        meshes[(s.sid, k)] = sl.mesh()
-                if not sl.busy and s.queue:
-                    ta, k = s.queue.pop(0)
-                    sl.submit(s.frames[k % len(s.frames)], tag=(ta, k))
+            for s in list(self.sessions):
+                for sl in s.slots:
+                    if sl.busy and sl.ready():
+                        nv, nt = sl.finish()
+                        ta, td, k = sl.tag
+                        t_end = time.perf_counter() - t0
+                        lat.append(t_end - ta)
+                        qwait.append(td - ta)
+                        grid_of.append(s.grid_n[0])
+                        done_frames += 1
+                        pending -= 1
+                        if keep_meshes is not None and (s.sid, k) in keep_meshes:
+                            meshes[(s.sid, k)] = sl.mesh()
+                    if not sl.busy and s.queue:
+                        ta, k = s.queue.pop(0)
+                        sl.submit(s.frames[k % len(s.frames)], tag=(ta, time.perf_counter() - t0, k))
+                # departure: past stop_s with nothing queued or in flight
+                if (s.stop_s is not None and now >= s.stop_s and not s.queue
+                        and not any(sl.busy for sl in s.slots)):
+                    self._depart(s)
+                    self.events.append(("leave", s.sid, round(now, 4)))
+                    for w in list(self.waiting):
+                        if self.admit(w):
+                            self.waiting.remove(w)
+                            self.events.append(("join", w.sid, round(time.perf_counter() - t0, 4), True, None))
+            # frames of sessions that never got in are not served
+            for w in self.waiting:
+                dropped += len(w.queue)
+                pending -= len(w.queue)
+                w.queue.clear()
         wall = time.perf_counter() - t0
         gc.enable()
         lat_ms = np.array(lat) * 1e3
+        q_ms = np.array(qwait) * 1e3
+        grids = np.array(grid_of)
+
+        def pct(a, q):
+            return float(np.percentile(a, q)) if len(a) else float("nan")
+        per_grid = {}
+        for g in sorted(set(grid_of)):
+            m = grids == g
+            per_grid[int(g)] = {"frames": int(m.sum()), "p50_ms": pct(lat_ms[m], 50), "p99_ms": pct(lat_ms[m], 99),
+                                "max_ms": float(lat_ms[m].max())}
         return {"frames": done_frames, "seconds": wall, "frames_per_s": done_frames / wall,
-                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-                "mean_ms": float(lat_ms.mean()), "sessions": len(self.sessions), "rejected": list(self.rejected),
+                "p50_ms": pct(lat_ms, 50), "p99_ms": pct(lat_ms, 99),
+                "max_ms": float(lat_ms.max()) if len(lat_ms) else float("nan"),
+                "mean_ms": float(lat_ms.mean()) if len(lat_ms) else float("nan"),
+                "queue_p99_ms": pct(q_ms, 99), "per_grid": per_grid,
+                "sessions": len(self.sessions), "rejected": list(self.rejected),
+                "not_served": dropped, "events": list(self.events),
                 "hbm_bytes": self.used, "meshes": meshes}
 
     def close(self):
         for s in self.sessions:
-            s.slot.close()
+            for sl in s.slots:
+                sl.close()
+            s.slots = []
+            s.slot = None
         self.sessions = []

@@ -74,3 +74,21 @@ def test_product_path_does_not_touch_the_oracle():
                 with open(os.path.join(dirpath, f)) as fh:
                     src = fh.read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", src).replace("the oracle", ""), f
+
+
+def test_estimate_bytes_needs_no_device(lib):
+    """ftr_estimate_bytes is host arithmetic: the grid terms dominate (the
+    spectra, the indicator and the brick pool, about 37 bytes per voxel), it
+    grows with points and mesh size, and bad arguments give -1."""
+    from paper_1712_03084_gb300 import ftr
+    e0 = ftr.ftr_estimate_bytes((256, 256, 256), 0, 0, 0, 0)
+    assert 30 * 256 ** 3 < e0 < 45 * 256 ** 3
+    e1 = ftr.ftr_estimate_bytes((256, 256, 256), 200000, 0, 100000, 200000)
+    e2 = ftr.ftr_estimate_bytes((256, 256, 256), 400000, 0, 100000, 200000)
+    assert e0 < e1 < e2
+    assert ftr.ftr_estimate_bytes((256, 256, 256), 0, 0, 0, 0, ftr.FTR_PREC_BF16X3) > e0
+    assert ftr.ftr_estimate_bytes((384, 384, 384), 0, 0, 0, 0) > 3 * e0
+    with pytest.raises(ftr.FtrError):
+        ftr.ftr_estimate_bytes((100, 256, 256), 0, 0, 0, 0)
+    with pytest.raises(ftr.FtrError):
+        ftr.ftr_estimate_bytes((256, 256, 256), -1, 0, 0, 0)

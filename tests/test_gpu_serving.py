@@ -31,19 +31,29 @@ def _frames(seed, n, K=3):
     return out
 
 
+def _same(a, b):
+    return a.keys() == b.keys() and all(np.array_equal(a[k], b[k]) for k in a)
+
+
 def test_batch_matches_sequential_and_alone(rt):
+    """Vertices, triangles and every texture output of each frame are
+    bit-identical whether the batch runs all at once, one frame after another,
+    or the frame runs alone on a fresh slot."""
     grids = [(64, 64, 64), (96, 96, 96), (64, 128, 64), (96, 96, 96)]
     frs = _frames(50, 4)
     fins = [rt.FrameInput.from_frame(f) for f in frs]
     boxes = [BOX] * 4
-    _, par = rt.run_batch(fins, grids, boxes)
-    _, seq = rt.run_batch(fins, grids, boxes, sequential=True)
-    assert par == seq
-    # alone: one slot, one frame
-    s = rt.Slot(grids[1], BOX, fins[1], fins[1].n_points)
-    s.submit(fins[1])
-    assert s.finish() == par[1]
-    s.close()
+    _, par = rt.run_batch(fins, grids, boxes, results=True)
+    _, seq = rt.run_batch(fins, grids, boxes, sequential=True, results=True)
+    for a, b in zip(par, seq):
+        assert len(a["vertices"]) > 1000 and _same(a, b)
+    for i in range(4):
+        s = rt.Slot(grids[i], BOX, fins[i], fins[i].n_points)
+        s.submit(fins[i])
+        s.finish()
+        alone = s.results()
+        s.close()
+        assert _same(alone, par[i]), i
 
 
 def test_server_mix_equals_alone_and_reports_latency(rt):
@@ -68,6 +78,21 @@ def test_server_mix_equals_alone_and_reports_latency(rt):
         alone.close()
         assert np.array_equal(v, va) and np.array_equal(t, ta)
     assert len(stats["meshes"]) >= 2
+
+
+def test_estimate_bounds_the_slot_after_its_frames(rt):
+    """The admission estimate (no allocation) is at least what a slot holds
+    after running every frame of its session, and not far above it."""
+    fins = [rt.FrameInput.from_frame(f) for f in _frames(95, 2, K=4)]
+    sess = rt.Session(0, (96, 96, 96), BOX, fins)
+    est = rt.slot_estimate_bytes(sess)
+    s = rt.Slot(sess.grid_n, BOX, fins[0], max(f.n_points for f in fins))
+    for f in fins:
+        s.submit(f)
+        s.finish()
+    real = s.device_bytes()
+    s.close()
+    assert real <= est <= 3 * real
 
 
 def test_admission_respects_the_hbm_budget(rt):
