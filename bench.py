@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision configuration")
     ap.add_argument("--plan", default=None,
                     help="lines per CTA of the y, z, inverse-y passes, e.g. 16,8,16 (default: autotune)")
+    ap.add_argument("--path", type=int, choices=[0, 1], default=None,
+                    help="transform path: 0 five axis passes, 1 plane-fused (default: autotuned)")
     ap.add_argument("--no-oracle-error", action="store_true",
                     help="skip the FP64 oracle frames (error of the timed frame and of the precision variants)")
     return ap.parse_args()
@@ -479,12 +481,14 @@ def run_ours(args, rank, world, local_rank):
 
     ensure_out(GRID ** 3 // 64)
 
+    sets = [(P[s:s + n], N[s:s + n], W[s:s + n]) for (s, n) in cams]
+
     def step():
         # the whole frame is queued before any host wait (ftr_frame_finish):
-        # the 4 per-camera ingests, then solve + mesh + texture as one CUDA graph
+        # one ingest of the 4 cameras' points, then solve + mesh + texture as
+        # one CUDA graph
         ctx.reset()
-        for (s, n) in cams:
-            ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+        ctx.splat_sets(sets)
         ftr.ftr_frame_launch(ctx.h, dviews, tol, outs["w"], outs["uv"], outs["rgb"], outs["tex"], cap[0])
 
     def finish():
@@ -508,10 +512,14 @@ def run_ours(args, rank, world, local_rank):
     # slab (cached per grid for the process), then the warm-up proper
     if args.plan:
         ctx.set_plan(tuple(int(v) for v in args.plan.split(",")))
-        tune_us = np.zeros((3, 4))
+        tune_us, chain_us = np.zeros((3, 4)), (0.0, 0.0)
     else:
         tune_us = ctx.autotune()
+        chain_us = (ctx.tune_report[12], ctx.tune_report[13])
+    if args.path is not None:
+        ctx.set_transform_path(args.path)
     plan = ctx.plan()
+    path = ctx.transform_path()
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             step()
@@ -546,8 +554,7 @@ def run_ours(args, rank, world, local_rank):
     # (events recorded on the context stream around every stage)
     def step_launched():
         ctx.reset()
-        for (s, n) in cams:
-            ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+        ctx.splat_sets(sets)
         ctx.solve(want_level=False)
         ftr.ftr_extract_mesh_async(ctx.h)
         ftr.ftr_texture_async(ctx.h, dviews, tol, outs["w"], outs["uv"], outs["rgb"], outs["tex"], cap[0])
@@ -670,7 +677,10 @@ def run_ours(args, rank, world, local_rank):
                    "grid": list(grid), "points": int(info["points_in"]), "vertices": int(info["n_vertices"]),
                    "triangles": int(info["n_tris"]), "cameras": K, "parallelism": f"replicas{world}",
                    "plan": {"lines_per_cta_y_z_iy": list(plan),
-                            "autotune_us_per_launch": [[round(float(v), 2) for v in row] for row in tune_us]},
+                            "transform_path": "plane-fused" if path == 1 else "five axis passes",
+                            "autotune_us_per_launch": [[round(float(v), 2) for v in row] for row in tune_us],
+                            "autotune_chain_us": {"five_pass": round(float(chain_us[0]), 2),
+                                                  "plane_fused": round(float(chain_us[1]), 2)}},
                    "l2": "flushed between steps (256 MiB write, untimed)"},
         "latency_ms": {"p50": round(float(np.percentile(step_ms_sorted, 50)), 4),
                        "p99": round(float(np.percentile(step_ms_sorted, 99)), 4)},
@@ -784,20 +794,63 @@ def run_multi(args, rank, dev, plain_frame=None):
                       f"memory per frame; saturated = every frame available at once; live = Poisson arrivals "
                       f"offered at {', '.join(str(int(100 * f)) for f in SWEEP_LOAD)} % of the saturated rate for "
                       f"{SWEEP_SECONDS} s each; latency = completion - arrival (host clock)"}
+    def summary(r):
+        return {"frames": r["frames"], "frames_per_s": round(r["frames_per_s"], 1),
+                "p50_ms": round(r["p50_ms"], 3), "p99_ms": round(r["p99_ms"], 3), "max_ms": round(r["max_ms"], 3),
+                "queue_p99_ms": round(r["queue_p99_ms"], 3),
+                "per_grid": {g: {k: round(v, 3) if isinstance(v, float) else v for k, v in d.items()}
+                             for g, d in r["per_grid"].items()}}
     srv = serve.Server(hbm_budget_bytes=120 * (1 << 30))
     admitted = [srv.admit(s) for s in sessions]
     live = srv.run(duration_s=2.0, seed=7 + rank)
     sat = srv.run(duration_s=3.0, seed=8 + rank, saturate=True)
+    used = srv.used
     srv.close()
-    out["served"] = {"sessions": len(sessions), "admitted": int(sum(admitted)), "hbm_gb": round(srv.used / 2 ** 30, 2),
+    # size-aware: the 384^3 sessions get two resident slots, so that one of
+    # their frames can start while the previous one is still on the device
+    for x in sessions:
+        x.n_slots = 2 if x.grid_n[0] >= 384 else 1
+    srv = serve.Server(hbm_budget_bytes=120 * (1 << 30))
+    for x in sessions:
+        srv.admit(x)
+    live2 = srv.run(duration_s=2.0, seed=7 + rank)
+    used2 = srv.used
+    srv.close()
+    for x in sessions:
+        x.n_slots = 1
+    out["served"] = {"sessions": len(sessions), "admitted": int(sum(admitted)), "hbm_gb": round(used / 2 ** 30, 2),
                      "grids": [s.grid_n[0] for s in sessions], "cameras": [len(s.frames[0].views) for s in sessions],
-                     "live": {"frames": live["frames"], "frames_per_s": round(live["frames_per_s"], 1),
-                              "p50_ms": round(live["p50_ms"], 3), "p99_ms": round(live["p99_ms"], 3)},
-                     "saturated": {"frames": sat["frames"], "frames_per_s": round(sat["frames_per_s"], 1),
-                                   "p50_ms": round(sat["p50_ms"], 3), "p99_ms": round(sat["p99_ms"], 3)},
+                     "live": summary(live), "saturated": summary(sat),
+                     "live_two_slots_for_384": dict(summary(live2), hbm_gb=round(used2 / 2 ** 30, 2)),
                      "config": "8 sessions, 30 fps Poisson arrivals each, 3-6 cameras, grids {128,256,384}^3, "
                                "texturing on, 120 GB HBM admission budget; latency = completion - arrival (host "
-                               "clock), inputs copied from pinned host memory per frame"}
+                               "clock), inputs copied from pinned host memory per frame; per_grid: latency by "
+                               "session grid; live_two_slots_for_384: the same arrivals with two resident slots per "
+                               "384^3 session"}
+    # continuous admission: a budget for six sessions; sessions 0 and 1 leave
+    # at 1 s, sessions 6 and 7 ask to join at 0.5 s and get in when the memory
+    # of a departed session is free again
+    est = [serve.slot_estimate_bytes(x) for x in sessions]
+    for x in sessions:
+        x.start_s, x.stop_s = 0.0, None
+    for i in (0, 1):
+        sessions[i].stop_s = 1.0
+    for i in (6, 7):
+        sessions[i].start_s = 0.5
+    srv = serve.Server(hbm_budget_bytes=120 * (1 << 30))
+    first = [srv.admit(x) for x in sessions[:6]]
+    # the budget: what the six hold, plus half a late session (not enough for one)
+    srv.budget = budget = srv.used + min(est[6], est[7]) // 2
+    churn = srv.run(duration_s=2.0, seed=11 + rank, late=sessions[6:])
+    srv.close()
+    for x in sessions:
+        x.start_s, x.stop_s = 0.0, None
+    out["served_churn"] = dict(summary(churn), budget_gb=round(budget / 2 ** 30, 2), admitted_first=int(sum(first)),
+                               events=[list(e) for e in churn["events"]], not_served=churn["not_served"],
+                               config="the 8 sessions above under a budget of six: sessions 0 and 1 leave at 1 s, "
+                                      "6 and 7 ask to join at 0.5 s (refused while the budget is full, admitted "
+                                      "when a departure frees it; their frames that arrive while they wait are not "
+                                      "served); events = (kind, session, t s, admitted, admission ms)")
     # the same sessions fed as RGB-D images: the raw reconstruction runs on the device
     srv = serve.Server(hbm_budget_bytes=120 * (1 << 30))
     for s in rgbd_sessions:
@@ -863,8 +916,7 @@ def run_precision(args, rank, dev, fr256, oracle=None):
 
             def frame():
                 ctx.reset()
-                for (s, n) in cams:
-                    ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+                ctx.splat_sets([(P[s:s + n], N[s:s + n], W[s:s + n]) for (s, n) in cams])
                 ftr.ftr_frame_launch(ctx.h, dviews, tol, *outs, cap)
 
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -886,8 +938,7 @@ def run_precision(args, rank, dev, fr256, oracle=None):
                 for i in range(steps):
                     flush.fill_(float(i))
                     ctx.reset()
-                    for (s, n) in cams:
-                        ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+                    ctx.splat_sets([(P[s:s + n], N[s:s + n], W[s:s + n]) for (s, n) in cams])
                     ctx.solve(want_level=False)
             torch.cuda.synchronize()
             prof = ctx.profile_read()
@@ -1026,8 +1077,7 @@ def run_table1(args, rank, dev, fr, flush):
 
             def frame():
                 ctx.reset()
-                for (s, n) in cams:
-                    ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+                ctx.splat_sets([(P[s:s + n], N[s:s + n], W[s:s + n]) for (s, n) in cams])
                 ftr.ftr_frame_launch(ctx.h, [], 0.0)
 
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -1101,8 +1151,8 @@ def run_poses(args, rank, dev, flush):
     def frame(i):
         d = poses[i % POSES]
         ctx.reset()
-        for (s0, n0) in d["cams"]:
-            ctx.splat(d["points"][s0:s0 + n0], d["normals"][s0:s0 + n0], d["weights"][s0:s0 + n0])
+        ctx.splat_sets([(d["points"][s0:s0 + n0], d["normals"][s0:s0 + n0], d["weights"][s0:s0 + n0])
+                        for (s0, n0) in d["cams"]])
         ftr.ftr_frame_launch(ctx.h, fixed, tol, *outs, cap)
 
     verts = []
@@ -1393,8 +1443,7 @@ def run_e2e_sync(args, ctx, fr, cams, tol, K, flush, stream, world, dev):
 
     def step():
         ctx.reset()
-        for (s, n) in cams:
-            ctx.splat(P[s:s + n], N[s:s + n], W[s:s + n])
+        ctx.splat_sets([(P[s:s + n], N[s:s + n], W[s:s + n]) for (s, n) in cams])
         ctx.solve(want_level=False)
         m = ctx.extract_mesh()
         if m.n_vertices > cap or m.n_tris > 2 * cap:

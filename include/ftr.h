@@ -108,6 +108,23 @@ int ftr_reset(ftr_ctx* ctx);
  */
 int ftr_splat(ftr_ctx* ctx, const float* points, const float* normals, const float* weights, int64_t n);
 
+typedef struct {
+    const float* points;   /* n x 3 float32, device */
+    const float* normals;  /* n x 3 float32, device */
+    const float* weights;  /* n float32, device, or NULL for W = 1 */
+    int64_t n;
+} ftr_point_set;
+
+/*
+ * The same as k calls of ftr_splat, one per set (e.g. one per camera), in
+ * one kernel launch: the sets' points are appended in set order, exactly as
+ * the separate calls would store them.  Every pointer must be device memory
+ * (FTR_EINVAL otherwise, before anything is enqueued); 1 <= k <= 16.  The
+ * sets are read before the call returns to the stream order (the caller may
+ * reuse them after the stream has passed this point).
+ */
+int ftr_splat_sets(ftr_ctx* ctx, const ftr_point_set* sets, int k);
+
 /*
  * Run the reconstruction of Sec. III-B on the points added since the last
  * ftr_reset: splat eq.(1)(2) (or the simple nearest-node splat), forward 3D
@@ -303,10 +320,16 @@ int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pi
  * divide the grid and leave at least two CTAs resident per SM (one CTA that
  * fills an SM stalls when other contexts' frames run concurrently).  The
  * choice is cached per device and grid for the process: later contexts of
- * the same grid take it without timing.  report (nullable): 12 floats,
- * microseconds per launch of F = 8, 16, 32, -16 for the y, z and inverse-y
- * passes (0 = not timed: cached or not a candidate).  Waits for the stream.
- * Split precision contexts keep F = 16 (their passes have no variants).
+ * the same grid take it without timing.  Then it times the whole forward
+ * filter inverse transform chain of both transform paths (see
+ * ftr_set_transform_path), each at its best tile heights, and keeps the
+ * faster path (cached with the plan).  report (nullable): 16 floats,
+ * [0..11] microseconds per launch of F = 8, 16, 32, -16 for the y, z and
+ * inverse-y passes of the five-pass path (0 = not timed: cached or not a
+ * candidate), [12] and [13] microseconds of the five-pass and of the
+ * plane-fused chain (0: not timed), [14] the path kept.  Waits for the
+ * stream.  Split precision contexts keep F = 16 and the five passes (their
+ * passes have no variants).
  */
 int ftr_autotune(ftr_ctx* ctx, float* report);
 
@@ -317,6 +340,30 @@ int ftr_get_plan(const ftr_ctx* ctx, int* plan);
  * tiles (n_z for the y passes, n_y for the z pass), or -16 for the y pass
  * when 16 divides n_z and n_y <= 256; else FTR_EINVAL. */
 int ftr_set_plan(ftr_ctx* ctx, const int* plan);
+
+/*
+ * Transform path of the FP32 transforms: 1 = plane-fused, 0 = five axis
+ * passes.  The plane-fused path runs the forward x and y transforms of a
+ * z-plane in one kernel (a thread-block cluster per plane: each CTA
+ * transforms its rows along x into its shared memory, then its k_x columns
+ * along y, reading every y from the cluster's shared memory), the z pass with
+ * the filter and the inverse z transform, and the inverse y and x transforms
+ * of a z-plane in one kernel the same way: the half spectrum moves through
+ * HBM twice per frame instead of four times.  It exists for the cubic grids
+ * 32 ... 384 and the elongated grids 32 x 64, 64 x 128, 128 x 256, 48 x 96,
+ * 384 x 48, 192 x 48, 32 x 384, 32 x 192, 48 x 32 (n_x x n_y) where its
+ * clusters fit the device.  A context starts on the five-pass path;
+ * ftr_autotune times both and keeps the faster (on a GB300 at 256^3 the
+ * five passes: each plane's CTAs wait on one another at every cluster
+ * barrier, where the independent tiles of the axis passes overlap).
+ * The z-pass plan (plan[1]) applies to both paths; plan[0] and plan[2] only
+ * to the five-pass path.  The paths agree within rounding (A rel-L2 ~1e-7),
+ * not bit for bit (the x transforms pair other rows).  Set: FTR_EINVAL if 1
+ * is asked where the fused kernels do not exist, FTR_ESTATE while a frame is
+ * pending; the next solve uses it.  Get: the path (or FTR_EINVAL).
+ */
+int ftr_get_transform_path(const ftr_ctx* ctx);
+int ftr_set_transform_path(ftr_ctx* ctx, int fused);
 
 /* Message of the last error on this context (never NULL). */
 const char* ftr_last_error(const ftr_ctx* ctx);
@@ -344,13 +391,24 @@ int ftr_get_inside_mask(ftr_ctx* ctx, uint32_t* out);
 /* Cube class (uint8) per cell, (n_z-1) x (n_y-1) x (n_x-1), of the current A, L. */
 int ftr_get_cube_classes(ftr_ctx* ctx, uint8_t* out);
 /* Raw copy of an internal buffer (first `bytes` bytes; waits): which = 0 the
- * x-pass / inverse-y buffer (3 x (n_x/2+1) n_y n_z complex64), which = 1 the
- * y-pass / z-pass buffer (2 x (n_x/2+1) n_y n_z complex64), both after
- * ftr_solve; which = 2 the output of the last ftr_splat_depth call over P
+ * x-pass / inverse-y buffer of the five-pass transforms (3 x (n_x/2+1) n_y
+ * n_z complex64), which = 1 the buffer of the two fields the z pass reads (2
+ * x (n_x/2+1) n_y n_z complex64; layout [k_x][k_y][z] on the five-pass
+ * path, [z][k_x][k_y] on the plane-fused one, field 0 overwritten by the
+ * filtered, inverse-z transformed spectrum), both after ftr_solve; which = 2 the output of the last ftr_splat_depth call over P
  * depth pixels in all: points (3 P float32), normals (3 P) and W (P), each
  * array's first (point count) entries valid, in pixel order (FTR_ESTATE
  * before the first such call). */
 int ftr_debug_buffer(ftr_ctx* ctx, int which, void* out, int64_t bytes);
+/* Raise, on the stream, the device flag a kernel sets when one of its bounded
+ * waits gives up (which = 0: the tensor-core completion wait of the split
+ * precision passes, 1: the bulk-copy wait of the y pass), as if a wait had
+ * timed out: the next call that reads the flags (ftr_solve with a level
+ * output, ftr_extract_mesh, ftr_frame_finish) returns FTR_ETIMEOUT and
+ * clears them; the context stays usable.  For tests of that error path
+ * without making a GPU wait run out.  FTR_EINVAL if the context has no such
+ * flag (which = 0 on an FP32 context). */
+int ftr_debug_raise_wait_flag(ftr_ctx* ctx, int which);
 /* The generated marching-cubes table: ntri[256] and tris[256 * 5 * 3] (-1 padded). */
 int ftr_mc_table(int32_t* ntri, int32_t* tris);
 /* Per-stage device time accounting (CUDA events on the context stream). */

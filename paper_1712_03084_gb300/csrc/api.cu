@@ -81,7 +81,8 @@ namespace {
 
 const char* kStageNames[ST_COUNT] = {"ingest", "splat_bin", "splat_accum", "fft_x_fwd", "fft_y_fwd",
                                      "fft_z_filter_inv", "fft_y_inv", "fft_x_inv", "level", "mc_count",
-                                     "mc_scan", "mc_emit", "mc_tris", "texture"};
+                                     "mc_scan", "mc_emit", "mc_tris", "texture", "fft_xy_fwd",
+                                     "fft_yx_inv"};
 
 bool supported_n(int n) {
     switch (n) {
@@ -98,11 +99,19 @@ cudaError_t ensure_device_ready(int dev) {
     std::lock_guard<std::mutex> lk(g_init_mu);
     if (dev >= 0 && dev < 64 && g_dev_ready[dev]) return cudaSuccess;
     cudaError_t e;
-    if ((e = fft_fx_init()) != cudaSuccess) return e;
-    if ((e = fft_fy_init()) != cudaSuccess) return e;
-    if ((e = fft_fz_init()) != cudaSuccess) return e;
-    if ((e = fft_iy_init()) != cudaSuccess) return e;
-    if ((e = fft_ix_init()) != cudaSuccess) return e;
+    // the small-DFT twiddles W_96^j, computed on the device in float64, then
+    // copied into every transform unit's constant table
+    float2* w96 = nullptr;
+    if ((e = cudaMalloc(&w96, 96 * sizeof(float2))) != cudaSuccess) return e;
+    if ((e = launch_twiddle(w96, 96, 0)) != cudaSuccess || (e = cudaStreamSynchronize(0)) != cudaSuccess ||
+        (e = fft_fx_init(w96)) != cudaSuccess || (e = fft_fy_init(w96)) != cudaSuccess ||
+        (e = fft_fz_init(w96)) != cudaSuccess || (e = fft_iy_init(w96)) != cudaSuccess ||
+        (e = fft_ix_init(w96)) != cudaSuccess || (e = fft_fused_a_init(w96)) != cudaSuccess ||
+        (e = fft_fused_b_init(w96)) != cudaSuccess || (e = fft_plane_init(w96)) != cudaSuccess) {
+        cudaFree(w96);
+        return e;
+    }
+    cudaFree(w96);
     if ((e = mc_init()) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) g_dev_ready[dev] = true;
     return cudaSuccess;
@@ -378,34 +387,31 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         delete c;
         return FTR_ENOMEM;
     }
+    // W_n^m of each axis, computed on the device in float64
     for (int a = 0; a < 3; ++a) {
-        const int n = grid_n[a];
-        std::vector<float2> tw(n);
-        for (int m = 0; m < n; ++m) {
-            const double ang = 2.0 * 3.14159265358979323846 * (double)m / (double)n;
-            tw[m] = make_float2((float)cos(ang), (float)(-sin(ang)));
-        }
-        if ((e = cudaMemcpy(c->d_tw[a], tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        if ((e = launch_twiddle(c->d_tw[a], grid_n[a], c->stream)) != cudaSuccess) {
             free_all(c);
             delete c;
             return FTR_ECUDA;
         }
     }
     if (prm.precision != FTR_PREC_FP32) {
-        std::vector<unsigned char> tab;
-        tc_build_table(prm.precision, tab);
-        if ((e = dalloc(&c->d_tc_table, tab.size())) != cudaSuccess || (e = dalloc(&c->d_tc_err, 1)) != cudaSuccess) {
+        if ((e = dalloc(&c->d_tc_table, tc_table_bytes())) != cudaSuccess || (e = dalloc(&c->d_tc_err, 1)) != cudaSuccess) {
             free_all(c);
             delete c;
             return FTR_ENOMEM;
         }
-        if ((e = cudaMemcpy(c->d_tc_table, tab.data(), tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        // the split DFT matrices, built on the device from float64 cos / sin
+        if ((e = tc_build_table(prm.precision, c->d_tc_table, c->stream)) != cudaSuccess ||
             (e = cudaMemset(c->d_tc_err, 0, sizeof(int))) != cudaSuccess || (e = tc_prepare(c)) != cudaSuccess) {
             free_all(c);
             delete c;
             return FTR_ECUDA;
         }
     }
+    // the plane-fused transforms where they are built for this grid and fit
+    c->fused_ok = prm.precision == FTR_PREC_FP32 && fused_available(c);
+    c->fused = 0;         // five axis passes until ftr_autotune times both paths
     for (int s = 0; s < ST_COUNT; ++s) {
         cudaEventCreate(&c->ev_start[s]);
         cudaEventCreate(&c->ev_stop[s]);
@@ -557,6 +563,39 @@ int raw_enqueue(ftr_ctx* c, const char* who, const ftr_view* views, int k, doubl
 
 }  // namespace
 
+int ftr_splat_sets(ftr_ctx* c, const ftr_point_set* sets, int k) {
+    if (!c) return FTR_EINVAL;
+    if (c->depth_async) return set_err(c, FTR_ESTATE, "ftr_splat_sets: the frame's points come from ftr_splat_depth_async");
+    if (k < 1 || k > kMaxSets || !sets) return set_err(c, FTR_EINVAL, "ftr_splat_sets: 1 <= k <= %d sets", kMaxSets);
+    IngestSets S{};
+    S.k = k;
+    S.base = c->n_pts;
+    S.off[0] = 0;
+    for (int s = 0; s < k; ++s) {
+        const ftr_point_set& p = sets[s];
+        if (p.n < 0) return set_err(c, FTR_EINVAL, "ftr_splat_sets: set %d has n < 0", s);
+        if (p.n > 0 && (!is_device_ptr(p.points) || !is_device_ptr(p.normals) ||
+                        (p.weights && !is_device_ptr(p.weights))))
+            return set_err(c, FTR_EINVAL, "ftr_splat_sets: set %d needs device points, normals (and weights)", s);
+        S.pts[s] = p.points;
+        S.nrm[s] = p.normals;
+        S.w[s] = p.weights;
+        S.off[s + 1] = S.off[s] + p.n;
+    }
+    const int64_t n = S.off[k];
+    if (n == 0) return FTR_OK;
+    if (c->n_pts + n > (int64_t)0x3fffffff) return set_err(c, FTR_EINVAL, "ftr_splat_sets: too many points per frame");
+    cudaError_t e;
+    if ((e = grow_points(c, c->n_pts + n)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_sets: point store");
+    prof_begin(c, ST_INGEST);
+    e = launch_ingest_sets(c, S);
+    prof_end(c, ST_INGEST);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_splat_sets: ingest");
+    c->n_pts += n;
+    c->points_in += n;
+    return FTR_OK;
+}
+
 int ftr_splat_depth(ftr_ctx* c, const ftr_view* views, int k, double step, double noise, int radius,
                     float* const* conf_out) {
     if (!c) return FTR_EINVAL;
@@ -594,6 +633,50 @@ int ftr_splat_depth_async(ftr_ctx* c, const ftr_view* views, int k, double step,
     return FTR_OK;
 }
 
+namespace {
+
+// The forward 3D FFT with the integration filter and the inverse 3D FFT
+// (Sec. III-B): three plane-fused kernels, or five axis passes.
+cudaError_t launch_transforms(ftr_ctx* c) {
+    cudaError_t e;
+    if (c->fused && c->p.precision == FTR_PREC_FP32) {
+        prof_begin(c, ST_FXY);
+        e = launch_fxy(c);
+        prof_end(c, ST_FXY);
+        if (e != cudaSuccess) return e;
+        prof_begin(c, ST_FZ);
+        e = launch_fz2(c);
+        prof_end(c, ST_FZ);
+        if (e != cudaSuccess) return e;
+        prof_begin(c, ST_IYX);
+        e = launch_iyx(c);
+        prof_end(c, ST_IYX);
+        return e;
+    }
+    prof_begin(c, ST_FX);
+    e = launch_fx(c);
+    prof_end(c, ST_FX);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, ST_FY);
+    e = launch_fy(c);
+    prof_end(c, ST_FY);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, ST_FZ);
+    e = launch_fz(c);
+    prof_end(c, ST_FZ);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, ST_IY);
+    e = launch_iy(c);
+    prof_end(c, ST_IY);
+    if (e != cudaSuccess) return e;
+    prof_begin(c, ST_IX);
+    e = launch_ix(c);
+    prof_end(c, ST_IX);
+    return e;
+}
+
+}  // namespace
+
 int ftr_solve(ftr_ctx* c, double* iso_level_out) {
     if (!c) return FTR_EINVAL;
     cudaError_t e;
@@ -604,26 +687,7 @@ int ftr_solve(ftr_ctx* c, double* iso_level_out) {
     if (!c->v_external) {
         if ((e = launch_splat(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: splat");
     }
-    prof_begin(c, ST_FX);
-    e = launch_fx(c);
-    prof_end(c, ST_FX);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: fft x");
-    prof_begin(c, ST_FY);
-    e = launch_fy(c);
-    prof_end(c, ST_FY);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: fft y");
-    prof_begin(c, ST_FZ);
-    e = launch_fz(c);
-    prof_end(c, ST_FZ);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: fft z + filter");
-    prof_begin(c, ST_IY);
-    e = launch_iy(c);
-    prof_end(c, ST_IY);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: inverse y");
-    prof_begin(c, ST_IX);
-    e = launch_ix(c);
-    prof_end(c, ST_IX);
-    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_solve: inverse x");
+    if ((e = launch_transforms(c)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: transforms");
     prof_begin(c, ST_LEVEL);
     e = launch_level(c);
     prof_end(c, ST_LEVEL);
@@ -869,11 +933,7 @@ int device_viewset(ftr_ctx* c, const ftr_view* views, int k, ViewSet& vs, const 
 cudaError_t enqueue_frame(ftr_ctx* c, const ViewSet& vs, float tol, const ftr_tex& out, int64_t out_capacity) {
     cudaError_t e;
     if ((e = launch_splat(c)) != cudaSuccess) return e;
-    if ((e = launch_fx(c)) != cudaSuccess) return e;
-    if ((e = launch_fy(c)) != cudaSuccess) return e;
-    if ((e = launch_fz(c)) != cudaSuccess) return e;
-    if ((e = launch_iy(c)) != cudaSuccess) return e;
-    if ((e = launch_ix(c)) != cudaSuccess) return e;
+    if ((e = launch_transforms(c)) != cudaSuccess) return e;
     if ((e = launch_level(c)) != cudaSuccess) return e;
     if ((e = launch_mc_count(c)) != cudaSuccess) return e;
     if ((e = launch_mc_emit(c)) != cudaSuccess) return e;
@@ -1157,7 +1217,7 @@ int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
 
 namespace {
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int, int, int>, std::array<int, 3>> g_plans;   // (device, n) -> lines per CTA
+std::map<std::tuple<int, int, int, int>, std::array<int, 4>> g_plans;   // (device, n) -> lines per CTA, path
 
 bool valid_lines(int f) { return f == 8 || f == 16 || f == 32; }
 
@@ -1188,10 +1248,27 @@ int ftr_set_plan(ftr_ctx* c, const int* plan) {
     return FTR_OK;
 }
 
+int ftr_get_transform_path(const ftr_ctx* c) {
+    if (!c) return FTR_EINVAL;
+    return c->fused;
+}
+
+int ftr_set_transform_path(ftr_ctx* c, int fused) {
+    if (!c || (fused != 0 && fused != 1)) return FTR_EINVAL;
+    if (fused && !c->fused_ok)
+        return set_err(c, FTR_EINVAL, "ftr_set_transform_path: no plane-fused kernels for this grid or precision");
+    if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_set_transform_path: a frame is pending");
+    c->fused = fused;
+    c->graph_valid = false;
+    c->solved = false;
+    c->meshed = false;
+    return FTR_OK;
+}
+
 int ftr_autotune(ftr_ctx* c, float* report) {
     if (!c) return FTR_EINVAL;
     if (report)
-        for (int i = 0; i < 12; ++i) report[i] = 0.f;
+        for (int i = 0; i < 16; ++i) report[i] = 0.f;
     if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_autotune: a frame is pending");
     if (c->p.precision != FTR_PREC_FP32) return FTR_OK;
     const auto key = std::make_tuple(c->device, c->g.n[0], c->g.n[1], c->g.n[2]);
@@ -1200,6 +1277,7 @@ int ftr_autotune(ftr_ctx* c, float* report) {
         auto it = g_plans.find(key);
         if (it != g_plans.end()) {
             for (int i = 0; i < 3; ++i) c->plan_lines[i] = it->second[i];
+            c->fused = it->second[3] && c->fused_ok ? 1 : 0;
             c->graph_valid = false;
             return FTR_OK;
         }
@@ -1219,55 +1297,95 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     cudaEventCreate(&t1);
     const int F[4] = {8, 16, 32, -16};
     const int reps = 5;
+    // mean microseconds of `reps` runs of f (after one untimed run); < 0 if it does not launch
+    auto time_us = [&](auto&& f) -> float {
+        if (f() != cudaSuccess) {
+            cudaGetLastError();
+            return -1.f;
+        }
+        cudaEventRecord(t0, c->stream);
+        for (int r = 0; r < reps; ++r) f();
+        cudaEventRecord(t1, c->stream);
+        if (cudaEventSynchronize(t1) != cudaSuccess) return -2.f;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        return 1000.f * ms / reps;
+    };
+    // candidates keep at least two CTAs per SM: a CTA that fills an SM
+    // alone waits for a whole SM to drain when frames of other contexts run
+    // concurrently
+    auto fits_twice = [&](auto&& f) {
+        int occ = 0;
+        c->occ_query = &occ;
+        const cudaError_t qe = f();
+        c->occ_query = nullptr;
+        if (qe != cudaSuccess) cudaGetLastError();
+        return qe == cudaSuccess && occ >= 2;
+    };
+    // one tile height per pass of the five-pass transforms, and of the z pass
+    // of the plane-fused ones
     std::array<int, 3> best = {16, 16, 16};
-    for (int pass = 0; pass < 3; ++pass) {
+    int best_fz2 = 16;
+    const int saved_path = c->fused;
+    for (int pass = 0; pass < 4; ++pass) {
+        if (pass == 3 && !c->fused_ok) break;
+        const int slot = pass == 3 ? 1 : pass;
+        c->fused = pass == 3 ? 1 : 0;
         float best_us = 1e30f;
         for (int v = 0; v < 4; ++v) {
-            if (!plan_fits(c, pass, F[v])) continue;
-            c->plan_lines[pass] = F[v];
-            auto run = [&]() { return pass == 0 ? launch_fy(c) : (pass == 1 ? launch_fz(c) : launch_iy(c)); };
-            // candidates keep at least two CTAs per SM: a CTA that fills an SM
-            // alone waits for a whole SM to drain when frames of other
-            // contexts run concurrently
-            int occ = 0;
-            c->occ_query = &occ;
-            const cudaError_t qe = run();
-            c->occ_query = nullptr;
-            if (qe != cudaSuccess || occ < 2) {
-                cudaGetLastError();
-                continue;
-            }
-            if (run() != cudaSuccess) {     // the variant does not fit: skip it
-                cudaGetLastError();
-                continue;
-            }
-            cudaEventRecord(t0, c->stream);
-            for (int r = 0; r < reps; ++r) run();
-            cudaEventRecord(t1, c->stream);
-            if ((e = cudaEventSynchronize(t1)) != cudaSuccess) {
+            if (!plan_fits(c, slot, F[v])) continue;
+            c->plan_lines[slot] = F[v];
+            auto run = [&]() {
+                if (pass == 3) return launch_fz2(c);
+                return pass == 0 ? launch_fy(c) : (pass == 1 ? launch_fz(c) : launch_iy(c));
+            };
+            if (!fits_twice(run)) continue;
+            const float us = time_us(run);
+            if (us == -2.f) {
                 cudaEventDestroy(t0);
                 cudaEventDestroy(t1);
-                return cuda_fail(c, e, "ftr_autotune");
+                c->fused = saved_path;
+                return cuda_fail(c, cudaGetLastError(), "ftr_autotune");
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            const float us = 1000.f * ms / reps;
-            if (report) report[4 * pass + v] = us;
+            if (us < 0.f) continue;          // the variant does not fit: skip it
+            if (report && pass < 3) report[4 * pass + v] = us;
             if (us < best_us) {
                 best_us = us;
-                best[pass] = F[v];
+                if (pass == 3)
+                    best_fz2 = F[v];
+                else
+                    best[pass] = F[v];
             }
         }
-        c->plan_lines[pass] = best[pass];
+        c->plan_lines[slot] = best[slot];
     }
+    // the transform path: both whole chains (forward, filter, inverse) at
+    // their best tile heights; the faster one is kept
+    int path = 0;
+    c->fused = 0;
+    for (int i = 0; i < 3; ++i) c->plan_lines[i] = best[i];
+    const float five_us = time_us([&]() { return launch_transforms(c); });
+    if (report) report[12] = five_us;
+    if (c->fused_ok) {
+        c->fused = 1;
+        c->plan_lines[1] = best_fz2;
+        const float fused_us = time_us([&]() { return launch_transforms(c); });
+        if (report) report[13] = fused_us;
+        if (fused_us > 0.f && (five_us < 0.f || fused_us < five_us)) path = 1;
+    }
+    if (path == 1) best[1] = best_fz2;
+    c->fused = path;
+    for (int i = 0; i < 3; ++i) c->plan_lines[i] = best[i];
+    if (report) report[14] = (float)path;
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ftr_autotune");
     c->graph_valid = false;
     c->solved = false;       // the timing runs overwrote the spectra and the indicator
     c->meshed = false;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        g_plans[key] = best;
+        g_plans[key] = {best[0], best[1], best[2], path};
     }
     return FTR_OK;
 }
@@ -1500,6 +1618,16 @@ int ftr_debug_buffer(ftr_ctx* c, int which, void* out, int64_t bytes) {
     cudaError_t e = cudaMemcpyAsync(out, src, (size_t)bytes, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_debug_buffer");
+    return FTR_OK;
+}
+
+int ftr_debug_raise_wait_flag(ftr_ctx* c, int which) {
+    if (!c) return FTR_EINVAL;
+    int* flag = which == 0 ? c->d_tc_err : (which == 1 ? c->d_kerr : nullptr);
+    if (!flag) return set_err(c, FTR_EINVAL, "ftr_debug_raise_wait_flag: no flag %d on this context", which);
+    // the flag's lowest byte to 1: the value a kernel writes when a bounded wait gives up
+    cudaError_t e = cudaMemsetAsync(flag, 1, 1, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ftr_debug_raise_wait_flag");
     return FTR_OK;
 }
 

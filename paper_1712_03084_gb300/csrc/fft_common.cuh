@@ -27,23 +27,13 @@
 
 namespace ftr {
 
-// W_96^j = exp(-2 pi i j / 96); filled from the host (double cos/sin) once per
-// device by each translation unit's init function.
+// W_96^j = exp(-2 pi i j / 96), a constant table of each translation unit,
+// copied once per device by the unit's init function from the table the
+// device computed in float64 (launch_twiddle, n = 96).
 static __constant__ float2 c_w96[96];
 
-static inline cudaError_t upload_w96_table(const void* symbol_ptr_unused = nullptr) {
-    (void)symbol_ptr_unused;
-    float2 h[96];
-    for (int j = 0; j < 96; ++j) {
-        double a = 2.0 * 3.14159265358979323846 * (double)j / 96.0;
-        h[j] = make_float2((float)cos(a), (float)(-sin(a)));
-    }
-    // exact values where the circle meets the axes and the diagonals
-    h[0] = make_float2(1.f, 0.f);
-    h[24] = make_float2(0.f, -1.f);
-    h[48] = make_float2(-1.f, 0.f);
-    h[72] = make_float2(0.f, 1.f);
-    return cudaMemcpyToSymbol(c_w96, h, sizeof(h));
+static inline cudaError_t upload_w96_table(const float2* w96_dev) {
+    return cudaMemcpyToSymbol(c_w96, w96_dev, 96 * sizeof(float2), 0, cudaMemcpyDeviceToDevice);
 }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

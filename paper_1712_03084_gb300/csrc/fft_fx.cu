@@ -138,7 +138,7 @@ cudaError_t run_fx(ftr_ctx* c) {
 
 }  // namespace
 
-cudaError_t fft_fx_init() { return upload_w96_table(); }
+cudaError_t fft_fx_init(const float2* w96) { return upload_w96_table(w96); }
 
 cudaError_t launch_fx(ftr_ctx* c) {
     if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 0);

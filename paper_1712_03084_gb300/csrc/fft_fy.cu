@@ -216,7 +216,7 @@ cudaError_t run_fy(ftr_ctx* c) {
 
 }  // namespace
 
-cudaError_t fft_fy_init() { return upload_w96_table(); }
+cudaError_t fft_fy_init(const float2* w96) { return upload_w96_table(w96); }
 
 cudaError_t launch_fy(ftr_ctx* c) {
     if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 1);

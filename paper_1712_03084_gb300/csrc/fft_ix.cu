@@ -102,7 +102,7 @@ cudaError_t run_ix(ftr_ctx* c) {
 
 }  // namespace
 
-cudaError_t fft_ix_init() { return upload_w96_table(); }
+cudaError_t fft_ix_init(const float2* w96) { return upload_w96_table(w96); }
 
 cudaError_t launch_ix(ftr_ctx* c) {
     if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 4);

@@ -710,68 +710,65 @@ cudaError_t run_pass_n(ftr_ctx* c, int pass, int n, bool launch) {
 
 int pass_axis(int pass) { return pass == 0 || pass == 4 ? 0 : (pass == 1 || pass == 3 ? 1 : 2); }
 
-// Host: one 16-bit value (bf16 or fp16, round to nearest even) of a double.
-unsigned short host_round16(double x, bool bf16) {
-    unsigned short b;
-    if (bf16) {
-        const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
-        memcpy(&b, &h, 2);
-    } else {
-        const __half h = __float2half_rn((float)x);
-        memcpy(&b, &h, 2);
-    }
-    return b;
-}
-double host_back16(unsigned short b, bool bf16) {
-    if (bf16) {
-        __nv_bfloat16 h;
-        memcpy(&h, &b, 2);
-        return (double)__bfloat162float(h);
-    }
-    __half h;
-    memcpy(&h, &b, 2);
-    return (double)__half2float(h);
-}
-
 }  // namespace
 
 bool tc_supported_n(int n) { return n == 64 || n == 128 || n == 256 || n == 384; }
 
 size_t tc_table_bytes() { return kTcTableBytes; }
 
+namespace {
+
 // The real 2R x 2R DFT matrices (B operand, K-major: element (output column
-// nn, input row kk)), split into hi / lo 16-bit parts.
-void tc_build_table(int precision, std::vector<unsigned char>& out) {
-    const bool bf16 = precision == FTR_PREC_BF16X3;
-    out.assign(kTcTableBytes, 0);
+// nn, input row kk)) of R = 8, 16, 24, 32 and both signs, split into hi / lo
+// 16-bit parts: one thread per complex entry (R, sign, q, m), the cos / sin
+// of 2 pi (m q mod R) / R in float64 (sincospi: exact at the quarter points).
+template <int P>
+__global__ void k_tc_table(unsigned char* __restrict__ out) {
     const int Rs[4] = {8, 16, 24, 32};
-    for (int R : Rs) {
-        for (int sign = -1; sign <= 1; sign += 2) {
-            unsigned short* hi = (unsigned short*)(out.data() + tc_block(R, sign, 0));
-            unsigned short* lo = (unsigned short*)(out.data() + tc_block(R, sign, 1));
-            for (int q = 0; q < R; ++q) {
-                for (int m = 0; m < R; ++m) {
-                    const int jm = (m * q) % R;
-                    double cr = cos(2.0 * 3.14159265358979323846 * jm / R);
-                    double ci = (double)sign * sin(2.0 * 3.14159265358979323846 * jm / R);
-                    if (fabs(cr) < 1e-15) cr = 0.0;
-                    if (fabs(ci) < 1e-15) ci = 0.0;
-                    // y_re = sum x_re cr - x_im ci; y_im = sum x_re ci + x_im cr
-                    const double ent[2][2] = {{cr, -ci}, {ci, cr}};   // [c_out][c_in]
-                    for (int co = 0; co < 2; ++co) {
-                        for (int ci_ = 0; ci_ < 2; ++ci_) {
-                            const double x = ent[co][ci_];
-                            const unsigned short h = host_round16(x, bf16);
-                            const unsigned short l = host_round16(x - host_back16(h, bf16), bf16);
-                            const int o = tc_off(R, 2 * q + co, 2 * m + ci_) / 2;
-                            hi[o] = h;
-                            lo[o] = l;
-                        }
-                    }
-                }
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int ri = 0; ri < 4; ++ri) {
+        const int R = Rs[ri];
+        const int per_sign = R * R;
+        if (t >= 2 * per_sign) {
+            t -= 2 * per_sign;
+            continue;
+        }
+        const int sign = t < per_sign ? -1 : 1;
+        const int u = t % per_sign;
+        const int q = u / R, m = u % R;
+        const int jm = (m * q) % R;
+        double sn, cs;
+        sincospi(2.0 * (double)jm / (double)R, &sn, &cs);
+        const double cr = cs, ci = (double)sign * sn;
+        // y_re = sum x_re cr - x_im ci; y_im = sum x_re ci + x_im cr
+        const double ent[2][2] = {{cr, -ci}, {ci, cr}};   // [c_out][c_in]
+        unsigned short* hi = (unsigned short*)(out + tc_block(R, sign, 0));
+        unsigned short* lo = (unsigned short*)(out + tc_block(R, sign, 1));
+        for (int co = 0; co < 2; ++co) {
+            for (int cin = 0; cin < 2; ++cin) {
+                const double x = ent[co][cin];
+                const unsigned short h = Half16<P>::rn((float)x);
+                const unsigned short l = Half16<P>::rn((float)(x - (double)Half16<P>::back(h)));
+                const int o = tc_off(R, 2 * q + co, 2 * m + cin) / 2;
+                hi[o] = h;
+                lo[o] = l;
             }
         }
+        return;
     }
+}
+
+}  // namespace
+
+cudaError_t tc_build_table(int precision, unsigned char* table_dev, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(table_dev, 0, kTcTableBytes, st);
+    if (e != cudaSuccess) return e;
+    const int entries = 2 * (8 * 8 + 16 * 16 + 24 * 24 + 32 * 32);
+    if (precision == FTR_PREC_BF16X3)
+        k_tc_table<FTR_PREC_BF16X3><<<(entries + 127) / 128, 128, 0, st>>>(table_dev);
+    else
+        k_tc_table<FTR_PREC_FP16X3><<<(entries + 127) / 128, 128, 0, st>>>(table_dev);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pass(ftr_ctx* c, int pass) {

@@ -36,6 +36,8 @@ enum Stage {
     ST_MC_EMIT,
     ST_MC_TRIS,
     ST_TEXTURE,
+    ST_FXY,           // plane-fused forward x + y
+    ST_IYX,           // plane-fused inverse y + x
     ST_COUNT
 };
 
@@ -126,12 +128,14 @@ struct ftr_ctx {
     float* d_vpool = nullptr;  // active bricks x 3 x 512 V values
 
     // spectra and indicator
-    float2* d_s0 = nullptr;    // 3 x Mh  [kx][z][y]
-    float2* d_s1 = nullptr;    // 2 x Mh  [kx][ky][z]
+    float2* d_s0 = nullptr;    // 3 x Mh  [kx][z][y] (five-pass path)
+    float2* d_s1 = nullptr;    // 2 x Mh  [kx][ky][z] (five-pass path) or [z][kx][ky] (plane-fused path)
     float* d_A = nullptr;      // M       [z][y][x]
     float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
     int plan_lines[3] = {16, 16, 16};      // lines per CTA of the y, z and inverse-y passes (-16: y pass
                                            // with bulk-copied tiles)
+    int fused = 0;                         // transform path: 1 plane-fused (x+y, z, y+x), 0 five axis passes
+    bool fused_ok = false;                 // the plane-fused kernels exist for this grid and fit the device
     int* occ_query = nullptr;              // set: the pass launchers report occupancy instead of launching
     unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
     int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
@@ -242,23 +246,46 @@ int cuda_fail(ftr_ctx* c, cudaError_t e, const char* what);
 void prof_begin(ftr_ctx* c, int stage);
 void prof_end(ftr_ctx* c, int stage);
 
-// per translation unit one-time device setup
-cudaError_t fft_fx_init();
-cudaError_t fft_fy_init();
-cudaError_t fft_fz_init();
-cudaError_t fft_iy_init();
-cudaError_t fft_ix_init();
+// per translation unit one-time device setup; w96: the device table W_96^j
+cudaError_t fft_fx_init(const float2* w96);
+cudaError_t fft_fy_init(const float2* w96);
+cudaError_t fft_fz_init(const float2* w96);
+cudaError_t fft_iy_init(const float2* w96);
+cudaError_t fft_ix_init(const float2* w96);
+cudaError_t fft_fused_a_init(const float2* w96);
+cudaError_t fft_fused_b_init(const float2* w96);
+cudaError_t fft_plane_init(const float2* w96);
+// W_n^m, m < n, in float64 on the device, stored float32 (twiddle.cu)
+cudaError_t launch_twiddle(float2* tw, int n, cudaStream_t st);
 cudaError_t mc_init();
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const float* w, int64_t n,
                           const int* n_dev = nullptr);   // n_dev: device count, n its bound
+// Point sets ingested in one launch (ftr_splat_sets): set s holds points
+// off[s] .. off[s + 1] - 1 of the launch, stored from slot base on.
+constexpr int kMaxSets = 16;
+struct IngestSets {
+    const float* pts[kMaxSets];
+    const float* nrm[kMaxSets];
+    const float* w[kMaxSets];
+    int64_t off[kMaxSets + 1];
+    int64_t base;
+    int k;
+};
+cudaError_t launch_ingest_sets(ftr_ctx* c, const IngestSets& S);
 cudaError_t launch_splat(ftr_ctx* c);          // bin + accumulate into d_vpool
 cudaError_t launch_fx(ftr_ctx* c);
 cudaError_t launch_fy(ftr_ctx* c);
 cudaError_t launch_fz(ftr_ctx* c);
 cudaError_t launch_iy(ftr_ctx* c);
 cudaError_t launch_ix(ftr_ctx* c);
+// plane-fused transform path (fft_plane.cu): forward x + y per z-plane, the
+// z pass on plane-major fields, inverse y + x per z-plane
+bool fused_available(ftr_ctx* c);
+cudaError_t launch_fxy(ftr_ctx* c);
+cudaError_t launch_fz2(ftr_ctx* c);
+cudaError_t launch_iyx(ftr_ctx* c);
 cudaError_t launch_level(ftr_ctx* c);
 // raw reconstruction (raw.cu): depth maps -> compacted points, normals, W
 struct RawParams {
@@ -274,7 +301,7 @@ int raw_max_radius();
 // 2 z fwd + filter + z inv, 3 y inv, 4 x inv
 bool tc_supported_n(int n);
 size_t tc_table_bytes();
-void tc_build_table(int precision, std::vector<unsigned char>& out);
+cudaError_t tc_build_table(int precision, unsigned char* table_dev, cudaStream_t st);
 cudaError_t launch_tc_pass(ftr_ctx* c, int pass);
 cudaError_t tc_prepare(ftr_ctx* c);
 cudaError_t launch_mc_bits(ftr_ctx* c);        // inside bits A >= L only

@@ -83,22 +83,18 @@ __device__ __forceinline__ bool node_t_pair(float x, float bmin, float ih, float
 }
 
 // n_dev (nullable): the point count on the device; n then only bounds it.
-__global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
-                         const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
-                         float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
-                         int64_t* npts_dev, const int* __restrict__ n_dev) {
-    pdl_wait();
-    if (n_dev) n = min(n, (int64_t)*n_dev);
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) *npts_dev = base + n;   // points stored so far: later kernels read the count here
-    if (i >= n) return;
+// One point: t per axis with every decision equal to the float64 one, the
+// acceptance test, and the point record at slot `dst`.
+__device__ __forceinline__ void ingest_one(const float* p, const float* q, const float* wp, int64_t dst, const GridDev& g,
+                                           int4* pbase, float4* pfrac, float4* pnrm, unsigned long long* dropped,
+                                           int* wild_weights) {
     bool ok = true;
     int fl[3] = {0, 0, 0};
     float fr[3] = {0.f, 0.f, 0.f};
     int up = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float x = pts[3 * i + c];
+        const float x = p[c];
         int fli;
         float r;
         bool u;
@@ -126,11 +122,38 @@ __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict_
         atomicAdd(dropped, 1ull);
         fl[0] = fl[1] = fl[2] = 0;
     }
-    pbase[base + i] = make_int4(fl[0], fl[1], fl[2], ok ? (1 | (up << 1)) : 0);
-    const float wi = w ? w[i] : 1.0f;
+    pbase[dst] = make_int4(fl[0], fl[1], fl[2], ok ? (1 | (up << 1)) : 0);
+    const float wi = wp ? *wp : 1.0f;
     if (ok && !(wi >= 0.f && wi <= 1.f)) atomicOr(wild_weights, 1);   // outside the fast path's range
-    pfrac[base + i] = make_float4(fr[0], fr[1], fr[2], wi);
-    pnrm[base + i] = make_float4(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], 0.f);
+    pfrac[dst] = make_float4(fr[0], fr[1], fr[2], wi);
+    pnrm[dst] = make_float4(q[0], q[1], q[2], 0.f);
+}
+
+__global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
+                         const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
+                         float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
+                         int64_t* npts_dev, const int* __restrict__ n_dev) {
+    pdl_wait();
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *npts_dev = base + n;   // points stored so far: later kernels read the count here
+    if (i >= n) return;
+    ingest_one(pts + 3 * i, nrm + 3 * i, w ? w + i : nullptr, base + i, g, pbase, pfrac, pnrm, dropped, wild_weights);
+}
+
+// Several point sets in one launch: thread i ingests point i of the
+// concatenation of the sets (set order, as separate launches would store them).
+__global__ void k_ingest_sets(IngestSets S, GridDev g, int4* pbase, float4* pfrac, float4* pnrm,
+                              unsigned long long* dropped, int* wild_weights, int64_t* npts_dev) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *npts_dev = S.base + S.off[S.k];
+    if (i >= S.off[S.k]) return;
+    int s = 0;
+    while (s + 1 < S.k && i >= S.off[s + 1]) ++s;
+    const int64_t j = i - S.off[s];
+    ingest_one(S.pts[s] + 3 * j, S.nrm[s] + 3 * j, S.w[s] ? S.w[s] + j : nullptr, S.base + i, g, pbase, pfrac, pnrm,
+               dropped, wild_weights);
 }
 
 // Brick range [lo, hi] per axis that the point's stencil overlaps.
@@ -593,6 +616,15 @@ cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const 
     // small CTAs spread the few float64 operations per point over every SM
     launch_pdl(k_ingest, blocks_for(n, 32), 32, 0, c->stream, pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
                                                        c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts, n_dev);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ingest_sets(ftr_ctx* c, const IngestSets& S) {
+    const int64_t n = S.off[S.k];
+    if (n == 0) return cudaSuccess;
+    launch_pdl(k_ingest_sets, blocks_for(n, 32), 32, 0, c->stream, S, c->g, c->pts.base, c->pts.frac, c->pts.nrm,
+               c->d_dropped, c->d_wild, c->d_npts);
     c->launches++;
     return cudaGetLastError();
 }

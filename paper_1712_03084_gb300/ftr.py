@@ -56,6 +56,11 @@ class ftr_tex(ctypes.Structure):
                 ("textured", ctypes.c_void_p)]
 
 
+class ftr_point_set(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("normals", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
 class ftr_camera(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int), ("h", ctypes.c_int), ("K", ctypes.c_float * 9),
                 ("world_to_cam", ctypes.c_float * 12)]
@@ -88,6 +93,7 @@ _SIGNATURES = [
     ("ftr_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ftr_splat", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_int64]),
+    ("ftr_splat_sets", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_point_set), ctypes.c_int]),
     ("ftr_splat_depth", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     ("ftr_splat_depth_async", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ftr_view), ctypes.c_int,
@@ -116,6 +122,8 @@ _SIGNATURES = [
     ("ftr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_get_transform_path", ctypes.c_int, [ctypes.c_void_p]),
+    ("ftr_set_transform_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_field_A", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -123,6 +131,7 @@ _SIGNATURES = [
     ("ftr_get_cube_classes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_inside_mask", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_debug_buffer", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64]),
+    ("ftr_debug_raise_wait_flag", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ftr_mc_table", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ftr_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -219,6 +228,19 @@ def ftr_splat(ctx, points, normals, weights=None):
     n = int(points.shape[0])
     _check(load().ftr_splat(ctx, _ptr(points, np.float32), _ptr(normals, np.float32),
                             _ptr(weights, np.float32), n), ctx)
+
+
+def ftr_splat_sets(ctx, sets):
+    """sets: list of (points, normals, weights-or-None) device tensors; one ingest launch."""
+    arr = (ftr_point_set * len(sets))()
+    for i, (p, n, w) in enumerate(sets):
+        arr[i].points = _ptr(p, np.float32)
+        arr[i].normals = _ptr(n, np.float32)
+        arr[i].weights = _ptr(w, np.float32)
+        arr[i].n = int(p.shape[0])
+        if n.shape[0] != p.shape[0] or (w is not None and w.shape[0] != p.shape[0]):
+            raise ValueError("points, normals and weights of a set must have the same length")
+    _check(load().ftr_splat_sets(ctx, arr, len(sets)), ctx)
 
 
 def ftr_solve(ctx, want_level=True):
@@ -388,12 +410,14 @@ def ftr_estimate_bytes(grid_n, points, depth_pixels, vertices, tris, precision=F
 
 
 def ftr_autotune(ctx):
-    """Time the tile plans; returns the 3 x 4 microseconds per launch (rows: y,
-    z, inverse-y passes; columns: 8, 16, 32 lines per CTA and the bulk-copied
-    16-line y pass; 0 = not timed)."""
-    rep = np.zeros(12, np.float32)
+    """Time the tile plans and the transform paths; returns the 16-float
+    report of include/ftr.h ([0..11]: microseconds per launch, rows y, z,
+    inverse-y passes x columns 8, 16, 32 lines per CTA and the bulk-copied
+    16-line y pass; [12], [13]: the five-pass and plane-fused chains; [14]:
+    the path kept; 0 = not timed)."""
+    rep = np.zeros(16, np.float32)
     _check(load().ftr_autotune(ctx, rep.ctypes.data), ctx)
-    return rep.reshape(3, 4)
+    return rep
 
 
 def ftr_get_plan(ctx):
@@ -405,6 +429,18 @@ def ftr_get_plan(ctx):
 def ftr_set_plan(ctx, plan):
     arr = np.ascontiguousarray(plan, dtype=np.int32)
     _check(load().ftr_set_plan(ctx, arr.ctypes.data), ctx)
+
+
+def ftr_get_transform_path(ctx):
+    """1: plane-fused transforms, 0: five axis passes."""
+    v = load().ftr_get_transform_path(ctx)
+    if v < 0:
+        _check(v, ctx)
+    return int(v)
+
+
+def ftr_set_transform_path(ctx, fused):
+    _check(load().ftr_set_transform_path(ctx, int(fused)), ctx)
 
 
 def ftr_last_error(ctx):
@@ -433,6 +469,10 @@ def ftr_get_cube_classes(ctx, out):
 
 def ftr_debug_buffer(ctx, which, out):
     _check(load().ftr_debug_buffer(ctx, int(which), _ptr(out), int(out.nbytes)), ctx)
+
+
+def ftr_debug_raise_wait_flag(ctx, which):
+    _check(load().ftr_debug_raise_wait_flag(ctx, int(which)), ctx)
 
 
 def ftr_mc_table():
@@ -545,6 +585,9 @@ class Context:
     def splat(self, points, normals, weights=None):
         ftr_splat(self.h, points, normals, weights)
 
+    def splat_sets(self, sets):
+        ftr_splat_sets(self.h, sets)
+
     def solve(self, want_level=True):
         return ftr_solve(self.h, want_level)
 
@@ -572,13 +615,22 @@ class Context:
         return ftr_stats(self.h)
 
     def autotune(self):
-        return ftr_autotune(self.h)
+        """Per-pass tile timings as 3 x 4 microseconds (the whole report is
+        kept in ``tune_report``)."""
+        self.tune_report = ftr_autotune(self.h)
+        return self.tune_report[:12].reshape(3, 4)
 
     def plan(self):
         return ftr_get_plan(self.h)
 
     def set_plan(self, plan):
         ftr_set_plan(self.h, plan)
+
+    def transform_path(self):
+        return ftr_get_transform_path(self.h)
+
+    def set_transform_path(self, fused):
+        ftr_set_transform_path(self.h, fused)
 
     def frame_info(self):
         return ftr_frame_info(self.h)

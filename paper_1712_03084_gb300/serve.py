@@ -149,8 +149,9 @@ class Slot:
             if fin.rgbd:
                 # points, normals and the confidence maps from the depth maps, on the device
                 ftr.ftr_splat_depth(self.ctx.h, self.views, conf_out=[d["conf"] for d in self.views], wait=False)
-            for (s, c) in fin.per_camera:
-                ftr.ftr_splat(self.ctx.h, self.P[s:s + c], self.N[s:s + c], self.W[s:s + c])
+            if fin.per_camera:        # every camera's points in one ingest launch
+                ftr.ftr_splat_sets(self.ctx.h, [(self.P[s:s + c], self.N[s:s + c], self.W[s:s + c])
+                                                for (s, c) in fin.per_camera])
             ftr.ftr_frame_launch(self.ctx.h, self.views, self.tol, self.out_w, self.out_uv, self.out_rgb,
                                  self.out_tex, self.cap)
             self.done.record(self.stream)

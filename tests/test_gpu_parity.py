@@ -59,6 +59,30 @@ def test_indicator_and_level(ftr, name):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", list(G.CASES))
+def test_both_transform_paths_match_the_oracle(ftr, name):
+    """The plane-fused transforms (forward x+y and inverse y+x per z-plane in
+    one thread-block cluster) and the five axis passes both meet the A and L
+    bars against the oracle, and agree with each other to rounding."""
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    r = G.oracle_result(name)
+    span = float(r["A"].max() - r["A"].min())
+    got = {}
+    for path in (1, 0):
+        ctx = ftr.Context(c["grid"], c["bbox"], splat_mode=c.get("mode", cv.SPLAT_WEIGHTED))
+        ctx.set_transform_path(path)                  # path 1 is built for every parity grid
+        ctx.reset()
+        ctx.splat(P, N, W)
+        L = ctx.solve()
+        A = ctx.field_A()
+        ctx.close()
+        assert G.rel_l2(A, r["A"]) <= 1e-5, path
+        assert abs(L - r["L"]) / span <= 1e-5, path
+        got[path] = A
+    assert G.rel_l2(got[1], got[0]) <= 2e-6
+
+
 @pytest.mark.parametrize("name", ["sphere64", "human96", "human_aniso"])
 def test_marching_cubes_bit_exact_on_oracle_field(ftr, name):
     c = G.CASES[name]
@@ -405,3 +429,37 @@ def test_inside_mask_is_the_binarised_volume(ftr, name):
     r = G.oracle_result(name)
     agree = np.mean(m == (r["A"] >= r["L"]))
     assert agree > 0.9999
+
+
+def test_point_sets_in_one_launch_equal_separate_calls(ftr):
+    """ftr_splat_sets (every camera's points ingested by one launch) stores
+    exactly what one ftr_splat call per camera stores: the same V, A, L and
+    the same counts; non-device sets are refused before anything runs."""
+    import torch
+    name = "human96"
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    dev = torch.device("cuda", 0)
+    Pd, Nd, Wd = (torch.from_numpy(x).to(dev) for x in (P, N, W))
+    cuts = [0, 5000, 5001, 17000, len(P)]
+    sets = [(Pd[a:b], Nd[a:b], Wd[a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
+    sets.append((Pd[:0], Nd[:0], None))                    # an empty set is allowed
+    res = []
+    for one_launch in (True, False):
+        ctx = ftr.Context(c["grid"], c["bbox"])
+        ctx.reset()
+        l0 = ctx.launch_count()
+        if one_launch:
+            ctx.splat_sets(sets)
+            assert ctx.launch_count() - l0 == 1
+        else:
+            for p, n, w in sets:
+                ctx.splat(p, n, w)
+        L = ctx.solve()
+        res.append((ctx.field_V(), ctx.field_A(), L, ctx.stats()))
+        if one_launch:
+            with pytest.raises(ftr.FtrError):
+                ctx.splat_sets([(torch.from_numpy(P[:10]), torch.from_numpy(N[:10]), None)])
+        ctx.close()
+    (V1, A1, L1, s1), (V2, A2, L2, s2) = res
+    assert np.array_equal(V1, V2) and np.array_equal(A1, A2) and L1 == L2 and s1 == s2

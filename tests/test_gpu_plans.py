@@ -24,10 +24,12 @@ def ftr():
     return F
 
 
-def _field(F, name, plan=None):
+def _field(F, name, plan=None, path=None):
     c = G.CASES[name]
     P, N, W, _ = G.case_inputs(name)
     ctx = F.Context(c["grid"], c["bbox"], splat_mode=c.get("mode", cv.SPLAT_WEIGHTED))
+    if path is not None:
+        ctx.set_transform_path(path)
     if plan is not None:
         ctx.set_plan(plan)
     ctx.reset()
@@ -52,6 +54,35 @@ def test_every_plan_is_bit_identical(ftr, name):
         assert L == ref_L, plan
 
 
+@pytest.mark.parametrize("name", ["human96", "human_aniso"])
+def test_every_z_plan_is_bit_identical_on_the_fused_path(ftr, name):
+    """The same for the z pass of the plane-fused transform path."""
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    ny = c["grid"][1]
+    ref = None
+    for fz in [f for f in (8, 16, 32) if ny % f == 0]:
+        ctx = ftr.Context(c["grid"], c["bbox"])
+        ctx.set_transform_path(1)
+        ctx.set_plan((16, fz, 16))
+        ctx.reset()
+        ctx.splat(P, N, W)
+        L = ctx.solve()
+        A = ctx.field_A()
+        ctx.close()
+        if ref is None:
+            ref = (A, L)
+        assert np.array_equal(A, ref[0]) and L == ref[1], fz
+
+
+def test_transform_path_is_refused_where_not_built(ftr):
+    ctx = ftr.Context((64, 96, 64), (-1, -1, -1, 1, 1, 1))     # no plane kernels for 64 x 96
+    assert ctx.transform_path() == 0
+    with pytest.raises(ftr.FtrError):
+        ctx.set_transform_path(1)
+    ctx.close()
+
+
 def test_plan_rejects_tiles_that_do_not_divide_the_grid(ftr):
     c = G.CASES["human_aniso"]          # 48 x 96 x 48: 32 does not divide n_z
     ctx = ftr.Context(c["grid"], c["bbox"])
@@ -66,14 +97,21 @@ def test_autotune_picks_a_fitting_plan_and_caches_it(ftr):
     c = G.CASES["human128"]
     a = ftr.Context(c["grid"], c["bbox"])
     rep = a.autotune()
+    full = a.tune_report
+    path = a.transform_path()
+    assert full[12] > 0 and full[13] > 0                          # both chains timed
+    assert path == int(full[14]) == (1 if full[13] < full[12] else 0)
     plan = a.plan()
     assert rep.shape == (3, 4) and (rep[:, 1] > 0).all()       # F = 16 always fits and is timed
     for p, f in enumerate(plan):
+        if p == 1 and path == 1:
+            continue                      # the fused path's z pass has its own tile height
         col = (8, 16, 32, -16).index(f)
         assert rep[p, col] > 0 and rep[p, col] == rep[p][rep[p] > 0].min()
     b = ftr.Context(c["grid"], c["bbox"])
     rep_b = b.autotune()
     assert b.plan() == plan and not rep_b.any()                   # from the cache, untimed
+    assert b.transform_path() == path
     # the tuned context still reconstructs the same field
     P, N, W, _ = G.case_inputs("human128")
     b.reset()
@@ -82,5 +120,5 @@ def test_autotune_picks_a_fitting_plan_and_caches_it(ftr):
     A = b.field_A()
     a.close()
     b.close()
-    ref, _ = _field(ftr, "human128", (16, 16, 16))
+    ref, _ = _field(ftr, "human128", (16, 16, 16), path)
     assert np.array_equal(A, ref)

@@ -102,3 +102,31 @@ def test_graph_frame_matches_separate_calls(ftr, prec):
     for v, t in got:
         assert np.array_equal(v, ref["vertices"])
         assert np.array_equal(t, ref["tris"])
+
+
+@pytest.mark.parametrize("prec,which", [(1, 0), (0, 1)])
+def test_a_timed_out_wait_is_reported_and_the_context_recovers(ftr, prec, which):
+    """A bounded device wait that gives up sets a flag that the next waiting
+    call turns into FTR_ETIMEOUT.  The flag is raised from the host here (no
+    GPU wait is made to run out): ftr_solve reports FTR_ETIMEOUT once, clears
+    the flag, and the next frame on the same context is right again."""
+    name = "sphere64"
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    ctx = ftr.Context(c["grid"], c["bbox"], precision=prec)
+    ctx.reset()
+    ctx.splat(P, N, W)
+    L0 = ctx.solve()
+    ftr.ftr_debug_raise_wait_flag(ctx.h, which)
+    ctx.reset()
+    ctx.splat(P, N, W)
+    with pytest.raises(ftr.FtrError) as e:
+        ctx.solve()
+    assert e.value.code == ftr.FTR_ETIMEOUT
+    ctx.reset()
+    ctx.splat(P, N, W)
+    assert ctx.solve() == L0
+    if prec == 0:
+        with pytest.raises(ftr.FtrError):
+            ftr.ftr_debug_raise_wait_flag(ctx.h, 0)       # an FP32 context has no tensor-core flag
+    ctx.close()
