@@ -64,6 +64,9 @@ def parse_args():
                     help="lines per CTA of the y, z, inverse-y passes, e.g. 16,8,16 (default: autotune)")
     ap.add_argument("--path", type=int, choices=[0, 1], default=None,
                     help="transform path: 0 five axis passes, 1 plane-fused (default: autotuned)")
+    ap.add_argument("--precision-only", action="store_true",
+                    help="run only the split-precision leg (for profiling its kernels)")
+    ap.add_argument("--precision-grids", default="256,384", help="grids of the split-precision leg, e.g. 256")
     ap.add_argument("--no-oracle-error", action="store_true",
                     help="skip the FP64 oracle frames (error of the timed frame and of the precision variants)")
     return ap.parse_args()
@@ -798,6 +801,9 @@ def run_multi(args, rank, dev, plain_frame=None):
         return {"frames": r["frames"], "frames_per_s": round(r["frames_per_s"], 1),
                 "p50_ms": round(r["p50_ms"], 3), "p99_ms": round(r["p99_ms"], 3), "max_ms": round(r["max_ms"], 3),
                 "queue_p99_ms": round(r["queue_p99_ms"], 3),
+                "host_submit_ms": {k: round(v, 3) for k, v in r["host_submit_ms"].items()},
+                "host_finish_ms": {k: round(v, 3) for k, v in r["host_finish_ms"].items()},
+                "slowest": r["slowest"],
                 "per_grid": {g: {k: round(v, 3) if isinstance(v, float) else v for k, v in d.items()}
                              for g, d in r["per_grid"].items()}}
     srv = serve.Server(hbm_budget_bytes=120 * (1 << 30))
@@ -886,7 +892,7 @@ def run_precision(args, rank, dev, fr256, oracle=None):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     steps = max(10, min(args.steps, 30))
     out = {}
-    for gname in ("human256", "human384"):
+    for gname in [f"human{int(v)}" for v in args.precision_grids.split(",")]:
         cfg = frame_config(gname)
         grid, box = cfg["grid_n"], cfg["bbox"]
         fr = fr256 if gname == "human256" else human_frame(seed=args.seed + rank, K=cfg["K"], ring=cfg["ring"],
@@ -1074,6 +1080,11 @@ def run_table1(args, rank, dev, fr, flush):
             stream = torch.cuda.Stream(device=dev)
             ctx = ftr.Context(grid, box, stream=stream.cuda_stream, splat_mode=mode)
             ctx.autotune()
+            if name == "simple":
+                rep = ctx.tune_report
+                row["transform_path"] = {"kept": "plane-fused" if ctx.transform_path() == 1 else "five axis passes",
+                                         "five_pass_us": round(float(rep[12]), 2),
+                                         "plane_fused_us": round(float(rep[13]), 2)}
 
             def frame():
                 ctx.reset()
@@ -1526,6 +1537,13 @@ def main():
             dist.init_process_group("gloo")
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.precision_only:
+        import torch
+        from paper_1712_03084_gb300 import build as pbuild
+        pbuild.build()
+        torch.cuda.set_device(local_rank)
+        _, fr = make_frame(args.seed + rank)
+        line = run_precision(args, rank, torch.device("cuda", local_rank), fr, None)
     else:
         line = run_ours(args, rank, world, local_rank)
     if world > 1:

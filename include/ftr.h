@@ -88,7 +88,8 @@ void ftr_default_params(ftr_params* p);
  * foreground object's bounding box", padded by the caller against circular
  * convolution).  grid_n[3] = (n_x, n_y, n_z); bbox[6] = (min x, min y, min z,
  * max x, max y, max z) in world units, max > min.  p may be NULL (defaults).
- * Allocates every device buffer the grid needs (about 60 bytes per voxel).
+ * Allocates every device buffer the grid needs (about 37 bytes per voxel:
+ * the spectra, the indicator and the brick pool; see ftr_estimate_bytes).
  * Returns FTR_EINVAL for an unsupported grid, FTR_ENOMEM if allocation fails.
  */
 int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ftr_ctx** out);
@@ -109,19 +110,20 @@ int ftr_reset(ftr_ctx* ctx);
 int ftr_splat(ftr_ctx* ctx, const float* points, const float* normals, const float* weights, int64_t n);
 
 typedef struct {
-    const float* points;   /* n x 3 float32, device */
-    const float* normals;  /* n x 3 float32, device */
-    const float* weights;  /* n float32, device, or NULL for W = 1 */
+    const float* points;   /* n x 3 float32, host or device */
+    const float* normals;  /* n x 3 float32, host or device */
+    const float* weights;  /* n float32, host or device, or NULL for W = 1 */
     int64_t n;
 } ftr_point_set;
 
 /*
  * The same as k calls of ftr_splat, one per set (e.g. one per camera), in
  * one kernel launch: the sets' points are appended in set order, exactly as
- * the separate calls would store them.  Every pointer must be device memory
- * (FTR_EINVAL otherwise, before anything is enqueued); 1 <= k <= 16.  The
- * sets are read before the call returns to the stream order (the caller may
- * reuse them after the stream has passed this point).
+ * the separate calls would store them.  1 <= k <= 16.  Device arrays are
+ * read in stream order (reuse them once the stream has passed this call);
+ * host arrays are copied into the context's staging buffer first and the
+ * call then waits for the stream.  FTR_EINVAL for k out of range, n < 0 or
+ * missing points / normals, before anything is enqueued.
  */
 int ftr_splat_sets(ftr_ctx* ctx, const ftr_point_set* sets, int k);
 

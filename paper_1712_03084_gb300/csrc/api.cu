@@ -417,6 +417,14 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         cudaEventCreate(&c->ev_stop[s]);
     }
     cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
+    // every brick empty (slot -1) until the first splat: the x passes read
+    // this table, also when ftr_autotune times the transforms before any frame
+    cudaMemsetAsync(c->d_brick_slot, 0xff, sizeof(int) * c->n_bricks, c->stream);
+    {
+        // no brick touched yet: an empty live z-slab (max brick z = -1)
+        const int meta0[8] = {0, 0, 0, -1, 0, 0, 0, 0};
+        cudaMemcpyAsync(c->d_meta, meta0, sizeof(meta0), cudaMemcpyHostToDevice, c->stream);
+    }
     cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
     cudaMemsetAsync(c->d_kerr, 0, sizeof(int), c->stream);
     c->h_flags[0] = c->h_flags[1] = 0;
@@ -571,12 +579,17 @@ int ftr_splat_sets(ftr_ctx* c, const ftr_point_set* sets, int k) {
     S.k = k;
     S.base = c->n_pts;
     S.off[0] = 0;
+    bool dev[kMaxSets][3];
+    size_t host_floats = 0;
     for (int s = 0; s < k; ++s) {
         const ftr_point_set& p = sets[s];
         if (p.n < 0) return set_err(c, FTR_EINVAL, "ftr_splat_sets: set %d has n < 0", s);
-        if (p.n > 0 && (!is_device_ptr(p.points) || !is_device_ptr(p.normals) ||
-                        (p.weights && !is_device_ptr(p.weights))))
-            return set_err(c, FTR_EINVAL, "ftr_splat_sets: set %d needs device points, normals (and weights)", s);
+        if (p.n > 0 && (!p.points || !p.normals))
+            return set_err(c, FTR_EINVAL, "ftr_splat_sets: set %d needs points and normals", s);
+        dev[s][0] = p.n == 0 || is_device_ptr(p.points);
+        dev[s][1] = p.n == 0 || is_device_ptr(p.normals);
+        dev[s][2] = p.n == 0 || !p.weights || is_device_ptr(p.weights);
+        host_floats += (size_t)p.n * ((dev[s][0] ? 0 : 3) + (dev[s][1] ? 0 : 3) + (dev[s][2] ? 0 : 1));
         S.pts[s] = p.points;
         S.nrm[s] = p.normals;
         S.w[s] = p.weights;
@@ -587,12 +600,36 @@ int ftr_splat_sets(ftr_ctx* c, const ftr_point_set* sets, int k) {
     if (c->n_pts + n > (int64_t)0x3fffffff) return set_err(c, FTR_EINVAL, "ftr_splat_sets: too many points per frame");
     cudaError_t e;
     if ((e = grow_points(c, c->n_pts + n)) != cudaSuccess) return cuda_fail(c, e, "ftr_splat_sets: point store");
+    // host arrays: copied into the staging buffer, then one launch for all sets
+    if (host_floats > 0) {
+        if ((e = ensure_stage(c, &c->d_stage, &c->stage_cap, sizeof(float) * host_floats)) != cudaSuccess)
+            return cuda_fail(c, e, "ftr_splat_sets: staging");
+        float* st = (float*)c->d_stage;
+        for (int s = 0; s < k; ++s) {
+            const int64_t m = S.off[s + 1] - S.off[s];
+            const float* src[3] = {S.pts[s], S.nrm[s], S.w[s]};
+            const int width[3] = {3, 3, 1};
+            for (int a = 0; a < 3; ++a) {
+                if (dev[s][a]) continue;
+                if ((e = cudaMemcpyAsync(st, src[a], sizeof(float) * width[a] * m, cudaMemcpyHostToDevice,
+                                         c->stream)) != cudaSuccess)
+                    return cuda_fail(c, e, "ftr_splat_sets: copy");
+                if (a == 0) S.pts[s] = st;
+                if (a == 1) S.nrm[s] = st;
+                if (a == 2) S.w[s] = st;
+                st += width[a] * m;
+            }
+        }
+    }
     prof_begin(c, ST_INGEST);
     e = launch_ingest_sets(c, S);
     prof_end(c, ST_INGEST);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_splat_sets: ingest");
     c->n_pts += n;
     c->points_in += n;
+    // the staging buffer is reused by the next call: keep host-staged calls ordered
+    if (host_floats > 0 && (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "ftr_splat_sets");
     return FTR_OK;
 }
 

@@ -387,7 +387,7 @@ __device__ __forceinline__ float fix_to_float(long long v) {
     return neg ? -f : f;
 }
 
-constexpr int kStage = 128;       // point records staged in shared memory per batch
+constexpr int kStage = kAccThreads;   // point records staged in shared memory per batch (one per thread)
 
 // Fixed-point contribution round(v * 2^40) = hi 2^20 + lo with two float to
 // int conversions: hi = round(v 2^20); r = v - hi 2^-20 is exact (Sterbenz,

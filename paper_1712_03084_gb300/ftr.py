@@ -231,7 +231,8 @@ def ftr_splat(ctx, points, normals, weights=None):
 
 
 def ftr_splat_sets(ctx, sets):
-    """sets: list of (points, normals, weights-or-None) device tensors; one ingest launch."""
+    """sets: list of (points, normals, weights-or-None) arrays or tensors (host
+    or device); one ingest launch."""
     arr = (ftr_point_set * len(sets))()
     for i, (p, n, w) in enumerate(sets):
         arr[i].points = _ptr(p, np.float32)

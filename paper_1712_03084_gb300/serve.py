@@ -392,6 +392,7 @@ class Server:
         pending_join = sorted((s for s in everyone if s not in self.sessions), key=lambda s: s.start_s)
         self.events = []
         lat, qwait, grid_of, done_frames, meshes = [], [], [], 0, {}
+        host_submit, host_finish, worst = [], [], []
         dropped = 0
         nxt = 0
         pending = len(arrivals)
@@ -414,19 +415,25 @@ class Server:
             for s in list(self.sessions):
                 for sl in s.slots:
                     if sl.busy and sl.ready():
+                        tf = time.perf_counter()
                         nv, nt = sl.finish()
+                        host_finish.append(time.perf_counter() - tf)
                         ta, td, k = sl.tag
                         t_end = time.perf_counter() - t0
                         lat.append(t_end - ta)
                         qwait.append(td - ta)
                         grid_of.append(s.grid_n[0])
+                        worst.append((t_end - ta, s.sid, k, round(1e3 * ta, 3), round(1e3 * (td - ta), 3),
+                                      round(1e3 * (t_end - td), 3)))
                         done_frames += 1
                         pending -= 1
                         if keep_meshes is not None and (s.sid, k) in keep_meshes:
                             meshes[(s.sid, k)] = sl.mesh()
                     if not sl.busy and s.queue:
                         ta, k = s.queue.pop(0)
-                        sl.submit(s.frames[k % len(s.frames)], tag=(ta, time.perf_counter() - t0, k))
+                        ts = time.perf_counter()
+                        sl.submit(s.frames[k % len(s.frames)], tag=(ta, ts - t0, k))
+                        host_submit.append(time.perf_counter() - ts)
                 # departure: past stop_s with nothing queued or in flight
                 if (s.stop_s is not None and now >= s.stop_s and not s.queue
                         and not any(sl.busy for sl in s.slots)):
@@ -459,6 +466,11 @@ class Server:
                 "max_ms": float(lat_ms.max()) if len(lat_ms) else float("nan"),
                 "mean_ms": float(lat_ms.mean()) if len(lat_ms) else float("nan"),
                 "queue_p99_ms": pct(q_ms, 99), "per_grid": per_grid,
+                "host_submit_ms": {"p50": pct(np.array(host_submit) * 1e3, 50), "p99": pct(np.array(host_submit) * 1e3, 99),
+                                   "max": float(np.max(host_submit) * 1e3) if host_submit else float("nan")},
+                "host_finish_ms": {"p50": pct(np.array(host_finish) * 1e3, 50), "p99": pct(np.array(host_finish) * 1e3, 99),
+                                   "max": float(np.max(host_finish) * 1e3) if host_finish else float("nan")},
+                "slowest": [list(w[1:]) for w in sorted(worst, reverse=True)[:5]],
                 "sessions": len(self.sessions), "rejected": list(self.rejected),
                 "not_served": dropped, "events": list(self.events),
                 "hbm_bytes": self.used, "meshes": meshes}

@@ -434,7 +434,7 @@ def test_inside_mask_is_the_binarised_volume(ftr, name):
 def test_point_sets_in_one_launch_equal_separate_calls(ftr):
     """ftr_splat_sets (every camera's points ingested by one launch) stores
     exactly what one ftr_splat call per camera stores: the same V, A, L and
-    the same counts; non-device sets are refused before anything runs."""
+    the same counts, with device sets and with host (staged) sets."""
     import torch
     name = "human96"
     c = G.CASES[name]
@@ -444,22 +444,24 @@ def test_point_sets_in_one_launch_equal_separate_calls(ftr):
     cuts = [0, 5000, 5001, 17000, len(P)]
     sets = [(Pd[a:b], Nd[a:b], Wd[a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
     sets.append((Pd[:0], Nd[:0], None))                    # an empty set is allowed
+    host_sets = [(P[a:b], N[a:b], W[a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
     res = []
-    for one_launch in (True, False):
+    for mode in ("one launch", "host sets", "separate calls"):
         ctx = ftr.Context(c["grid"], c["bbox"])
         ctx.reset()
         l0 = ctx.launch_count()
-        if one_launch:
+        if mode == "one launch":
             ctx.splat_sets(sets)
+            assert ctx.launch_count() - l0 == 1
+        elif mode == "host sets":
+            ctx.splat_sets(host_sets)
             assert ctx.launch_count() - l0 == 1
         else:
             for p, n, w in sets:
                 ctx.splat(p, n, w)
         L = ctx.solve()
         res.append((ctx.field_V(), ctx.field_A(), L, ctx.stats()))
-        if one_launch:
-            with pytest.raises(ftr.FtrError):
-                ctx.splat_sets([(torch.from_numpy(P[:10]), torch.from_numpy(N[:10]), None)])
         ctx.close()
-    (V1, A1, L1, s1), (V2, A2, L2, s2) = res
-    assert np.array_equal(V1, V2) and np.array_equal(A1, A2) and L1 == L2 and s1 == s2
+    for V2, A2, L2, s2 in res[1:]:
+        V1, A1, L1, s1 = res[0]
+        assert np.array_equal(V1, V2) and np.array_equal(A1, A2) and L1 == L2 and s1 == s2

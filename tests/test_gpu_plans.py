@@ -122,3 +122,24 @@ def test_autotune_picks_a_fitting_plan_and_caches_it(ftr):
     b.close()
     ref, _ = _field(ftr, "human128", (16, 16, 16), path)
     assert np.array_equal(A, ref)
+
+
+def test_autotune_before_the_first_frame_on_reused_memory(ftr):
+    """A context timed by ftr_autotune before it has splatted anything (its
+    brick table never written by a frame) runs every transform kernel on its
+    initial state; on memory another context has just used and released
+    this must neither read outside its buffers nor change the results."""
+    c = G.CASES["human96"]
+    P, N, W, _ = G.case_inputs("human96")
+    ref, _ = _field(ftr, "human96")          # leaves its memory to the allocator
+    ctx = ftr.Context(c["grid"], c["bbox"])
+    ctx.autotune()
+    plan, path = ctx.plan(), ctx.transform_path()
+    ctx.reset()
+    ctx.splat(P, N, W)
+    L = ctx.solve()
+    A = ctx.field_A()
+    ctx.close()
+    ref_p, ref_pL = _field(ftr, "human96", plan, path)
+    assert np.array_equal(A, ref_p) and L == ref_pL
+    assert G.rel_l2(A, ref) <= 2e-6
