@@ -62,8 +62,8 @@ def parse_args():
     ap.add_argument("--no-precision", action="store_true", help="skip the split-precision configuration")
     ap.add_argument("--plan", default=None,
                     help="lines per CTA of the y, z, inverse-y passes, e.g. 16,8,16 (default: autotune)")
-    ap.add_argument("--path", type=int, choices=[0, 1], default=None,
-                    help="transform path: 0 five axis passes, 1 plane-fused (default: autotuned)")
+    ap.add_argument("--path", type=int, choices=[0, 1, 2], default=None,
+                    help="transform path: 0 five axis passes, 1 plane-fused, 2 persistent y+z (default: autotuned)")
     ap.add_argument("--precision-only", action="store_true",
                     help="run only the split-precision leg (for profiling its kernels)")
     ap.add_argument("--precision-grids", default="256,384", help="grids of the split-precision leg, e.g. 256")
@@ -170,6 +170,7 @@ STAGE_SOURCES = {
     "fft_x_inv": ["fft_ix.cu", "fft_common.cuh"],
     "fft_xy_fwd": ["fft_fused.cuh", "fft_common.cuh"],
     "fft_yx_inv": ["fft_fused.cuh", "fft_common.cuh"],
+    "fft_yz_fwd_filter_inv": ["fft_yz.cu", "fft_common.cuh"],
     "splat_accum": ["splat.cu"],
     "mc_count": ["mc.cu"],
     "mc_emit": ["mc.cu"],
@@ -227,6 +228,8 @@ def algorithmic_bytes(stage, info, grid, k_views):
         return c8 * mh_full + 4 * M
     if stage == "fft_z_filter_inv":
         return 2 * c8 * mh_live + c8 * mh_full
+    if stage == "fft_yz_fwd_filter_inv":   # three x-transformed fields of the live planes read, A^ written
+        return 3 * c8 * mh_live + c8 * mh_full
     if stage == "fft_y_inv":
         return 2 * c8 * mh_full
     if stage == "fft_x_inv":
@@ -515,10 +518,10 @@ def run_ours(args, rank, world, local_rank):
     # slab (cached per grid for the process), then the warm-up proper
     if args.plan:
         ctx.set_plan(tuple(int(v) for v in args.plan.split(",")))
-        tune_us, chain_us = np.zeros((3, 4)), (0.0, 0.0)
+        tune_us, chain_us = np.zeros((3, 4)), (0.0, 0.0, 0.0)
     else:
         tune_us = ctx.autotune()
-        chain_us = (ctx.tune_report[12], ctx.tune_report[13])
+        chain_us = (ctx.tune_report[12], ctx.tune_report[13], ctx.tune_report[15])
     if args.path is not None:
         ctx.set_transform_path(args.path)
     plan = ctx.plan()
@@ -680,10 +683,11 @@ def run_ours(args, rank, world, local_rank):
                    "grid": list(grid), "points": int(info["points_in"]), "vertices": int(info["n_vertices"]),
                    "triangles": int(info["n_tris"]), "cameras": K, "parallelism": f"replicas{world}",
                    "plan": {"lines_per_cta_y_z_iy": list(plan),
-                            "transform_path": "plane-fused" if path == 1 else "five axis passes",
+                            "transform_path": PATH_NAMES[path],
                             "autotune_us_per_launch": [[round(float(v), 2) for v in row] for row in tune_us],
                             "autotune_chain_us": {"five_pass": round(float(chain_us[0]), 2),
-                                                  "plane_fused": round(float(chain_us[1]), 2)}},
+                                                  "plane_fused": round(float(chain_us[1]), 2),
+                                                  "persistent_y_z": round(float(chain_us[2]), 2)}},
                    "l2": "flushed between steps (256 MiB write, untimed)"},
         "latency_ms": {"p50": round(float(np.percentile(step_ms_sorted, 50)), 4),
                        "p99": round(float(np.percentile(step_ms_sorted, 99)), 4)},
@@ -876,7 +880,9 @@ def run_multi(args, rank, dev, plain_frame=None):
 
 
 PREC_NAMES = ((0, "fp32"), (1, "bf16x3"), (2, "fp16x3"))
-FFT_STAGES = ("fft_x_fwd", "fft_y_fwd", "fft_xy_fwd", "fft_z_filter_inv", "fft_y_inv", "fft_x_inv", "fft_yx_inv")
+PATH_NAMES = {0: "five axis passes", 1: "plane-fused", 2: "five passes, y and z passes in one persistent kernel"}
+FFT_STAGES = ("fft_x_fwd", "fft_y_fwd", "fft_xy_fwd", "fft_z_filter_inv", "fft_yz_fwd_filter_inv", "fft_y_inv",
+              "fft_x_inv", "fft_yx_inv")
 SWEEP_LOAD = (0.25, 0.5, 0.75, 0.9)
 SWEEP_SECONDS = 1.0
 
@@ -1082,9 +1088,10 @@ def run_table1(args, rank, dev, fr, flush):
             ctx.autotune()
             if name == "simple":
                 rep = ctx.tune_report
-                row["transform_path"] = {"kept": "plane-fused" if ctx.transform_path() == 1 else "five axis passes",
+                row["transform_path"] = {"kept": PATH_NAMES[ctx.transform_path()],
                                          "five_pass_us": round(float(rep[12]), 2),
-                                         "plane_fused_us": round(float(rep[13]), 2)}
+                                         "plane_fused_us": round(float(rep[13]), 2),
+                                         "persistent_y_z_us": round(float(rep[15]), 2)}
 
             def frame():
                 ctx.reset()

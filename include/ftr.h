@@ -301,8 +301,9 @@ int64_t ftr_device_bytes(const ftr_ctx* ctx);
  * inputs (no staging), at `precision` (an FTR_PREC_* code): the same
  * accounting as ftr_device_bytes, applied to the capacities the library's
  * growth rules give at those sizes.  Allocates nothing and needs no device,
- * so a server can refuse a session before creating anything for it.
- * Returns -1 for an unsupported grid or a negative size. */
+ * so a server can refuse a session before creating anything for it.  The
+ * ring of transform path 2 (about 40 MB, only while that path is in use) is
+ * not included.  Returns -1 for an unsupported grid or a negative size. */
 int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pixels, int64_t vertices,
                            int64_t tris, int precision);
 
@@ -328,9 +329,9 @@ int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pi
  * faster path (cached with the plan).  report (nullable): 16 floats,
  * [0..11] microseconds per launch of F = 8, 16, 32, -16 for the y, z and
  * inverse-y passes of the five-pass path (0 = not timed: cached or not a
- * candidate), [12] and [13] microseconds of the five-pass and of the
- * plane-fused chain (0: not timed), [14] the path kept.  Waits for the
- * stream.  Split precision contexts keep F = 16 and the five passes (their
+ * candidate), [12], [13] and [15] microseconds of the five-pass, the
+ * plane-fused and the persistent y+z chain (0: not timed), [14] the path
+ * kept.  Waits for the stream.  Split precision contexts keep F = 16 and the five passes (their
  * passes have no variants).
  */
 int ftr_autotune(ftr_ctx* ctx, float* report);
@@ -344,8 +345,13 @@ int ftr_get_plan(const ftr_ctx* ctx, int* plan);
 int ftr_set_plan(ftr_ctx* ctx, const int* plan);
 
 /*
- * Transform path of the FP32 transforms: 1 = plane-fused, 0 = five axis
- * passes.  The plane-fused path runs the forward x and y transforms of a
+ * Transform path of the FP32 transforms: 0 = five axis passes, 1 =
+ * plane-fused, 2 = the five passes with the forward y pass and the z pass
+ * (filter, inverse z) in one persistent kernel whose y tiles hand each k_x
+ * plane to its z tiles through a ring of k_x planes that stays in L2
+ * (about 40 MB; grids with n_y = n_z in {64, 96, 128, 192, 256, 384}; the
+ * per-line arithmetic of path 0 with 16-line y and z tiles, equal to it
+ * within rounding).  The plane-fused path runs the forward x and y transforms of a
  * z-plane in one kernel (a thread-block cluster per plane: each CTA
  * transforms its rows along x into its shared memory, then its k_x columns
  * along y, reading every y from the cluster's shared memory), the z pass with
@@ -361,8 +367,12 @@ int ftr_set_plan(ftr_ctx* ctx, const int* plan);
  * The z-pass plan (plan[1]) applies to both paths; plan[0] and plan[2] only
  * to the five-pass path.  The paths agree within rounding (A rel-L2 ~1e-7),
  * not bit for bit (the x transforms pair other rows).  Set: FTR_EINVAL if 1
- * is asked where the fused kernels do not exist, FTR_ESTATE while a frame is
- * pending; the next solve uses it.  Get: the path (or FTR_EINVAL).
+ * is asked where the fused kernels do not exist (2 likewise), FTR_ESTATE
+ * while a frame is pending; the next solve uses it.  The ring of path 2 is
+ * allocated when the path is set (FTR_ENOMEM if it does not fit) and freed
+ * when another is set; ftr_autotune allocates it to time the path and frees
+ * it unless the path is kept.  ftr_device_bytes counts it while it exists;
+ * ftr_estimate_bytes does not.  Get: the path (or FTR_EINVAL).
  */
 int ftr_get_transform_path(const ftr_ctx* ctx);
 int ftr_set_transform_path(ftr_ctx* ctx, int fused);

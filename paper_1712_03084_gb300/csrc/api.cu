@@ -82,7 +82,7 @@ namespace {
 const char* kStageNames[ST_COUNT] = {"ingest", "splat_bin", "splat_accum", "fft_x_fwd", "fft_y_fwd",
                                      "fft_z_filter_inv", "fft_y_inv", "fft_x_inv", "level", "mc_count",
                                      "mc_scan", "mc_emit", "mc_tris", "texture", "fft_xy_fwd",
-                                     "fft_yx_inv"};
+                                     "fft_yx_inv", "fft_yz_fwd_filter_inv"};
 
 bool supported_n(int n) {
     switch (n) {
@@ -107,7 +107,8 @@ cudaError_t ensure_device_ready(int dev) {
         (e = fft_fx_init(w96)) != cudaSuccess || (e = fft_fy_init(w96)) != cudaSuccess ||
         (e = fft_fz_init(w96)) != cudaSuccess || (e = fft_iy_init(w96)) != cudaSuccess ||
         (e = fft_ix_init(w96)) != cudaSuccess || (e = fft_fused_a_init(w96)) != cudaSuccess ||
-        (e = fft_fused_b_init(w96)) != cudaSuccess || (e = fft_plane_init(w96)) != cudaSuccess) {
+        (e = fft_fused_b_init(w96)) != cudaSuccess || (e = fft_plane_init(w96)) != cudaSuccess ||
+        (e = fft_yz_init(w96)) != cudaSuccess) {
         cudaFree(w96);
         return e;
     }
@@ -244,6 +245,8 @@ void free_all(ftr_ctx* c) {
     if (c->h_raw_total) cudaFreeHost(c->h_raw_total);
     dfree(c->d_tc_err);
     dfree(c->d_kerr);
+    dfree(c->d_ring);
+    dfree(c->d_yz_sync);
     dfree(c->d_level);
     dfree(c->d_levelf);
     dfree(c->d_level_part);
@@ -409,6 +412,9 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
             return FTR_ECUDA;
         }
     }
+    // the persistent y+z pass where it is built for this grid; its ring is
+    // allocated only while that path is in use (or being timed)
+    c->yz_ok = prm.precision == FTR_PREC_FP32 && yz_supported(c->g.n);
     // the plane-fused transforms where they are built for this grid and fit
     c->fused_ok = prm.precision == FTR_PREC_FP32 && fused_available(c);
     c->fused = 0;         // five axis passes until ftr_autotune times both paths
@@ -676,7 +682,25 @@ namespace {
 // (Sec. III-B): three plane-fused kernels, or five axis passes.
 cudaError_t launch_transforms(ftr_ctx* c) {
     cudaError_t e;
-    if (c->fused && c->p.precision == FTR_PREC_FP32) {
+    if (c->fused == 2 && c->p.precision == FTR_PREC_FP32) {
+        prof_begin(c, ST_FX);
+        e = launch_fx(c);
+        prof_end(c, ST_FX);
+        if (e != cudaSuccess) return e;
+        prof_begin(c, ST_FYZ);
+        e = launch_fyz(c);
+        prof_end(c, ST_FYZ);
+        if (e != cudaSuccess) return e;
+        prof_begin(c, ST_IY);
+        e = launch_iy(c);
+        prof_end(c, ST_IY);
+        if (e != cudaSuccess) return e;
+        prof_begin(c, ST_IX);
+        e = launch_ix(c);
+        prof_end(c, ST_IX);
+        return e;
+    }
+    if (c->fused == 1 && c->p.precision == FTR_PREC_FP32) {
         prof_begin(c, ST_FXY);
         e = launch_fxy(c);
         prof_end(c, ST_FXY);
@@ -1290,11 +1314,43 @@ int ftr_get_transform_path(const ftr_ctx* c) {
     return c->fused;
 }
 
+namespace {
+// The ring and counters of the persistent y+z pass, allocated on first use.
+cudaError_t ensure_yz_ring(ftr_ctx* c) {
+    if (c->d_ring && c->d_yz_sync) return cudaSuccess;
+    cudaError_t e;
+    if ((e = dalloc(&c->d_ring, yz_ring_elems(c->g.n))) != cudaSuccess ||
+        (e = dalloc(&c->d_yz_sync, (size_t)yz_sync_ints(c->g.n))) != cudaSuccess) {
+        dfree(c->d_ring);
+        dfree(c->d_yz_sync);
+        cudaGetLastError();
+    }
+    return e;
+}
+
+// Free them once another path is chosen (the context's graph is rebuilt
+// before its next launch, so no captured launch refers to them).
+void release_yz_ring(ftr_ctx* c) {
+    if (!c->d_ring && !c->d_yz_sync) return;
+    cudaStreamSynchronize(c->stream);
+    dfree(c->d_ring);
+    dfree(c->d_yz_sync);
+}
+}  // namespace
+
 int ftr_set_transform_path(ftr_ctx* c, int fused) {
-    if (!c || (fused != 0 && fused != 1)) return FTR_EINVAL;
-    if (fused && !c->fused_ok)
+    if (!c || fused < 0 || fused > 2) return FTR_EINVAL;
+    if (fused == 1 && !c->fused_ok)
         return set_err(c, FTR_EINVAL, "ftr_set_transform_path: no plane-fused kernels for this grid or precision");
+    if (fused == 2 && !c->yz_ok)
+        return set_err(c, FTR_EINVAL, "ftr_set_transform_path: no persistent y+z kernel for this grid or precision");
     if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_set_transform_path: a frame is pending");
+    if (fused == 2) {
+        if (ensure_yz_ring(c) != cudaSuccess)
+            return set_err(c, FTR_ENOMEM, "ftr_set_transform_path: no device memory for the y+z ring");
+    } else {
+        release_yz_ring(c);
+    }
     c->fused = fused;
     c->graph_valid = false;
     c->solved = false;
@@ -1314,7 +1370,10 @@ int ftr_autotune(ftr_ctx* c, float* report) {
         auto it = g_plans.find(key);
         if (it != g_plans.end()) {
             for (int i = 0; i < 3; ++i) c->plan_lines[i] = it->second[i];
-            c->fused = it->second[3] && c->fused_ok ? 1 : 0;
+            int pth = it->second[3];
+            if (pth == 2 && !(c->yz_ok && ensure_yz_ring(c) == cudaSuccess)) pth = 0;
+            c->fused = (pth == 1 && c->fused_ok) || pth == 2 ? pth : 0;
+            if (c->fused != 2) release_yz_ring(c);
             c->graph_valid = false;
             return FTR_OK;
         }
@@ -1403,15 +1462,30 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     for (int i = 0; i < 3; ++i) c->plan_lines[i] = best[i];
     const float five_us = time_us([&]() { return launch_transforms(c); });
     if (report) report[12] = five_us;
+    float best_chain = five_us;
     if (c->fused_ok) {
         c->fused = 1;
         c->plan_lines[1] = best_fz2;
         const float fused_us = time_us([&]() { return launch_transforms(c); });
         if (report) report[13] = fused_us;
-        if (fused_us > 0.f && (five_us < 0.f || fused_us < five_us)) path = 1;
+        if (fused_us > 0.f && (best_chain < 0.f || fused_us < best_chain)) {
+            path = 1;
+            best_chain = fused_us;
+        }
+        c->plan_lines[1] = best[1];
+    }
+    if (c->yz_ok && ensure_yz_ring(c) == cudaSuccess) {
+        c->fused = 2;
+        const float yz_us = time_us([&]() { return launch_transforms(c); });
+        if (report) report[15] = yz_us;
+        if (yz_us > 0.f && (best_chain < 0.f || yz_us < best_chain)) {
+            path = 2;
+            best_chain = yz_us;
+        }
     }
     if (path == 1) best[1] = best_fz2;
     c->fused = path;
+    if (path != 2) release_yz_ring(c);
     for (int i = 0; i < 3; ++i) c->plan_lines[i] = best[i];
     if (report) report[14] = (float)path;
     cudaEventDestroy(t0);
@@ -1433,6 +1507,7 @@ struct Caps {
     int64_t pts = 0, stage = 0, tex_stage = 0, entries = 0, units = 0, heavy = 0, raw = 0, raw_tiles = 0;
     int64_t mc_nodes = 0, verts = 0, tris = 0;
     bool tc = false;
+    bool yz = false;     // the persistent y+z pass's ring and counters
 };
 
 int64_t context_bytes(const int n[3], const Caps& k) {
@@ -1452,6 +1527,7 @@ int64_t context_bytes(const int n[3], const Caps& k) {
     b += 5 * Mh * (int64_t)sizeof(float2) + M * (int64_t)sizeof(float);
     b += (int64_t)(n[0] + n[1] + n[2]) * (int64_t)sizeof(float2);
     if (k.tc) b += (int64_t)tc_table_bytes() + 16;
+    if (k.yz) b += (int64_t)(yz_ring_elems(n) * sizeof(float2)) + (int64_t)yz_sync_ints(n) * (int64_t)sizeof(int);
     b += k.raw * 7 * (int64_t)sizeof(float) + k.raw_tiles * (int64_t)sizeof(int);
     b += (2 * level_blocks + 8) * (int64_t)sizeof(double);
     b += (6 * mc_blocks + 16) * (int64_t)sizeof(int);
@@ -1483,6 +1559,7 @@ int64_t ftr_device_bytes(const ftr_ctx* c) {
     k.verts = c->cap_verts;
     k.tris = c->cap_tris;
     k.tc = c->d_tc_table != nullptr;
+    k.yz = c->d_ring != nullptr;
     return context_bytes(c->g.n, k);
 }
 
@@ -1507,6 +1584,7 @@ int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pi
     k.verts = vertices + vertices / 2 + 1024;
     k.tris = tris + tris / 2 + 1024;
     k.tc = precision != FTR_PREC_FP32;
+    k.yz = false;   // the y+z ring exists only while transform path 2 is in use
     return context_bytes(grid_n, k);
 }
 

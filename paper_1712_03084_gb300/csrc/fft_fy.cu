@@ -18,11 +18,11 @@ namespace {
 // Load line f's elements y = N2 n1 + r (contiguous) and run step 1.
 template <int N, int F>
 __device__ __forceinline__ void load_step1(const float2* __restrict__ src, int r, int f, float2* smem,
-                                           const float2* __restrict__ tw) {
+                                           const float2* __restrict__ tw, uint64_t pol) {
     using X = Xchg<N, F>;
     float2 v[X::N1];
 #pragma unroll
-    for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = src[X::N2 * n1 + r];
+    for (int n1 = 0; n1 < X::N1; ++n1) v[n1] = ld_l2hint(src + X::N2 * n1 + r, pol);
     fft_step1<N, F, -1>(v, f, r, smem, tw);
 }
 
@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
             prefetch_l2(line + 2 * Mh + X::N2 * n1 + r1);
         }
     }
+    const uint64_t pin = l2_evict_first(), pout = l2_evict_last();
     // x component: transform along y and park it (line index fastest)
-    if (r1 < X::N2) load_step1<N, F>(line, r1, f1, smem, tw);
+    if (r1 < X::N2) load_step1<N, F>(line, r1, f1, smem, tw, pin);
     __syncthreads();
     float2 o[X::N2];
     if (i2 < X::N1) fft_step2<N, F, -1>(o, f2, i2, smem);
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
         for (int k2 = 0; k2 < X::N2; ++k2) stash[f2 + (F + 1) * (i2 + X::N1 * k2)] = o[k2];
     }
     // y component: transform, then W = x + j w_y y goes out as field 0
-    if (r1 < X::N2) load_step1<N, F>(line + Mh, r1, f1, smem, tw);
+    if (r1 < X::N2) load_step1<N, F>(line + Mh, r1, f1, smem, tw, pin);
     __syncthreads();
     if (i2 < X::N1) fft_step2<N, F, -1>(o, f2, i2, smem);
     __syncthreads();
@@ -83,16 +84,16 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT, MinCtasF<N, F>::value)
             const int ky = i2 + X::N1 * k2;
             const float wy = (ky == N / 2) ? 0.f : wy_scale * (float)signed_bin(ky, N);
             const float2 w = stash[f2 + (F + 1) * ky];
-            s1[out_base + (size_t)nz * ky] = make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x);
+            st_l2hint(s1 + out_base + (size_t)nz * ky, make_float2(w.x - wy * o[k2].y, w.y + wy * o[k2].x), pout);
         }
     }
     // z component: transform and write as field 1
-    if (r1 < X::N2) load_step1<N, F>(line + 2 * Mh, r1, f1, smem, tw);
+    if (r1 < X::N2) load_step1<N, F>(line + 2 * Mh, r1, f1, smem, tw, pin);
     __syncthreads();
     if (i2 < X::N1) {
         fft_step2<N, F, -1>(o, f2, i2, smem);
 #pragma unroll
-        for (int k2 = 0; k2 < X::N2; ++k2) s1[Mh + out_base + (size_t)nz * (i2 + X::N1 * k2)] = o[k2];
+        for (int k2 = 0; k2 < X::N2; ++k2) st_l2hint(s1 + Mh + out_base + (size_t)nz * (i2 + X::N1 * k2), o[k2], pout);
     }
 }
 

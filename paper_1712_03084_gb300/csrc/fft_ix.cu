@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
     const int y0 = blockIdx.x * kRows;
     const int z = blockIdx.y;
     const int tid = threadIdx.x;
+    const uint64_t pin = l2_evict_first(), pout = l2_evict_last();
     // every load of the staging is issued before the first shared-memory store
     constexpr int kPer = (kRows * NKX + kLines * Xchg<N, kLines>::NT - 1) / (kLines * Xchg<N, kLines>::NT);
     {
@@ -37,7 +38,8 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
         for (int i = 0; i < kPer; ++i) {
             const int k = tid + i * (int)blockDim.x;
             const int row = k & (kRows - 1), kx = k >> 4;
-            st[i] = k < kRows * NKX ? src[(size_t)(y0 + row) + (size_t)ny * (z + (size_t)nz * kx)] : make_float2(0.f, 0.f);
+            st[i] = k < kRows * NKX ? ld_l2hint(src + (size_t)(y0 + row) + (size_t)ny * (z + (size_t)nz * kx), pin)
+                                    : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
@@ -78,8 +80,8 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
         float* rb = A + (size_t)N * ((size_t)(y0 + f2 + kLines) + (size_t)ny * z);
 #pragma unroll
         for (int k2 = 0; k2 < X::N2; ++k2) {
-            ra[i2 + X::N1 * k2] = o[k2].x;
-            rb[i2 + X::N1 * k2] = o[k2].y;
+            st_l2hint(ra + i2 + X::N1 * k2, o[k2].x, pout);
+            st_l2hint(rb + i2 + X::N1 * k2, o[k2].y, pout);
         }
     }
 }

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT)
     const int z0 = blockIdx.x * F;
     const int kx = blockIdx.y;
     const int tid = threadIdx.x;
+    const uint64_t pin = l2_evict_first(), pout = l2_evict_last();
     // step 1: line index fastest (the input is contiguous along z)
     const int f1 = tid % F, j1 = tid / F;
     if (j1 < X::N2) {
@@ -28,7 +29,7 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT)
 #pragma unroll
         for (int n1 = 0; n1 < X::N1; ++n1) {
             const int ky = X::N2 * n1 + j1;
-            v[n1] = src[(size_t)(z0 + f1) + (size_t)nz * ((size_t)ky + (size_t)N * kx)];
+            v[n1] = ld_l2hint(src + (size_t)(z0 + f1) + (size_t)nz * ((size_t)ky + (size_t)N * kx), pin);
         }
         fft_step1<N, F, +1>(v, f1, j1, smem, tw);
     }
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(F * Xchg<N, F>::NT)
         fft_step2<N, F, +1>(o, f2, i2, smem);
         float2* out = dst + (size_t)N * ((size_t)(z0 + f2) + (size_t)nz * kx);
 #pragma unroll
-        for (int k2 = 0; k2 < X::N2; ++k2) out[i2 + X::N1 * k2] = o[k2];
+        for (int k2 = 0; k2 < X::N2; ++k2) st_l2hint(out + i2 + X::N1 * k2, o[k2], pout);
     }
 }
 

@@ -38,6 +38,7 @@ enum Stage {
     ST_TEXTURE,
     ST_FXY,           // plane-fused forward x + y
     ST_IYX,           // plane-fused inverse y + x
+    ST_FYZ,           // forward y + z pass (filter, inverse z) through an L2 ring
     ST_COUNT
 };
 
@@ -134,8 +135,12 @@ struct ftr_ctx {
     float2* d_tw[3] = {nullptr, nullptr, nullptr};   // W_n^m per axis
     int plan_lines[3] = {16, 16, 16};      // lines per CTA of the y, z and inverse-y passes (-16: y pass
                                            // with bulk-copied tiles)
-    int fused = 0;                         // transform path: 1 plane-fused (x+y, z, y+x), 0 five axis passes
+    int fused = 0;                         // transform path: 0 five axis passes, 1 plane-fused (x+y, z, y+x),
+                                           // 2 five passes with the y and z passes in one persistent kernel
     bool fused_ok = false;                 // the plane-fused kernels exist for this grid and fit the device
+    bool yz_ok = false;                    // the persistent y+z kernel exists for this grid
+    float2* d_ring = nullptr;              // its ring of k_x planes (2 fields each)
+    int* d_yz_sync = nullptr;              // its ticket and per-k_x tile counters
     int* occ_query = nullptr;              // set: the pass launchers report occupancy instead of launching
     unsigned char* d_tc_table = nullptr;   // split DFT matrices of the tensor-core passes
     int* d_tc_err = nullptr;               // set when a tensor-core completion wait gave up
@@ -286,6 +291,13 @@ bool fused_available(ftr_ctx* c);
 cudaError_t launch_fxy(ftr_ctx* c);
 cudaError_t launch_fz2(ftr_ctx* c);
 cudaError_t launch_iyx(ftr_ctx* c);
+// forward y pass and z pass in one persistent kernel (fft_yz.cu)
+cudaError_t fft_yz_init(const float2* w96);
+bool yz_supported(const int n[3]);
+int yz_ring_planes(const int n[3]);
+size_t yz_ring_elems(const int n[3]);
+int yz_sync_ints(const int n[3]);
+cudaError_t launch_fyz(ftr_ctx* c);
 cudaError_t launch_level(ftr_ctx* c);
 // raw reconstruction (raw.cu): depth maps -> compacted points, normals, W
 struct RawParams {

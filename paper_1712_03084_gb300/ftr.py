@@ -414,8 +414,8 @@ def ftr_autotune(ctx):
     """Time the tile plans and the transform paths; returns the 16-float
     report of include/ftr.h ([0..11]: microseconds per launch, rows y, z,
     inverse-y passes x columns 8, 16, 32 lines per CTA and the bulk-copied
-    16-line y pass; [12], [13]: the five-pass and plane-fused chains; [14]:
-    the path kept; 0 = not timed)."""
+    16-line y pass; [12], [13], [15]: the five-pass, plane-fused and
+    persistent y+z chains; [14]: the path kept; 0 = not timed)."""
     rep = np.zeros(16, np.float32)
     _check(load().ftr_autotune(ctx, rep.ctypes.data), ctx)
     return rep
@@ -433,7 +433,8 @@ def ftr_set_plan(ctx, plan):
 
 
 def ftr_get_transform_path(ctx):
-    """1: plane-fused transforms, 0: five axis passes."""
+    """0: five axis passes, 1: plane-fused, 2: five passes with the y and z
+    passes in one persistent kernel."""
     v = load().ftr_get_transform_path(ctx)
     if v < 0:
         _check(v, ctx)

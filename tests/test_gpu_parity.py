@@ -83,6 +83,37 @@ def test_both_transform_paths_match_the_oracle(ftr, name):
     assert G.rel_l2(got[1], got[0]) <= 2e-6
 
 
+@pytest.mark.parametrize("name", ["sphere64", "human96", "human128"])
+def test_persistent_y_z_pass_equals_the_five_passes(ftr, name):
+    """Transform path 2 (the y pass and the z pass in one persistent kernel,
+    the intermediate handed over through an L2 ring of k_x planes) runs the
+    per-line arithmetic of the five passes with 16-line tiles: A and L agree
+    with them to rounding (the two kernels are compiled separately, so the
+    last bits may differ) and with the oracle within its bars, also over two
+    frames in a row (the ring and the counters are reused); both frames of
+    path 2 are bit-identical (the handover order does not change a value)."""
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    res = {}
+    for path in (0, 2):
+        ctx = ftr.Context(c["grid"], c["bbox"])
+        ctx.set_transform_path(path)
+        ctx.set_plan((16, 16, 16))
+        out = []
+        for _ in range(2):
+            ctx.reset()
+            ctx.splat(P, N, W)
+            out.append((ctx.solve(), ctx.field_A()))
+        ctx.close()
+        res[path] = out
+    r = G.oracle_result(name)
+    span = float(r["A"].max() - r["A"].min())
+    for (L0, A0), (L2, A2) in zip(res[0], res[2]):
+        assert G.rel_l2(A2, A0) <= 1e-6 and abs(L2 - L0) / span <= 1e-7
+        assert G.rel_l2(A2, r["A"]) <= 1e-5 and abs(L2 - r["L"]) / span <= 1e-5
+    assert res[2][0][0] == res[2][1][0] and np.array_equal(res[2][0][1], res[2][1][1])
+
+
 @pytest.mark.parametrize("name", ["sphere64", "human96", "human_aniso"])
 def test_marching_cubes_bit_exact_on_oracle_field(ftr, name):
     c = G.CASES[name]

@@ -76,11 +76,31 @@ def test_every_z_plan_is_bit_identical_on_the_fused_path(ftr, name):
 
 
 def test_transform_path_is_refused_where_not_built(ftr):
-    ctx = ftr.Context((64, 96, 64), (-1, -1, -1, 1, 1, 1))     # no plane kernels for 64 x 96
+    ctx = ftr.Context((64, 96, 64), (-1, -1, -1, 1, 1, 1))     # no plane kernels for 64 x 96, n_y != n_z
     assert ctx.transform_path() == 0
-    with pytest.raises(ftr.FtrError):
-        ctx.set_transform_path(1)
+    for path in (1, 2, 3):
+        with pytest.raises(ftr.FtrError):
+            ctx.set_transform_path(path)
     ctx.close()
+
+
+def test_y_z_ring_exists_only_while_its_path_is_in_use(ftr):
+    """Path 2's ring (about 40 MB of k_x planes, all of them on small grids)
+    and its counters are allocated when the path is set and freed when
+    another is; ftr_device_bytes counts them meanwhile."""
+    for grid in ((128, 128, 128), (256, 256, 256)):
+        ctx = ftr.Context(grid, (-1, -1, -1, 1, 1, 1))
+        b0 = ftr.ftr_device_bytes(ctx.h)
+        ctx.set_transform_path(2)
+        nkx = grid[0] // 2 + 1
+        planes = min(nkx, max(4, (40 << 20) // (2 * 8 * grid[1] * grid[2])))
+        assert ftr.ftr_device_bytes(ctx.h) - b0 == planes * 2 * grid[1] * grid[2] * 8 + (1 + 2 * nkx) * 4
+        ctx.set_transform_path(1)
+        assert ftr.ftr_device_bytes(ctx.h) == b0
+        ctx.set_transform_path(2)
+        ctx.set_transform_path(0)
+        assert ftr.ftr_device_bytes(ctx.h) == b0
+        ctx.close()
 
 
 def test_plan_rejects_tiles_that_do_not_divide_the_grid(ftr):
@@ -99,8 +119,9 @@ def test_autotune_picks_a_fitting_plan_and_caches_it(ftr):
     rep = a.autotune()
     full = a.tune_report
     path = a.transform_path()
-    assert full[12] > 0 and full[13] > 0                          # both chains timed
-    assert path == int(full[14]) == (1 if full[13] < full[12] else 0)
+    assert full[12] > 0 and full[13] > 0 and full[15] > 0         # all three chains timed
+    chains = {0: full[12], 1: full[13], 2: full[15]}
+    assert path == int(full[14]) == min(chains, key=chains.get)
     plan = a.plan()
     assert rep.shape == (3, 4) and (rep[:, 1] > 0).all()       # F = 16 always fits and is timed
     for p, f in enumerate(plan):
