@@ -174,6 +174,7 @@ STAGE_SOURCES = {
     "splat_accum": ["splat.cu"],
     "mc_count": ["mc.cu"],
     "mc_emit": ["mc.cu"],
+    "mc_tris": ["mc.cu"],
     "texture": ["texture.cu"],
 }
 
@@ -238,9 +239,12 @@ def algorithmic_bytes(stage, info, grid, k_views):
         return info["pairs"] * (4 + 48) + info["bricks"] * 512 * 3 * 4
     if stage == "mc_count":           # A read once, the inside bits written (count reads them from L2)
         return 4 * M + M // 8
-    if stage == "mc_emit":            # bits of the rows, A at both ends of each crossing edge, vertices,
-        # normals and one 16-byte record per vertex-owning node written
-        return M // 8 + info["n_vertices"] * (8 + 24 + 16)
+    if stage == "mc_emit":            # the inside bits read, one 16-byte record per active node written
+        # (at most one per vertex)
+        return M // 8 + 16 * info["n_vertices"]
+    if stage == "mc_tris":            # the records read, A at both ends of each crossing edge, vertices
+        # and normals written, three indices per triangle
+        return info["n_vertices"] * (16 + 8 + 24) + 12 * info["n_tris"]
     if stage == "texture":
         return info["n_vertices"] * (12 + k_views * 12 + 4)
     return None

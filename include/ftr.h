@@ -310,10 +310,12 @@ int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pi
 /*
  * Tile plans (no counterpart in the paper, which gives no kernel design).
  * The y, z and inverse-y FFT passes each move F lines per CTA, F in
- * {8, 16, 32}; for the y pass F = -16 means 16 lines whose three component
- * tiles are fetched by bulk asynchronous copies at the CTA's start (lines
- * of at most 256).  Every plan computes bit-identical results (each line's
- * arithmetic does not depend on the plan), only the speed differs.
+ * {8, 16, 32}; F = -16 means 16 lines whose input tiles are fetched by bulk
+ * asynchronous copies at the CTA's start: the y pass's three component
+ * tiles (lines of at most 256), or the z pass's two fields, each line's
+ * live z range only.  Every plan computes bit-identical results (each
+ * line's arithmetic does not depend on the plan), only the speed differs.
+ * The plane-fused path's z pass takes 8, 16 or 32 (-16 runs it with 16).
  *
  * ftr_autotune times each pass's candidate F on this context's grid (a few
  * launches each, on the context's own buffers, so no frame may be pending:
@@ -341,7 +343,8 @@ int ftr_get_plan(const ftr_ctx* ctx, int* plan);
 
 /* Force a plan: each entry 8, 16 or 32 and a divisor of the axis the pass
  * tiles (n_z for the y passes, n_y for the z pass), or -16 for the y pass
- * when 16 divides n_z and n_y <= 256; else FTR_EINVAL. */
+ * when 16 divides n_z and n_y <= 256, or for the z pass when 16 divides
+ * n_y; else FTR_EINVAL. */
 int ftr_set_plan(ftr_ctx* ctx, const int* plan);
 
 /*

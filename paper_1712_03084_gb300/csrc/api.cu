@@ -252,7 +252,6 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_level_part);
     dfree(c->d_ticket);
     dfree(c->d_mc_blk);
-    dfree(c->d_mc_tile);
     dfree(c->d_mc_bits);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
@@ -368,7 +367,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_s0, 3 * c->Mh);
     ALLOC(c->d_s1, 2 * c->Mh);
     ALLOC(c->d_A, c->M);
-    for (int a = 0; a < 3; ++a) ALLOC(c->d_tw[a], grid_n[a]);
+    for (int a = 0; a < 3; ++a) ALLOC(c->d_tw[a], 3 * grid_n[a]);
     c->level_blocks = 304;
     ALLOC(c->d_level, 2);
     ALLOC(c->d_levelf, 2);
@@ -376,7 +375,6 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     ALLOC(c->d_ticket, 1);
     c->mc_blocks = grid_n[1] * grid_n[2];      // marching cubes counts per grid row
     ALLOC(c->d_mc_blk, 3 * c->mc_blocks);
-    ALLOC(c->d_mc_tile, (c->mc_blocks + kMcScanTile - 1) / kMcScanTile + 1);
     {
         int wp = 1;
         while (wp < (grid_n[0] + 31) / 32) wp <<= 1;
@@ -392,7 +390,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     }
     // W_n^m of each axis, computed on the device in float64
     for (int a = 0; a < 3; ++a) {
-        if ((e = launch_twiddle(c->d_tw[a], grid_n[a], c->stream)) != cudaSuccess) {
+        if ((e = launch_axis_twiddles(c->d_tw[a], grid_n[a], c->stream)) != cudaSuccess) {
             free_all(c);
             delete c;
             return FTR_ECUDA;
@@ -1287,7 +1285,7 @@ bool valid_lines(int f) { return f == 8 || f == 16 || f == 32; }
 // lines, lines of at most 256).
 bool plan_fits(const ftr_ctx* c, int pass, int f) {
     const int n = pass == 1 ? c->g.n[1] : c->g.n[2];
-    if (f == -16) return pass == 0 && n % 16 == 0 && c->g.n[1] <= 256;
+    if (f == -16) return (pass == 0 && n % 16 == 0 && c->g.n[1] <= 256) || (pass == 1 && n % 16 == 0);
     return valid_lines(f) && n % f == 0;
 }
 }  // namespace
@@ -1429,7 +1427,7 @@ int ftr_autotune(ftr_ctx* c, float* report) {
         c->fused = pass == 3 ? 1 : 0;
         float best_us = 1e30f;
         for (int v = 0; v < 4; ++v) {
-            if (!plan_fits(c, slot, F[v])) continue;
+            if (!plan_fits(c, slot, F[v]) || (pass == 3 && F[v] < 0)) continue;   // the fused z pass: 8, 16, 32
             c->plan_lines[slot] = F[v];
             auto run = [&]() {
                 if (pass == 3) return launch_fz2(c);
@@ -1525,7 +1523,7 @@ int64_t context_bytes(const int n[3], const Caps& k) {
     b += k.heavy * (4 * kBrickVox * 8 + 4) + nb * 8;   // heavy-brick accumulators, chunk offsets
     b += nb * 3 * kBrickVox * (int64_t)sizeof(float);
     b += 5 * Mh * (int64_t)sizeof(float2) + M * (int64_t)sizeof(float);
-    b += (int64_t)(n[0] + n[1] + n[2]) * (int64_t)sizeof(float2);
+    b += 3 * (int64_t)(n[0] + n[1] + n[2]) * (int64_t)sizeof(float2);
     if (k.tc) b += (int64_t)tc_table_bytes() + 16;
     if (k.yz) b += (int64_t)(yz_ring_elems(n) * sizeof(float2)) + (int64_t)yz_sync_ints(n) * (int64_t)sizeof(int);
     b += k.raw * 7 * (int64_t)sizeof(float) + k.raw_tiles * (int64_t)sizeof(int);

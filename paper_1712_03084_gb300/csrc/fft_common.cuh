@@ -201,7 +201,8 @@ struct Xchg {
 };
 
 // Step 1 of a length-N transform: regs hold x[N2 n1 + j]; afterwards the
-// twiddled step-1 results sit in the exchange buffer.  tw = W_N^m table.
+// twiddled step-1 results sit in the exchange buffer.  tw = the axis table
+// (W_N^m, then W_N^(j k1) as [k1 < N1][j < N2], then as [k1 < N2][j < N1]).
 template <int N, int F, int SIGN>
 __device__ __forceinline__ void fft_step1(float2 (&v)[Plan<N>::N1], int f, int j, float2* xs,
                                           const float2* __restrict__ tw) {
@@ -209,7 +210,7 @@ __device__ __forceinline__ void fft_step1(float2 (&v)[Plan<N>::N1], int f, int j
     Dft<X::N1, SIGN>::run(v);
 #pragma unroll
     for (int k1 = 0; k1 < X::N1; ++k1) {
-        float2 w = (k1 == 0 || j == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[(j * k1) % N]);
+        float2 w = (k1 == 0 || j == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[N + k1 * X::N2 + j]);
         if (SIGN > 0) w.y = -w.y;
         xs[X::idx(f, j, k1)] = (k1 == 0) ? v[k1] : cmul(v[k1], w);
     }
@@ -234,7 +235,7 @@ __device__ __forceinline__ void fft_step1_swapped(float2 (&v)[Plan<N>::N2], int 
     Dft<X::N2, SIGN>::run(v);
 #pragma unroll
     for (int k1 = 0; k1 < X::N2; ++k1) {
-        float2 w = (k1 == 0 || j == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[(j * k1) % N]);
+        float2 w = (k1 == 0 || j == 0) ? make_float2(1.f, 0.f) : __ldg(&tw[2 * N + k1 * X::N1 + j]);
         if (SIGN > 0) w.y = -w.y;
         xs[X::idxr(f, j, k1)] = (k1 == 0) ? v[k1] : cmul(v[k1], w);
     }

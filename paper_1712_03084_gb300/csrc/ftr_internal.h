@@ -16,7 +16,6 @@ constexpr int kBrick = 8;                 // splat accumulation brick edge (node
 constexpr int kBrickVox = kBrick * kBrick * kBrick;
 constexpr int kMaxViews = 8;
 constexpr int kBrickScanTile = 256;   // bricks per tile of the brick-count scan (one block scan per CTA)
-constexpr int kMcScanTile = 256;      // grid rows per tile of the marching-cubes row scan
 constexpr int kMcThreads = 256;           // marching-cubes CTA size (chunks of 8 grid rows)
 constexpr int kMaxTrisPerCase = 5;
 constexpr int kSplatChunk = 1024;          // (point, brick) pairs per accumulation work unit
@@ -166,8 +165,7 @@ struct ftr_ctx {
 
     // marching cubes
     int mc_blocks = 0;             // grid rows n_y n_z
-    int* d_mc_blk = nullptr;       // 3 x mc_blocks (per grid row: active nodes, vertices, triangles)
-    int3* d_mc_tile = nullptr;     // tile sums / offsets of the chunk scan
+    int* d_mc_blk = nullptr;       // 3 x mc_blocks ints: tile and group sums of the marching-cubes count
     unsigned* d_mc_bits = nullptr; // inside bits, 32 nodes per word, rows padded to a power-of-two word count
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
@@ -262,6 +260,8 @@ cudaError_t fft_fused_b_init(const float2* w96);
 cudaError_t fft_plane_init(const float2* w96);
 // W_n^m, m < n, in float64 on the device, stored float32 (twiddle.cu)
 cudaError_t launch_twiddle(float2* tw, int n, cudaStream_t st);
+// An axis table: W_n^m, then its copies in the order of the two twiddle steps (3 n entries).
+cudaError_t launch_axis_twiddles(float2* tw, int n, cudaStream_t st);
 cudaError_t mc_init();
 
 // launchers (return cudaError_t of the launch)
@@ -318,8 +318,8 @@ cudaError_t launch_tc_pass(ftr_ctx* c, int pass);
 cudaError_t tc_prepare(ftr_ctx* c);
 cudaError_t launch_mc_bits(ftr_ctx* c);        // inside bits A >= L only
 int mc_words_per_row(int nx);                  // padded words per grid row of the inside bits
-cudaError_t launch_mc_count(ftr_ctx* c);       // count + scan
-cudaError_t launch_mc_emit(ftr_ctx* c);        // vertices, node records, triangles
+cudaError_t launch_mc_count(ftr_ctx* c);       // inside bits, then tile and group counts
+cudaError_t launch_mc_emit(ftr_ctx* c);        // offsets and node records, then vertices and triangles
 cudaError_t launch_mc_totals(ftr_ctx* c);      // totals (active, verts, tris) to h_mc_tot
 cudaError_t launch_flags(ftr_ctx* c);          // device wait flags to h_flags (api.cu)
 cudaError_t launch_mc_classes(ftr_ctx* c, uint8_t* out_dev);

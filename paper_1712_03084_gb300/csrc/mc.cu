@@ -15,13 +15,13 @@
 // toward +x, +y, +z and AND/OR of the eight corner masks the cells whose
 // corners differ (exactly the cells with triangles).  Launches:
 //   bits   the inside bits of every node
-//   count  per row: active nodes (owning a vertex or lower corner of a cell
-//          with triangles), vertices, triangles
-//   scan   three coalesced launches: exclusive offsets of the row counts
-//   emit   rows with surface only: per word an exclusive prefix over the
-//          row's words, then its active nodes in x order: one 16-byte
-//          record per node (node, edge bits | class << 8, first vertex,
-//          first triangle)
+//   count  per tile of (row, word) threads: active nodes (owning a vertex
+//          or lower corner of a cell with triangles), vertices, triangles;
+//          also summed per group of 256 tiles
+//   emit   per tile: its offset from the group and tile sums before it, a
+//          CTA scan of its counts, the rows' offsets, and per active node
+//          in x order one 16-byte record (node, edge bits | class << 8,
+//          first vertex, first triangle)
 //   tris   one thread per active node: the vertices of its crossing edges
 //          (t = (L - A0)/(A1 - A0), normal -grad A by central differences,
 //          one-sided at the border, lerped), then its triangles' corners
@@ -76,10 +76,12 @@ __device__ __forceinline__ int ntri_of(int cls) { return (cls == 0 || cls == 255
 // (y + n_y z) holds x = 32 w .. 32 w + 31 (bit i = node 32 w + i; zero past
 // n_x); rows are `wp` words apart (wp = the words per row rounded up to a
 // power of two).  One warp per row, one ballot per word.
+// It also zeroes `zero[0 .. nzero)` (the group sums of k_mc_count_tiles).
 __global__ void __launch_bounds__(kMcThreads) k_mc_bits(GridDev g, const float* __restrict__ A,
                                                         const float* __restrict__ levelf, unsigned* __restrict__ bits,
-                                                        int nrows, int wp) {
+                                                        int nrows, int wp, int* __restrict__ zero, int nzero) {
     pdl_wait();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * blockDim.x) zero[i] = 0;
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
     if (row >= nrows) return;                    // warp-uniform
     const int lane = threadIdx.x & 31;
@@ -156,44 +158,6 @@ __device__ __forceinline__ int cell_class(const WordMasks& m, int i) {
     return cls;
 }
 
-// Thread per (row, word), rows in groups of wp lanes: active nodes, vertices
-// and triangles of the row.
-__global__ void __launch_bounds__(kMcThreads) k_mc_count_bits(GridDev g, const unsigned* __restrict__ bits,
-                                                              int* __restrict__ cnt, int nrows, int wp) {
-    pdl_wait();
-    __shared__ unsigned char s_ntri[256];
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
-    __syncthreads();
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(t / wp), w = (int)(t % wp);
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int nw = (nx + 31) >> 5;
-    int na = 0, nv = 0, nt = 0;
-    if (row < nrows && w < nw) {
-        const int y = row % ny, z = row / ny;
-        const WordMasks m = word_masks(bits, row, w, nw, wp, nx, y < ny - 1, z < nz - 1, ny);
-        na = __popc(m.ex | m.ey | m.ez | m.mixed);
-        nv = __popc(m.ex) + __popc(m.ey) + __popc(m.ez);
-        unsigned mm = m.mixed;
-        while (mm) {
-            const int i = __ffs(mm) - 1;
-            mm &= mm - 1;
-            nt += s_ntri[cell_class(m, i)];
-        }
-    }
-    // sum over the wp lanes of the row (aligned groups inside a warp)
-    for (int o = 1; o < wp; o <<= 1) {
-        na += __shfl_xor_sync(0xffffffffu, na, o);
-        nv += __shfl_xor_sync(0xffffffffu, nv, o);
-        nt += __shfl_xor_sync(0xffffffffu, nt, o);
-    }
-    if (w == 0 && row < nrows) {
-        cnt[row] = na;
-        cnt[nrows + row] = nv;
-        cnt[2 * nrows + row] = nt;
-    }
-}
-
 // Block-wide exclusive scan of 3 ints (kMcThreads threads); returns totals.
 __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -233,72 +197,129 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
     return make_int3(before.x + inc.x - v.x, before.y + inc.y - v.y, before.z + inc.z - v.z);
 }
 
-// Exclusive scan of the three row-count arrays (length nb) in tiles of
-// kScanTile: tile sums, then each tile adds up the sums before it and writes
-// off[a * (nb + 1) + i]; totals go to off[a * (nb + 1) + nb].
-constexpr int kScanTile = kMcScanTile;
-static_assert(kScanTile % kMcThreads == 0, "a tile is a whole number of block scans");
+// ------------------------------------------------- tiles: count, then emit
+// Both kernels run over the (row, word) threads in node order in the same
+// tiles of kMcThreads.  The count kernel writes each tile's sums (active
+// nodes, vertices, triangles) and adds them into its group's sums (256 tiles
+// per group; integer atomics, so the order does not matter).  The emit
+// kernel's tile gets its offset from the groups before it and the tiles
+// before it in its group (at most 255 + a few loads, spread over the CTA),
+// scans its own counts, and writes its rows' offsets and its node records.
+//
+// Tile state (agg) and group sums (sup, zeroed by k_mc_bits) as int4: active
+// nodes, vertices, triangles, unused.
+struct WordCounts {
+    WordMasks m;
+    unsigned act;
+    int3 c;
+};
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_tile_sums(const int* __restrict__ blk, int nb, int3* tile) {
-    pdl_wait();
-    __shared__ int3 sh[kMcThreads / 32];
-    int3 v = make_int3(0, 0, 0);
-    for (int k = 0; k < kScanTile / kMcThreads; ++k) {
-        const int i = blockIdx.x * kScanTile + k * kMcThreads + threadIdx.x;
-        if (i < nb) {
-            v.x += blk[i];
-            v.y += blk[nb + i];
-            v.z += blk[2 * nb + i];
+__device__ __forceinline__ WordCounts word_counts(const GridDev& g, const unsigned* __restrict__ bits, int64_t t,
+                                                  int nrows, int wp, const unsigned char* s_ntri) {
+    WordCounts r;
+    r.act = 0u;
+    r.c = make_int3(0, 0, 0);
+    const int row = (int)(t / wp), w = (int)(t % wp);
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int nw = (nx + 31) >> 5;
+    if (row < nrows && w < nw) {
+        const int y = row % ny, z = row / ny;
+        r.m = word_masks(bits, row, w, nw, wp, nx, y < ny - 1, z < nz - 1, ny);
+        r.act = r.m.ex | r.m.ey | r.m.ez | r.m.mixed;
+        r.c.x = __popc(r.act);
+        r.c.y = __popc(r.m.ex) + __popc(r.m.ey) + __popc(r.m.ez);
+        unsigned mm = r.m.mixed;
+        while (mm) {
+            const int i = __ffs(mm) - 1;
+            mm &= mm - 1;
+            r.c.z += s_ntri[cell_class(r.m, i)];
         }
     }
-    int3 tot;
-    block_scan3(v, tot, sh);
-    if (threadIdx.x == 0) tile[blockIdx.x] = tot;
+    return r;
 }
 
-// Per tile: the exclusive offset is the sum of the (few) tile sums before
-// it, summed by every CTA itself (no separate scan launch); CTA 0 also writes
-// the totals.  Then the tile's rows get their offsets.
-__global__ void __launch_bounds__(kMcThreads) k_mc_tile_write(const int* __restrict__ blk, int nb,
-                                                              const int3* __restrict__ tile, int ntiles, int* off) {
+constexpr int kMcGroup = 256;     // tiles per group sum
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_count_tiles(GridDev g, const unsigned* __restrict__ bits,
+                                                               int nrows, int wp, int4* __restrict__ agg,
+                                                               int* __restrict__ sup) {
     pdl_wait();
+    __shared__ unsigned char s_ntri[256];
     __shared__ int3 sh[kMcThreads / 32];
-    int3 pre = make_int3(0, 0, 0), all = make_int3(0, 0, 0);
-    for (int i = threadIdx.x; i < ntiles; i += kMcThreads) {
-        const int3 v = tile[i];
-        if (i < (int)blockIdx.x) {
-            pre.x += v.x;
-            pre.y += v.y;
-            pre.z += v.z;
-        }
-        all.x += v.x;
-        all.y += v.y;
-        all.z += v.z;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
+    __syncthreads();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const WordCounts wc = word_counts(g, bits, t, nrows, wp, s_ntri);
+    int3 tot;
+    block_scan3(wc.c, tot, sh);
+    if (threadIdx.x == 0) {
+        agg[blockIdx.x] = make_int4(tot.x, tot.y, tot.z, 0);
+        int* s = sup + 4 * (blockIdx.x / kMcGroup);
+        if (tot.x) atomicAdd(&s[0], tot.x);
+        if (tot.y) atomicAdd(&s[1], tot.y);
+        if (tot.z) atomicAdd(&s[2], tot.z);
     }
-    int3 run, total;
-    block_scan3(pre, run, sh);
-    block_scan3(all, total, sh);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        off[nb] = total.x;
-        off[(nb + 1) + nb] = total.y;
-        off[2 * (nb + 1) + nb] = total.z;
-        off[3 * (nb + 1) + 0] = total.x;     // totals for the host
-        off[3 * (nb + 1) + 1] = total.y;
-        off[3 * (nb + 1) + 2] = total.z;
+}
+
+__global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const unsigned* __restrict__ bits,
+                                                              int nrows, int wp, int ntiles,
+                                                              const int4* __restrict__ agg,
+                                                              const int4* __restrict__ sup, int* __restrict__ off,
+                                                              int4* __restrict__ nodes, int cap_nodes) {
+    pdl_wait();
+    __shared__ unsigned char s_ntri[256];
+    __shared__ int3 sh[kMcThreads / 32];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
+    // the sums of every tile before this one: whole groups, then this group's tiles
+    const int tile = blockIdx.x, grp = tile / kMcGroup;
+    int3 pre = make_int3(0, 0, 0);
+    for (int k = threadIdx.x; k < grp; k += blockDim.x) {
+        const int4 v = sup[k];
+        pre.x += v.x;
+        pre.y += v.y;
+        pre.z += v.z;
     }
-    for (int k = 0; k < kScanTile / kMcThreads; ++k) {
-        const int i = blockIdx.x * kScanTile + k * kMcThreads + threadIdx.x;
-        const int3 v = i < nb ? make_int3(blk[i], blk[nb + i], blk[2 * nb + i]) : make_int3(0, 0, 0);
-        int3 tot;
-        const int3 ex = block_scan3(v, tot, sh);
-        if (i < nb) {
-            off[i] = run.x + ex.x;
-            off[(nb + 1) + i] = run.y + ex.y;
-            off[2 * (nb + 1) + i] = run.z + ex.z;
-        }
-        run.x += tot.x;
-        run.y += tot.y;
-        run.z += tot.z;
+    for (int k = grp * kMcGroup + threadIdx.x; k < tile; k += blockDim.x) {
+        const int4 v = agg[k];
+        pre.x += v.x;
+        pre.y += v.y;
+        pre.z += v.z;
+    }
+    __syncthreads();
+    int3 base;
+    block_scan3(pre, base, sh);
+    const int64_t t = (int64_t)tile * blockDim.x + threadIdx.x;
+    const WordCounts wc = word_counts(g, bits, t, nrows, wp, s_ntri);
+    int3 tot;
+    const int3 ex = block_scan3(wc.c, tot, sh);
+    const int row = (int)(t / wp), w = (int)(t % wp);
+    int ja = base.x + ex.x, jv = base.y + ex.y, jt = base.z + ex.z;
+    if (w == 0 && row < nrows) {
+        off[row] = ja;
+        off[(nrows + 1) + row] = jv;
+        off[2 * (nrows + 1) + row] = jt;
+    }
+    if (tile == ntiles - 1 && threadIdx.x == 0) {
+        const int3 all = make_int3(base.x + tot.x, base.y + tot.y, base.z + tot.z);
+        off[nrows] = all.x;
+        off[(nrows + 1) + nrows] = all.y;
+        off[2 * (nrows + 1) + nrows] = all.z;
+        off[3 * (nrows + 1) + 0] = all.x;     // totals for the host
+        off[3 * (nrows + 1) + 1] = all.y;
+        off[3 * (nrows + 1) + 2] = all.z;
+    }
+    const int64_t rowbase = (int64_t)row * g.n[0];
+    unsigned rem = wc.act;
+    while (rem) {
+        const int i = __ffs(rem) - 1;
+        rem &= rem - 1;
+        const int flags = (int)((wc.m.ex >> i) & 1u) | ((int)((wc.m.ey >> i) & 1u) << 1) |
+                          ((int)((wc.m.ez >> i) & 1u) << 2);
+        const int cls = ((wc.m.mixed >> i) & 1u) ? cell_class(wc.m, i) : 0;
+        if (ja < cap_nodes) nodes[ja] = make_int4((int)(rowbase + 32 * w + i), flags | (cls << 8), jv, jt);
+        ++ja;
+        jv += __popc(flags);
+        jt += cls ? s_ntri[cls] : 0;
     }
 }
 
@@ -347,75 +368,6 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
         vnrm[3 * (int64_t)vi + 1] = nv[1] * inv;
         vnrm[3 * (int64_t)vi + 2] = nv[2] * inv;
         ++vi;
-    }
-}
-
-// Thread per (row, word) in groups of wp lanes, rows with surface only: the
-// group's exclusive prefix of (active nodes, vertices, triangles) plus the
-// row offsets give every thread its output positions; it then walks its
-// active nodes in x order writing the node record (node, edge bits | class
-// << 8, first vertex, first triangle).  Vertices are computed per record by
-// k_mc_tris, one thread per node.
-__global__ void __launch_bounds__(kMcThreads) k_mc_emit_bits(GridDev g, const unsigned* __restrict__ bits,
-                                                             const int* __restrict__ cnt, const int* __restrict__ off,
-                                                             int nrows, int wp, int4* __restrict__ nodes,
-                                                             int cap_nodes) {
-    pdl_wait();
-    __shared__ unsigned char s_ntri[256];
-    for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
-    __syncthreads();
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = (int)(t / wp), w = (int)(t % wp);
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int nw = (nx + 31) >> 5;
-    const bool live = row < nrows && cnt[row] > 0;      // the same for the whole group
-    const int y = row % ny, z = row / ny;
-    WordMasks m;
-    unsigned act = 0u;
-    int ca = 0, cv = 0, ct = 0;
-    if (live && w < nw) {
-        m = word_masks(bits, row, w, nw, wp, nx, y < ny - 1, z < nz - 1, ny);
-        act = m.ex | m.ey | m.ez | m.mixed;
-        ca = __popc(act);
-        cv = __popc(m.ex) + __popc(m.ey) + __popc(m.ez);
-        unsigned mm = m.mixed;
-        while (mm) {
-            const int i = __ffs(mm) - 1;
-            mm &= mm - 1;
-            ct += s_ntri[cell_class(m, i)];
-        }
-    }
-    // inclusive prefix inside the group (all lanes of the warp take part)
-    int pa = ca, pv = cv, pt = ct;
-    const int gl = (int)(threadIdx.x & 31) % wp;
-    for (int o = 1; o < wp; o <<= 1) {
-        const int a = __shfl_up_sync(0xffffffffu, pa, o, wp);
-        const int b = __shfl_up_sync(0xffffffffu, pv, o, wp);
-        const int c = __shfl_up_sync(0xffffffffu, pt, o, wp);
-        if (gl >= o) {
-            pa += a;
-            pv += b;
-            pt += c;
-        }
-    }
-    if (!act) return;
-    int ja = off[row] + pa - ca;
-    int jv = off[(nrows + 1) + row] + pv - cv;
-    int jt = off[2 * (nrows + 1) + row] + pt - ct;
-    const int64_t rowbase = (int64_t)row * nx;
-    unsigned rem = act;
-    while (rem) {
-        const int i = __ffs(rem) - 1;
-        rem &= rem - 1;
-        const int x = 32 * w + i;
-        const int flags = (int)((m.ex >> i) & 1u) | ((int)((m.ey >> i) & 1u) << 1) | ((int)((m.ez >> i) & 1u) << 2);
-        const int cls = ((m.mixed >> i) & 1u) ? cell_class(m, i) : 0;
-        const int ntr = cls ? s_ntri[cls] : 0;
-        const int64_t n = rowbase + x;
-        if (ja < cap_nodes) nodes[ja] = make_int4((int)n, flags | (cls << 8), jv, jt);
-        ++ja;
-        jv += __popc(flags);
-        jt += ntr;
     }
 }
 
@@ -517,10 +469,16 @@ static int mc_words(int nx) {
     return wp;
 }
 
+// Tiles of kMcThreads (row, word) threads, and where the tile sums and the
+// group sums sit in the per-row count buffer (3 x n_rows ints: room for both
+// with up to 16 words per row, every supported grid).
+static int mc_tiles(int nrows, int wp) { return (int)(((int64_t)nrows * wp + kMcThreads - 1) / kMcThreads); }
+static int mc_groups(int ntiles) { return (ntiles + kMcGroup - 1) / kMcGroup; }
+
 cudaError_t launch_mc_bits(ftr_ctx* c) {
     const int nr = c->mc_blocks;
     launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
-               c->d_mc_bits, nr, mc_words(c->g.n[0]));
+               c->d_mc_bits, nr, mc_words(c->g.n[0]), (int*)nullptr, 0);
     c->launches++;
     return cudaGetLastError();
 }
@@ -530,23 +488,18 @@ int mc_words_per_row(int nx) { return mc_words(nx); }
 cudaError_t launch_mc_count(ftr_ctx* c) {
     const int nr = c->mc_blocks;              // grid rows n_y n_z
     const int wp = mc_words(c->g.n[0]);
+    const int ntiles = mc_tiles(nr, wp);
+    if (4 * (ntiles + mc_groups(ntiles)) > 3 * nr) return cudaErrorInvalidValue;
+    int4* agg = reinterpret_cast<int4*>(c->d_mc_blk);
+    int* sup = c->d_mc_blk + 4 * ntiles;
     prof_begin(c, ST_MC_COUNT);
     launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
-               c->d_mc_bits, nr, wp);
-    const int64_t threads = (int64_t)nr * wp;
-    launch_pdl(k_mc_count_bits, (unsigned)((threads + kMcThreads - 1) / kMcThreads), kMcThreads, 0, c->stream, c->g,
-               c->d_mc_bits, c->d_mc_blk, nr, wp);
+               c->d_mc_bits, nr, wp, sup, 4 * mc_groups(ntiles));
+    launch_pdl(k_mc_count_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, agg,
+               sup);
     c->launches += 2;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
-    if (e != cudaSuccess) return e;
-    prof_begin(c, ST_MC_SCAN);
-    const int ntiles = (nr + kScanTile - 1) / kScanTile;
-    launch_pdl(k_mc_tile_sums, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile);
-    launch_pdl(k_mc_tile_write, ntiles, kMcThreads, 0, c->stream, c->d_mc_blk, nr, c->d_mc_tile, ntiles, c->d_mc_off);
-    c->launches += 2;
-    e = cudaGetLastError();
-    prof_end(c, ST_MC_SCAN);
     return e;
 }
 
@@ -559,13 +512,16 @@ cudaError_t launch_mc_totals(ftr_ctx* c) {
                            c->stream);
 }
 
+// The rows' offsets and the node records, then the vertices and triangles.
 cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int nr = c->mc_blocks;
     const int wp = mc_words(c->g.n[0]);
-    const int64_t threads = (int64_t)nr * wp;
+    const int ntiles = mc_tiles(nr, wp);
+    const int4* agg = reinterpret_cast<const int4*>(c->d_mc_blk);
+    const int4* sup = reinterpret_cast<const int4*>(c->d_mc_blk + 4 * ntiles);
     prof_begin(c, ST_MC_EMIT);
-    launch_pdl(k_mc_emit_bits, (unsigned)((threads + kMcThreads - 1) / kMcThreads), kMcThreads, 0, c->stream, c->g,
-               c->d_mc_bits, c->d_mc_blk, c->d_mc_off, nr, wp, c->d_mc_nodes, (int)c->cap_mc_nodes);
+    launch_pdl(k_mc_emit_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, ntiles,
+               agg, sup, c->d_mc_off, c->d_mc_nodes, (int)c->cap_mc_nodes);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);

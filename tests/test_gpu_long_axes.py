@@ -101,6 +101,8 @@ def test_long_axis_every_plan_is_bit_identical(ftr, name):
     choices = [[f for f in (8, 16, 32) if (ny if p == 1 else nz) % f == 0] for p in range(3)]
     if nz % 16 == 0 and ny <= 256:
         choices[0].append(-16)
+    if ny % 16 == 0:
+        choices[1].append(-16)
     for plan in itertools.product(*choices):
         try:
             g = _gpu(ftr, grid, plan)

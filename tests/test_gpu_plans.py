@@ -1,5 +1,5 @@
 """Tile plans of the y, z and inverse-y FFT passes (8, 16 or 32 lines per CTA;
--16: the y pass with its tiles fetched by bulk asynchronous copies).
+-16: the y or z pass with its tiles fetched by bulk asynchronous copies).
 
 Every plan runs the same per-line arithmetic, so the indicator must be
 bit-identical whatever the plan; the autotuner must pick a plan that fits
@@ -48,6 +48,8 @@ def test_every_plan_is_bit_identical(ftr, name):
     choices = [[f for f in (8, 16, 32) if (ny if p == 1 else nz) % f == 0] for p in range(3)]
     if nz % 16 == 0 and ny <= 256:
         choices[0].append(-16)          # the y pass with bulk-copied tiles
+    if ny % 16 == 0:
+        choices[1].append(-16)          # the z pass with bulk-copied tiles
     for plan in itertools.product(*choices):
         A, L = _field(ftr, name, plan)
         assert np.array_equal(A, ref_A), plan
