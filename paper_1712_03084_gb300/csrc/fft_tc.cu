@@ -54,6 +54,19 @@ __host__ __device__ constexpr int tc_off(int R, int row, int k) {
     return (row >> 3) * (32 * R) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
+// The A operands (the data) use padded core-matrix strides: core matrices
+// adjacent along K are LBO_A bytes apart and 8-row groups SBO_A bytes apart,
+// chosen so that the stores that fill them spread over the 32 shared-memory
+// banks (the step-2 operand is written 4 bytes per row by threads that hold
+// one K column each; with the dense strides 128 / 32 R those stores conflict
+// 8-fold).  The MMA reads any such strides; only the B operands (the DFT
+// matrices) keep the dense layout of the table.
+__host__ __device__ constexpr int lbo_a(int R) { return R == 8 ? 192 : (R == 16 ? 160 : 144); }
+__host__ __device__ constexpr int sbo_a(int R) { return R == 8 ? 336 : (R == 16 ? 624 : (R == 24 ? 880 : 1168)); }
+__host__ __device__ constexpr int a_off(int R, int row, int k) {
+    return (row >> 3) * sbo_a(R) + (k >> 3) * lbo_a(R) + (row & 7) * 16 + (k & 7) * 2;
+}
+
 template <int P> struct Half16;
 template <> struct Half16<FTR_PREC_BF16X3> {
     __device__ static unsigned short rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -83,14 +96,15 @@ struct Tc {
     static constexpr int tiles(int rows) { return (rows + 127) / 128; }
     static constexpr int TA = tiles(F * N2);   // rows carrying length-N1 vectors
     static constexpr int TB = tiles(F * N1);   // rows carrying length-N2 vectors
-    static constexpr int APART = cmax(TA * 128 * 4 * N1, TB * 128 * 4 * N2);
+    static constexpr int APART = cmax(TA * 16 * sbo_a(N1), TB * 16 * sbo_a(N2));
     static constexpr int COLS = cpow2(cmax(TA * 2 * N1, TB * 2 * N2));
     static constexpr int NSIGN = (FWD ? 1 : 0) + (INV ? 1 : 0);
     static constexpr int BR1 = 16 * N1 * N1;
     static constexpr int BR2 = (N1 == N2) ? 0 : 16 * N2 * N2;
     static constexpr int BBYTES = NSIGN * (BR1 + BR2);
+    static constexpr int TWBYTES = 8 * N;                  // W_N^m, m < N
     static constexpr int HDR = 16 + ((4 * F + 15) / 16) * 16;
-    static constexpr int BYTES = HDR + BBYTES + 2 * APART;
+    static constexpr int BYTES = HDR + BBYTES + TWBYTES + 2 * APART;
 
     unsigned char* base;
     uint32_t tmem;
@@ -103,8 +117,9 @@ struct Tc {
         const int s = (FWD && INV && sign > 0) ? 1 : 0;
         return base + HDR + s * (BR1 + BR2) + (R == N1 ? 0 : BR1);
     }
-    __device__ unsigned char* ahi() const { return base + HDR + BBYTES; }
-    __device__ unsigned char* alo() const { return base + HDR + BBYTES + APART; }
+    __device__ const float2* twsm() const { return (const float2*)(base + HDR + BBYTES); }
+    __device__ unsigned char* ahi() const { return base + HDR + BBYTES + TWBYTES; }
+    __device__ unsigned char* alo() const { return base + HDR + BBYTES + TWBYTES + APART; }
 
     __device__ void copy_b(const unsigned char* __restrict__ table, int R, int sign) {
         const int bytes = 8 * R * R;
@@ -116,12 +131,17 @@ struct Tc {
         }
     }
 
-    // Collective: stage the DFT matrices, allocate Tensor Memory, set up the
-    // completion barrier.
-    __device__ void init(unsigned char* smem, const unsigned char* __restrict__ table, int* err_flag) {
+    // Collective: stage the DFT matrices and the twiddles W_N^m (tw, m < N),
+    // allocate Tensor Memory, set up the completion barrier.
+    __device__ void init(unsigned char* smem, const unsigned char* __restrict__ table,
+                         const float2* __restrict__ tw, int* err_flag) {
         base = smem;
         phase = 0;
         err = err_flag;
+        {
+            float2* t = (float2*)(base + HDR + BBYTES);
+            for (int i = threadIdx.x; i < N; i += blockDim.x) t[i] = tw[i];
+        }
         if (FWD) {
             copy_b(table, N1, -1);
             if (N2 != N1) copy_b(table, N2, -1);
@@ -166,7 +186,7 @@ struct Tc {
             H.z = h[4] | ((uint32_t)h[5] << 16); H.w = h[6] | ((uint32_t)h[7] << 16);
             L.x = l[0] | ((uint32_t)l[1] << 16); L.y = l[2] | ((uint32_t)l[3] << 16);
             L.z = l[4] | ((uint32_t)l[5] << 16); L.w = l[6] | ((uint32_t)l[7] << 16);
-            const int o = tc_off(R, row, 8 * q);
+            const int o = a_off(R, row, 8 * q);
             *(uint4*)(ahi() + o) = H;
             *(uint4*)(alo() + o) = L;
         }
@@ -178,7 +198,7 @@ struct Tc {
         unsigned short hr, lr, hi, li;
         split16<P>(v.x, hr, lr);
         split16<P>(v.y, hi, li);
-        const int o = tc_off(R, row, 2 * m);
+        const int o = a_off(R, row, 2 * m);
         *(uint32_t*)(ahi() + o) = hr | ((uint32_t)hi << 16);
         *(uint32_t*)(alo() + o) = lr | ((uint32_t)li << 16);
     }
@@ -192,7 +212,8 @@ struct Tc {
         __syncthreads();
         tc::fence_after_sync();
         if (threadIdx.x == 0) {
-            constexpr uint32_t SBO = 32 * R;
+            constexpr uint32_t SBO = 32 * R;                 // B: dense
+            constexpr uint32_t LA = lbo_a(R), SA = sbo_a(R);  // A: padded
             const uint32_t id = tc::idesc_f16(P == FTR_PREC_BF16X3, 128, 2 * R);
             const uint32_t a0 = tc::smem_u32(ahi()), a1 = tc::smem_u32(alo());
             const uint32_t b0 = tc::smem_u32(bmat(R, SIGN)), b1 = b0 + 8 * R * R;
@@ -200,11 +221,11 @@ struct Tc {
             for (int t = 0; t < nt; ++t) {
 #pragma unroll
                 for (int s = 0; s < R / 8; ++s) {
-                    const uint32_t ao = t * 16 * SBO + s * 256, bo = s * 256;
+                    const uint32_t ao = t * 16 * SA + s * 2 * LA, bo = s * 256;
                     const uint32_t d = tmem + t * 2 * R;
-                    tc::mma_f16(d, tc::desc_kmajor(a1 + ao, 128, SBO), tc::desc_kmajor(b0 + bo, 128, SBO), id, s > 0);
-                    tc::mma_f16(d, tc::desc_kmajor(a0 + ao, 128, SBO), tc::desc_kmajor(b1 + bo, 128, SBO), id, 1);
-                    tc::mma_f16(d, tc::desc_kmajor(a0 + ao, 128, SBO), tc::desc_kmajor(b0 + bo, 128, SBO), id, 1);
+                    tc::mma_f16(d, tc::desc_kmajor(a1 + ao, LA, SA), tc::desc_kmajor(b0 + bo, 128, SBO), id, s > 0);
+                    tc::mma_f16(d, tc::desc_kmajor(a0 + ao, LA, SA), tc::desc_kmajor(b1 + bo, 128, SBO), id, 1);
+                    tc::mma_f16(d, tc::desc_kmajor(a0 + ao, LA, SA), tc::desc_kmajor(b0 + bo, 128, SBO), id, 1);
                 }
             }
             tc::mma_commit(mbar());
@@ -221,8 +242,13 @@ struct Tc {
         const int w = threadIdx.x >> 5, t = w >> 2;
         if (t < tiles(rows)) {
             const uint32_t a = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(t * 2 * R);
+            if ((2 * R) % 32 == 0) {
 #pragma unroll
-            for (int c = 0; c < 2 * R / 16; ++c) tc::tmem_ld16(a + 16 * c, buf + 16 * c);
+                for (int c = 0; c < 2 * R / 32; ++c) tc::tmem_ld32(a + 32 * c, buf + 32 * c);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 2 * R / 16; ++c) tc::tmem_ld16(a + 16 * c, buf + 16 * c);
+            }
         }
         return (int)threadIdx.x < rows;
     }
@@ -232,8 +258,7 @@ struct Tc {
     // holds X[k1 + R1 k2] (k2 < R2) of line t / R1 with k1 = t % R1, or (with
     // LINE_FAST) of line t % F with k1 = t / F.  tw: W_{R1 R2}^m, m < R1 R2.
     template <int R1, int R2, int SIGN, bool LINE_FAST>
-    __device__ void dft(const float2 (&v)[R1], bool act, int f, int j, float2 (&out)[R2],
-                        const float2* __restrict__ tw) {
+    __device__ void dft(const float2 (&v)[R1], bool act, int f, int j, float2 (&out)[R2]) {
         constexpr int NN = R1 * R2;
         const int tid = threadIdx.x;
         float scale = 1.f;
@@ -267,7 +292,7 @@ struct Tc {
                 for (int k1 = 0; k1 < R1; ++k1) {
                     float2 y = make_float2(buf[2 * k1], buf[2 * k1 + 1]);
                     if (k1 != 0 && j1 != 0) {
-                        float2 w = __ldg(&tw[(j1 * k1) % NN]);
+                        float2 w = twsm()[(j1 * k1) % NN];
                         if (SIGN > 0) w.y = -w.y;
                         y = cmul(y, w);
                     }
@@ -345,8 +370,11 @@ __global__ void __launch_bounds__(kFxLines * Plan<N>::N1)
         return;
     }
     E e;
-    e.init(smem_raw, table, err);
-    float2* park = (float2*)(smem_raw + E::BYTES);
+    e.init(smem_raw, table, tw, err);
+    // the transformed lines are parked in the operand buffers, which are free
+    // once the last product has been read back
+    static_assert(sizeof(float2) * ZS * N <= 2 * E::APART, "park fits the operand buffers");
+    float2* park = (float2*)e.ahi();
     const int f = tid / N1, r = tid % N1;
     const int lz = z & 7;
     const bool act = r < N2;
@@ -369,7 +397,7 @@ __global__ void __launch_bounds__(kFxLines * Plan<N>::N1)
         }
     }
     float2 o[N2];
-    e.template dft<N1, N2, -1, false>(v, act, f, r, o, tw);
+    e.template dft<N1, N2, -1, false>(v, act, f, r, o);
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) park[f + ZS * (r + N1 * k2)] = o[k2];
     __syncthreads();
@@ -407,7 +435,7 @@ __global__ void __launch_bounds__(kFxLines * Plan<N>::N1)
 constexpr int kLines16 = 16;
 
 template <int N, int P>
-__global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
+__global__ void __launch_bounds__(kLines16 * Plan<N>::N1, kLines16 * Plan<N>::N1 <= 256 ? 2 : 1)
     k_tc_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
             const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
@@ -424,7 +452,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     live_z_range(meta, zl, zh);
     if (z0 < zl || z0 >= zh) return;
     E e;
-    e.init(smem_raw, table, err);
+    e.init(smem_raw, table, tw, err);
     float2* stash = (float2*)(smem_raw + E::BYTES);
     const int f1 = tid / N1, r1 = tid % N1;
     const bool act = r1 < N2;
@@ -437,7 +465,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
 #pragma unroll
             for (int n1 = 0; n1 < N1; ++n1) v[n1] = line[(size_t)c * Mh + N2 * n1 + r1];
         }
-        e.template dft<N1, N2, -1, true>(v, act, f1, r1, o, tw);
+        e.template dft<N1, N2, -1, true>(v, act, f1, r1, o);
         if (c == 0) {
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) stash[f2 + (F + 1) * (i2 + N1 * k2)] = o[k2];
@@ -459,7 +487,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
 
 // ------------------------------------------- z forward + filter + z inverse
 template <int N, int P>
-__global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
+__global__ void __launch_bounds__(kLines16 * Plan<N>::N1, kLines16 * Plan<N>::N1 <= 256 ? 3 : 1)
     k_tc_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
             float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
@@ -477,7 +505,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     int zl, zh;
     live_z_range(meta, zl, zh);
     E e;
-    e.init(smem_raw, table, err);
+    e.init(smem_raw, table, tw, err);
     const size_t line = (size_t)N * ((size_t)(ky0 + f) + (size_t)ny * kx);
     float2 v[N1], xw[N2], xh[N2];
 #pragma unroll
@@ -485,13 +513,13 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
         const int z = N2 * n1 + r;
         v[n1] = (act && z >= zl && z < zh) ? s1[line + z] : make_float2(0.f, 0.f);
     }
-    e.template dft<N1, N2, -1, false>(v, act, f, r, xw, tw);
+    e.template dft<N1, N2, -1, false>(v, act, f, r, xw);
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
         const int z = N2 * n1 + r;
         v[n1] = (act && z >= zl && z < zh) ? s1[Mh + line + z] : make_float2(0.f, 0.f);
     }
-    e.template dft<N1, N2, -1, false>(v, act, f, r, xh, tw);
+    e.template dft<N1, N2, -1, false>(v, act, f, r, xh);
     // thread (f, r): bins k_z = r + N1 k2 of line f
     {
         const int ky = ky0 + f;
@@ -511,7 +539,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     }
     // inverse along z, N = N2 x N1: thread (f, r) holds x[r + N1 k2]
     float2 o[N1];
-    e.template dft<N2, N1, +1, false>(xw, true, f, r, o, tw);
+    e.template dft<N2, N1, +1, false>(xw, true, f, r, o);
     if (tid < F * N2) {
         const int fo = tid / N2, ko = tid % N2;
         float2* dst = s1 + (size_t)N * ((size_t)(ky0 + fo) + (size_t)ny * kx);
@@ -536,7 +564,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
     const int kx = blockIdx.y;
     const int tid = threadIdx.x;
     E e;
-    e.init(smem_raw, table, err);
+    e.init(smem_raw, table, tw, err);
     const int f1 = tid % F, j1 = tid / F;
     const bool act = j1 < N2;
     float2 v[N1], o[N2];
@@ -547,7 +575,7 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
             v[n1] = src[(size_t)(z0 + f1) + (size_t)nz * ((size_t)ky + (size_t)N * kx)];
         }
     }
-    e.template dft<N1, N2, +1, false>(v, act, f1, j1, o, tw);
+    e.template dft<N1, N2, +1, false>(v, act, f1, j1, o);
     const int f2 = tid / N1, i2 = tid % N1;
     float2* out = dst + (size_t)N * ((size_t)(z0 + f2) + (size_t)nz * kx);
 #pragma unroll
@@ -574,8 +602,11 @@ __global__ void __launch_bounds__(kIxLines * Plan<N>::N1)
     const int z = blockIdx.y;
     const int tid = threadIdx.x;
     E e;
-    e.init(smem_raw, table, err);
-    float2* hs = (float2*)(smem_raw + E::BYTES);
+    e.init(smem_raw, table, tw, err);
+    // the half-spectrum rows are staged in the operand buffers, which the
+    // transform fills only after every thread has read its inputs
+    static_assert(sizeof(float2) * kHs * (N / 2 + 1) <= 2 * E::APART, "staging fits the operand buffers");
+    float2* hs = (float2*)e.ahi();
     for (int k = tid; k < kIxRows * NKX; k += blockDim.x) {
         const int row = k & (kIxRows - 1), kx = k >> 4;
         hs[kx * kHs + row] = src[(size_t)(y0 + row) + (size_t)ny * (z + (size_t)nz * kx)];
@@ -604,7 +635,8 @@ __global__ void __launch_bounds__(kIxLines * Plan<N>::N1)
             v[n1] = make_float2(xa.x - xb.y, xa.y + xb.x);
         }
     }
-    e.template dft<N1, N2, +1, false>(v, act, f1, j1, o, tw);
+    __syncthreads();                             // every input is in registers: the staging area becomes the operand
+    e.template dft<N1, N2, +1, false>(v, act, f1, j1, o);
     const int f2 = tid / N1, i2 = tid % N1;
     float* ra = A + (size_t)N * ((size_t)(y0 + f2) + (size_t)ny * z);
     float* rb = A + (size_t)N * ((size_t)(y0 + f2 + kIxLines) + (size_t)ny * z);
@@ -640,7 +672,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
     switch (pass) {
         case 0: {
             using E = Tc<N, kFxLines, P, true, false>;
-            const size_t smem = E::BYTES + sizeof(float2) * (kFxLines + 1) * N;
+            const size_t smem = E::BYTES;
             if ((e = set_smem(k_tc_fx<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
             dim3 grid(c->g.n[1] / kFxRows, c->g.n[2]);
@@ -685,7 +717,7 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
         }
         default: {
             using E = Tc<N, kIxLines, P, false, true>;
-            const size_t smem = E::BYTES + sizeof(float2) * kHs * (N / 2 + 1);
+            const size_t smem = E::BYTES;
             if ((e = set_smem(k_tc_ix<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
             dim3 grid(c->g.n[1] / kIxRows, c->g.n[2]);
