@@ -429,20 +429,32 @@ __global__ void __launch_bounds__(kFxLines * Plan<N>::N1)
     e.finish();
 }
 
+// Lines per CTA of the y, inverse-y and z passes: 16; the z pass takes 8
+// where the step-1 DFT is longer than 16 (384 points: a CTA of 8 x 24
+// threads, three of which fit an SM; measured faster there, and slower for
+// the y passes).
+template <int N>
+struct TcLines {
+    static constexpr int value = 16;
+};
+template <int N>
+struct TcLinesZ {
+    static constexpr int value = Plan<N>::N1 > 16 ? 8 : 16;
+};
+
 // ---------------------------------------------------------------- y forward
-// Same as the fp32 y pass: 16 y lines per component, W = Y[j w_x X V_x] +
+// Same as the fp32 y pass: F y lines per component, W = Y[j w_x X V_x] +
 // j w_y Y[X V_y] and Y[X V_z] out in [k_x][k_y][z].
-constexpr int kLines16 = 16;
 
 template <int N, int P>
-__global__ void __launch_bounds__(kLines16 * Plan<N>::N1, kLines16 * Plan<N>::N1 <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(TcLines<N>::value * Plan<N>::N1, TcLines<N>::value * Plan<N>::N1 <= 256 ? 2 : 1)
     k_tc_fy(GridDev g, const float2* __restrict__ s0, float2* __restrict__ s1, int64_t Mh,
             const float2* __restrict__ tw, float wy_scale, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
     pdl_wait();
-    using E = Tc<N, kLines16, P, true, false>;
+    using E = Tc<N, TcLines<N>::value, P, true, false>;
     constexpr int N1 = E::N1, N2 = E::N2;
-    constexpr int F = kLines16;
+    constexpr int F = TcLines<N>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nz = g.n[2];
     const int z0 = blockIdx.x * F;
@@ -487,14 +499,14 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1, kLines16 * Plan<N>::N1
 
 // ------------------------------------------- z forward + filter + z inverse
 template <int N, int P>
-__global__ void __launch_bounds__(kLines16 * Plan<N>::N1, kLines16 * Plan<N>::N1 <= 256 ? 3 : 1)
+__global__ void __launch_bounds__(TcLinesZ<N>::value * Plan<N>::N1, TcLinesZ<N>::value * Plan<N>::N1 <= 256 ? 3 : 1)
     k_tc_fz(GridDev g, float2* __restrict__ s1, int64_t Mh, const float2* __restrict__ tw, float wx_scale,
             float wy_scale, float wz_scale, float inv_m, const int* __restrict__ meta,
             const unsigned char* __restrict__ table, int* err) {
     pdl_wait();
-    using E = Tc<N, kLines16, P, true, true>;
+    using E = Tc<N, TcLinesZ<N>::value, P, true, true>;
     constexpr int N1 = E::N1, N2 = E::N2;
-    constexpr int F = kLines16;
+    constexpr int F = TcLinesZ<N>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ny = g.n[1];
     const int ky0 = blockIdx.x * F;
@@ -551,13 +563,13 @@ __global__ void __launch_bounds__(kLines16 * Plan<N>::N1, kLines16 * Plan<N>::N1
 
 // ---------------------------------------------------------------- y inverse
 template <int N, int P>
-__global__ void __launch_bounds__(kLines16 * Plan<N>::N1)
+__global__ void __launch_bounds__(TcLines<N>::value * Plan<N>::N1)
     k_tc_iy(GridDev g, const float2* __restrict__ src, float2* __restrict__ dst, const float2* __restrict__ tw,
             const unsigned char* __restrict__ table, int* err) {
     pdl_wait();
-    using E = Tc<N, kLines16, P, false, true>;
+    using E = Tc<N, TcLines<N>::value, P, false, true>;
     constexpr int N1 = E::N1, N2 = E::N2;
-    constexpr int F = kLines16;
+    constexpr int F = TcLines<N>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nz = g.n[2];
     const int z0 = blockIdx.x * F;
@@ -682,22 +694,22 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             break;
         }
         case 1: {
-            using E = Tc<N, kLines16, P, true, false>;
-            const size_t smem = E::BYTES + sizeof(float2) * (kLines16 + 1) * N;
+            using E = Tc<N, TcLines<N>::value, P, true, false>;
+            const size_t smem = E::BYTES + sizeof(float2) * (TcLines<N>::value + 1) * N;
             if ((e = set_smem(k_tc_fy<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
-            dim3 grid(c->g.n[2] / kLines16, c->g.n[0] / 2 + 1);
+            dim3 grid(c->g.n[2] / TcLines<N>::value, c->g.n[0] / 2 + 1);
             const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
             launch_pdl(k_tc_fy<N, P>, grid, E::T, smem, c->stream, c->g, c->d_s0, c->d_s1, c->Mh, c->d_tw[1], wy,
                                                           c->d_meta, tab, err);
             break;
         }
         case 2: {
-            using E = Tc<N, kLines16, P, true, true>;
+            using E = Tc<N, TcLinesZ<N>::value, P, true, true>;
             const size_t smem = E::BYTES;
             if ((e = set_smem(k_tc_fz<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
-            dim3 grid(c->g.n[1] / kLines16, c->g.n[0] / 2 + 1);
+            dim3 grid(c->g.n[1] / TcLinesZ<N>::value, c->g.n[0] / 2 + 1);
             const float wx = (float)(two_pi / (c->g.n[0] * c->g.h[0]));
             const float wy = (float)(two_pi / (c->g.n[1] * c->g.h[1]));
             const float wz = (float)(two_pi / (c->g.n[2] * c->g.h[2]));
@@ -707,11 +719,11 @@ cudaError_t run_pass(ftr_ctx* c, int pass, bool launch) {
             break;
         }
         case 3: {
-            using E = Tc<N, kLines16, P, false, true>;
+            using E = Tc<N, TcLines<N>::value, P, false, true>;
             const size_t smem = E::BYTES;
             if ((e = set_smem(k_tc_iy<N, P>, smem, c->device)) != cudaSuccess) return e;
             if (!launch) return cudaSuccess;
-            dim3 grid(c->g.n[2] / kLines16, c->g.n[0] / 2 + 1);
+            dim3 grid(c->g.n[2] / TcLines<N>::value, c->g.n[0] / 2 + 1);
             launch_pdl(k_tc_iy<N, P>, grid, E::T, smem, c->stream, c->g, c->d_s1, c->d_s0, c->d_tw[1], tab, err);
             break;
         }
