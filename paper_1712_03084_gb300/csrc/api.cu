@@ -253,6 +253,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_ticket);
     dfree(c->d_mc_blk);
     dfree(c->d_mc_bits);
+    dfree(c->d_rowmm);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -381,6 +382,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         ALLOC(c->d_mc_bits, (size_t)c->mc_blocks * wp);
     }
     ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
+    ALLOC(c->d_rowmm, c->mc_blocks);
 #undef ALLOC
     if ((e = cudaMallocHost((void**)&c->h_mc_tot, 4 * sizeof(int))) != cudaSuccess ||
         (e = cudaMallocHost((void**)&c->h_flags, 2 * sizeof(int))) != cudaSuccess) {
@@ -434,6 +436,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     c->h_flags[0] = c->h_flags[1] = 0;
     cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
     cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
+    cudaMemsetAsync(c->d_brick_cnt, 0, sizeof(int) * c->n_bricks, c->stream);
     double zero2[2] = {0.0, 0.0};
     float zerof[2] = {0.f, 0.f};
     cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
@@ -466,6 +469,8 @@ int ftr_reset(ftr_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->d_dropped, 0, sizeof(unsigned long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wild, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
+    // the ingest counts each point into the bricks its stencil overlaps
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_brick_cnt, 0, sizeof(int) * c->n_bricks, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_reset");
     return FTR_OK;
 }
@@ -707,6 +712,7 @@ cudaError_t launch_transforms(ftr_ctx* c) {
         e = launch_fz2(c);
         prof_end(c, ST_FZ);
         if (e != cudaSuccess) return e;
+        c->rowmm_valid = false;   // the plane-fused inverse writes no row bounds
         prof_begin(c, ST_IYX);
         e = launch_iyx(c);
         prof_end(c, ST_IYX);
@@ -1530,6 +1536,7 @@ int64_t context_bytes(const int n[3], const Caps& k) {
     b += (2 * level_blocks + 8) * (int64_t)sizeof(double);
     b += (6 * mc_blocks + 16) * (int64_t)sizeof(int);
     b += mc_blocks * 16 * (int64_t)sizeof(unsigned);   // inside bits (upper bound)
+    b += mc_blocks * (int64_t)sizeof(float2);          // row min / max of A
     b += k.mc_nodes * (int64_t)sizeof(int4) + k.verts * 6 * (int64_t)sizeof(float) +
          k.tris * 3 * (int64_t)sizeof(int32_t);
     return b;
@@ -1654,6 +1661,7 @@ int ftr_set_indicator(ftr_ctx* c, const float* A, double level) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_levelf, lvf, sizeof(lvf), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "ftr_set_indicator");
+    c->rowmm_valid = false;   // the row bounds belong to the transform's A
     c->solved = true;
     c->meshed = false;
     return FTR_OK;

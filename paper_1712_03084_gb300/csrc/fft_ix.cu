@@ -6,7 +6,10 @@
 // Hermitian extension X[n-k] = conj X[k], Z = X_a + i X_b gives
 // IDFT(Z) = x_a + i x_b.  The imaginary parts of the k_x = 0 and k_x = n_x/2
 // bins are dropped (they are zero for an exactly Hermitian spectrum).  The
-// 1/M normalisation was applied in the z pass.  Output: A[z][y][x].
+// 1/M normalisation was applied in the z pass.  Output: A[z][y][x], and per
+// grid row (y + n_y z) the minimum and maximum of the values written (NaN
+// for both if the row holds a NaN), from which the marching cubes fill rows
+// that lie wholly on one side of the level without reading them.
 #include "fft_common.cuh"
 #include "ftr_internal.h"
 
@@ -19,8 +22,10 @@ constexpr int kHs = kRows + 1;
 
 template <int N>
 __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
-    k_ix(GridDev g, const float2* __restrict__ src, float* __restrict__ A, const float2* __restrict__ tw) {
+    k_ix(GridDev g, const float2* __restrict__ src, float* __restrict__ A, const float2* __restrict__ tw,
+         float2* __restrict__ rowmm) {
     pdl_wait();
+    __shared__ float2 s_mm[kRows][Xchg<N, kLines>::NT];
     using X = Xchg<N, kLines>;
     constexpr int NKX = N / 2 + 1;
     extern __shared__ float2 smem[];
@@ -78,11 +83,34 @@ __global__ void __launch_bounds__(kLines * Xchg<N, kLines>::NT)
         fft_step2<N, kLines, +1>(o, f2, i2, smem);
         float* ra = A + (size_t)N * ((size_t)(y0 + f2) + (size_t)ny * z);
         float* rb = A + (size_t)N * ((size_t)(y0 + f2 + kLines) + (size_t)ny * z);
+        float mna = INFINITY, mxa = -INFINITY, mnb = INFINITY, mxb = -INFINITY;
+        bool nan = false;
 #pragma unroll
         for (int k2 = 0; k2 < X::N2; ++k2) {
             st_l2hint(ra + i2 + X::N1 * k2, o[k2].x, pout);
             st_l2hint(rb + i2 + X::N1 * k2, o[k2].y, pout);
+            mna = fminf(mna, o[k2].x);
+            mxa = fmaxf(mxa, o[k2].x);
+            mnb = fminf(mnb, o[k2].y);
+            mxb = fmaxf(mxb, o[k2].y);
+            nan |= (o[k2].x != o[k2].x) | (o[k2].y != o[k2].y);
         }
+        if (nan) mna = mxa = mnb = mxb = NAN;     // NaN bounds: the row is read in full
+        s_mm[f2][i2] = make_float2(mna, mxa);
+        s_mm[f2 + kLines][i2] = make_float2(mnb, mxb);
+    }
+    __syncthreads();
+    if (tid < kRows) {
+        float mn = INFINITY, mx = -INFINITY;
+        bool nan = false;
+#pragma unroll
+        for (int i = 0; i < X::N1; ++i) {
+            const float2 m = s_mm[tid][i];
+            nan |= m.x != m.x;
+            mn = fminf(mn, m.x);
+            mx = fmaxf(mx, m.y);
+        }
+        rowmm[(size_t)(y0 + tid) + (size_t)ny * z] = nan ? make_float2(NAN, NAN) : make_float2(mn, mx);
     }
 }
 
@@ -97,8 +125,9 @@ cudaError_t run_ix(ftr_ctx* c) {
         attr_done[c->device & 63] = true;
     }
     dim3 grid(c->g.n[1] / kRows, c->g.n[2]);
-    launch_pdl(k_ix<N>, grid, kLines * X::NT, smem, c->stream, c->g, c->d_s0, c->d_A, c->d_tw[0]);
+    launch_pdl(k_ix<N>, grid, kLines * X::NT, smem, c->stream, c->g, c->d_s0, c->d_A, c->d_tw[0], c->d_rowmm);
     c->launches++;
+    c->rowmm_valid = true;
     return cudaGetLastError();
 }
 
@@ -107,7 +136,10 @@ cudaError_t run_ix(ftr_ctx* c) {
 cudaError_t fft_ix_init(const float2* w96) { return upload_w96_table(w96); }
 
 cudaError_t launch_ix(ftr_ctx* c) {
-    if (c->p.precision != FTR_PREC_FP32) return launch_tc_pass(c, 4);
+    if (c->p.precision != FTR_PREC_FP32) {
+        c->rowmm_valid = false;   // the tensor-core x inverse writes no row bounds
+        return launch_tc_pass(c, 4);
+    }
     switch (c->g.n[0]) {
         case 32: return run_ix<32>(c);
         case 48: return run_ix<48>(c);

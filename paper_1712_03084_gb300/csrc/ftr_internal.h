@@ -167,6 +167,8 @@ struct ftr_ctx {
     int mc_blocks = 0;             // grid rows n_y n_z
     int* d_mc_blk = nullptr;       // 3 x mc_blocks ints: tile and group sums of the marching-cubes count
     unsigned* d_mc_bits = nullptr; // inside bits, 32 nodes per word, rows padded to a power-of-two word count
+    float2* d_rowmm = nullptr;     // per grid row (y + n_y z): min and max of A, written with A by the x inverse
+    bool rowmm_valid = false;      // d_rowmm belongs to the current A (the fp32 five-pass x inverse wrote it)
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
     int* h_flags = nullptr;        // pinned: the device wait flags (tensor-core, bulk copy) of the last frame

@@ -77,9 +77,13 @@ __device__ __forceinline__ int ntri_of(int cls) { return (cls == 0 || cls == 255
 // n_x); rows are `wp` words apart (wp = the words per row rounded up to a
 // power of two).  One warp per row, one ballot per word.
 // It also zeroes `zero[0 .. nzero)` (the group sums of k_mc_count_tiles).
+// rowmm (nullable): per row the minimum and maximum of A; a row whose maximum
+// is below the level, or whose minimum is at or above it, gets its words
+// without reading A (the same bits: every node of the row decides alike).
 __global__ void __launch_bounds__(kMcThreads) k_mc_bits(GridDev g, const float* __restrict__ A,
                                                         const float* __restrict__ levelf, unsigned* __restrict__ bits,
-                                                        int nrows, int wp, int* __restrict__ zero, int nzero) {
+                                                        int nrows, int wp, int* __restrict__ zero, int nzero,
+                                                        const float2* __restrict__ rowmm) {
     pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * blockDim.x) zero[i] = 0;
     const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
@@ -89,6 +93,17 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_bits(GridDev g, const float* 
     const int nx = g.n[0];
     const float* a = A + (int64_t)row * nx;
     const int nw = (nx + 31) >> 5;
+    if (rowmm) {
+        const float2 mm = rowmm[row];
+        if (mm.y < L || mm.x >= L) {            // false for NaN bounds
+            if (lane < wp) {
+                unsigned word = 0u;
+                if (lane < nw && mm.x >= L) word = (32 * (lane + 1) <= nx) ? 0xffffffffu : ((1u << (nx - 32 * lane)) - 1u);
+                bits[(int64_t)row * wp + lane] = word;
+            }
+            return;
+        }
+    }
     unsigned mine = 0u;
     // up to 8 words per batch: all loads are issued before the first ballot
     for (int w0 = 0; w0 < nw; w0 += 8) {
@@ -289,9 +304,17 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const u
     int3 base;
     block_scan3(pre, base, sh);
     const int64_t t = (int64_t)tile * blockDim.x + threadIdx.x;
-    const WordCounts wc = word_counts(g, bits, t, nrows, wp, s_ntri);
-    int3 tot;
-    const int3 ex = block_scan3(wc.c, tot, sh);
+    // a tile the count found empty (most of the grid) has only its rows'
+    // offsets to write
+    const int4 mine = agg[tile];
+    WordCounts wc;
+    int3 tot = make_int3(0, 0, 0), ex = make_int3(0, 0, 0);
+    if ((mine.x | mine.y | mine.z) != 0) {
+        wc = word_counts(g, bits, t, nrows, wp, s_ntri);
+        ex = block_scan3(wc.c, tot, sh);
+    } else {
+        wc.act = 0u;
+    }
     const int row = (int)(t / wp), w = (int)(t % wp);
     int ja = base.x + ex.x, jv = base.y + ex.y, jt = base.z + ex.z;
     if (w == 0 && row < nrows) {
@@ -478,7 +501,8 @@ static int mc_groups(int ntiles) { return (ntiles + kMcGroup - 1) / kMcGroup; }
 cudaError_t launch_mc_bits(ftr_ctx* c) {
     const int nr = c->mc_blocks;
     launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
-               c->d_mc_bits, nr, mc_words(c->g.n[0]), (int*)nullptr, 0);
+               c->d_mc_bits, nr, mc_words(c->g.n[0]), (int*)nullptr, 0,
+               (const float2*)(c->rowmm_valid ? c->d_rowmm : nullptr));
     c->launches++;
     return cudaGetLastError();
 }
@@ -494,7 +518,8 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
     int* sup = c->d_mc_blk + 4 * ntiles;
     prof_begin(c, ST_MC_COUNT);
     launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
-               c->d_mc_bits, nr, wp, sup, 4 * mc_groups(ntiles));
+               c->d_mc_bits, nr, wp, sup, 4 * mc_groups(ntiles),
+               (const float2*)(c->rowmm_valid ? c->d_rowmm : nullptr));
     launch_pdl(k_mc_count_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, agg,
                sup);
     c->launches += 2;

@@ -7,8 +7,9 @@
 // cut into 8^3-node bricks; only bricks touched by some stencil get storage.
 // Per frame:
 //   ingest  point -> (floor t, t - floor t, W, N); t as a float pair, the
-//           float64 path only within 1e-5 of a decision
-//   count   per point, +1 on every brick its stencil overlaps
+//           float64 path only within 1e-5 of a decision; an accepted point
+//           adds 1 to every brick its stencil overlaps (counts zeroed when
+//           the frame is reset)
 //   scan    256-brick tiles: per-tile sums, then each tile adds the sums
 //           before it and writes brick offsets, a dense slot per touched
 //           brick and the accumulation chunks (no single-CTA scan)
@@ -82,12 +83,31 @@ __device__ __forceinline__ bool node_t_pair(float x, float bmin, float ih, float
     return true;
 }
 
+// Brick range [lo, hi] per axis that the point's stencil overlaps.
+__device__ __forceinline__ bool stencil_bricks(const int4 b, int mode, int lo[3], int hi[3]) {
+    if (!(b.w & 1)) return false;
+    const int bb[3] = {b.x, b.y, b.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (mode == FTR_SPLAT_WEIGHTED) {
+            lo[c] = (bb[c] - 1) >> 3;
+            hi[c] = (bb[c] + 2) >> 3;
+        } else {
+            int node = bb[c] + ((b.w >> (1 + c)) & 1);
+            lo[c] = hi[c] = node >> 3;
+        }
+    }
+    return true;
+}
+
 // n_dev (nullable): the point count on the device; n then only bounds it.
 // One point: t per axis with every decision equal to the float64 one, the
 // acceptance test, and the point record at slot `dst`.
+// An accepted point also counts itself into every brick its stencil overlaps
+// (cnt: per-brick point counts of the frame, zeroed when the frame starts).
 __device__ __forceinline__ void ingest_one(const float* p, const float* q, const float* wp, int64_t dst, const GridDev& g,
                                            int4* pbase, float4* pfrac, float4* pnrm, unsigned long long* dropped,
-                                           int* wild_weights) {
+                                           int* wild_weights, int* cnt) {
     bool ok = true;
     int fl[3] = {0, 0, 0};
     float fr[3] = {0.f, 0.f, 0.f};
@@ -122,7 +142,14 @@ __device__ __forceinline__ void ingest_one(const float* p, const float* q, const
         atomicAdd(dropped, 1ull);
         fl[0] = fl[1] = fl[2] = 0;
     }
-    pbase[dst] = make_int4(fl[0], fl[1], fl[2], ok ? (1 | (up << 1)) : 0);
+    const int4 rec = make_int4(fl[0], fl[1], fl[2], ok ? (1 | (up << 1)) : 0);
+    pbase[dst] = rec;
+    int lo[3], hi[3];
+    if (stencil_bricks(rec, g.mode, lo, hi)) {
+        for (int bz = lo[2]; bz <= hi[2]; ++bz)
+            for (int by = lo[1]; by <= hi[1]; ++by)
+                for (int bx = lo[0]; bx <= hi[0]; ++bx) atomicAdd(&cnt[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
+    }
     const float wi = wp ? *wp : 1.0f;
     if (ok && !(wi >= 0.f && wi <= 1.f)) atomicOr(wild_weights, 1);   // outside the fast path's range
     pfrac[dst] = make_float4(fr[0], fr[1], fr[2], wi);
@@ -132,19 +159,20 @@ __device__ __forceinline__ void ingest_one(const float* p, const float* q, const
 __global__ void k_ingest(const float* __restrict__ pts, const float* __restrict__ nrm,
                          const float* __restrict__ w, int64_t n, int64_t base, GridDev g, int4* pbase,
                          float4* pfrac, float4* pnrm, unsigned long long* dropped, int* wild_weights,
-                         int64_t* npts_dev, const int* __restrict__ n_dev) {
+                         int64_t* npts_dev, const int* __restrict__ n_dev, int* cnt) {
     pdl_wait();
     if (n_dev) n = min(n, (int64_t)*n_dev);
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *npts_dev = base + n;   // points stored so far: later kernels read the count here
     if (i >= n) return;
-    ingest_one(pts + 3 * i, nrm + 3 * i, w ? w + i : nullptr, base + i, g, pbase, pfrac, pnrm, dropped, wild_weights);
+    ingest_one(pts + 3 * i, nrm + 3 * i, w ? w + i : nullptr, base + i, g, pbase, pfrac, pnrm, dropped, wild_weights,
+               cnt);
 }
 
 // Several point sets in one launch: thread i ingests point i of the
 // concatenation of the sets (set order, as separate launches would store them).
 __global__ void k_ingest_sets(IngestSets S, GridDev g, int4* pbase, float4* pfrac, float4* pnrm,
-                              unsigned long long* dropped, int* wild_weights, int64_t* npts_dev) {
+                              unsigned long long* dropped, int* wild_weights, int64_t* npts_dev, int* cnt) {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *npts_dev = S.base + S.off[S.k];
@@ -153,41 +181,11 @@ __global__ void k_ingest_sets(IngestSets S, GridDev g, int4* pbase, float4* pfra
     while (s + 1 < S.k && i >= S.off[s + 1]) ++s;
     const int64_t j = i - S.off[s];
     ingest_one(S.pts[s] + 3 * j, S.nrm[s] + 3 * j, S.w[s] ? S.w[s] + j : nullptr, S.base + i, g, pbase, pfrac, pnrm,
-               dropped, wild_weights);
-}
-
-// Brick range [lo, hi] per axis that the point's stencil overlaps.
-__device__ __forceinline__ bool stencil_bricks(const int4 b, int mode, int lo[3], int hi[3]) {
-    if (!(b.w & 1)) return false;
-    const int bb[3] = {b.x, b.y, b.z};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (mode == FTR_SPLAT_WEIGHTED) {
-            lo[c] = (bb[c] - 1) >> 3;
-            hi[c] = (bb[c] + 2) >> 3;
-        } else {
-            int node = bb[c] + ((b.w >> (1 + c)) & 1);
-            lo[c] = hi[c] = node >> 3;
-        }
-    }
-    return true;
+               dropped, wild_weights, cnt);
 }
 
 // Grid-stride over the stored points; the count is read on the device, so the
 // launch does not depend on it.
-__global__ void k_brick_count(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
-                              int* cnt) {
-    pdl_wait();
-    const int64_t n = *npts;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int lo[3], hi[3];
-        if (!stencil_bricks(pbase[i], g.mode, lo, hi)) continue;
-        for (int bz = lo[2]; bz <= hi[2]; ++bz)
-            for (int by = lo[1]; by <= hi[1]; ++by)
-                for (int bx = lo[0]; bx <= hi[0]; ++bx) atomicAdd(&cnt[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
-    }
-}
-
 __global__ void k_brick_fill(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
                              int* cursor, int* entries) {
     pdl_wait();
@@ -615,7 +613,8 @@ cudaError_t launch_ingest(ftr_ctx* c, const float* pts, const float* nrm, const 
     if (n == 0) return cudaSuccess;
     // small CTAs spread the few float64 operations per point over every SM
     launch_pdl(k_ingest, blocks_for(n, 32), 32, 0, c->stream, pts, nrm, w, n, c->n_pts, c->g, c->pts.base, c->pts.frac,
-                                                       c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts, n_dev);
+                                                       c->pts.nrm, c->d_dropped, c->d_wild, c->d_npts, n_dev,
+                                                       c->d_brick_cnt);
     c->launches++;
     return cudaGetLastError();
 }
@@ -624,7 +623,7 @@ cudaError_t launch_ingest_sets(ftr_ctx* c, const IngestSets& S) {
     const int64_t n = S.off[S.k];
     if (n == 0) return cudaSuccess;
     launch_pdl(k_ingest_sets, blocks_for(n, 32), 32, 0, c->stream, S, c->g, c->pts.base, c->pts.frac, c->pts.nrm,
-               c->d_dropped, c->d_wild, c->d_npts);
+               c->d_dropped, c->d_wild, c->d_npts, c->d_brick_cnt);
     c->launches++;
     return cudaGetLastError();
 }
@@ -635,10 +634,7 @@ cudaError_t launch_splat(ftr_ctx* c) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     if (sms <= 0) sms = 152;
     prof_begin(c, ST_SPLAT_BIN);
-    if ((e = cudaMemsetAsync(c->d_brick_cnt, 0, sizeof(int) * c->n_bricks, c->stream)) != cudaSuccess) return e;
-    launch_pdl(k_brick_count, sms * 2, 256, 0, c->stream, c->pts.base, c->d_npts, c->g, c->d_brick_cnt);
-    c->launches++;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the per-brick point counts were taken by the ingest
     const int ntiles = (c->n_bricks + kTile - 1) / kTile;
     launch_pdl(k_brick_tile_sums, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->d_tile, c->d_meta);
     launch_pdl(k_brick_tile_write, ntiles, kScanT, 0, c->stream, c->d_brick_cnt, c->n_bricks, c->g.nb[0] * c->g.nb[1],
