@@ -179,6 +179,12 @@ cudaError_t grow_points(ftr_ctx* c, int64_t need) {
     return cudaSuccess;
 }
 
+int64_t heavy_capacity(int64_t points) {
+    int64_t cap = 64;
+    while (cap < 8 * points / kSplatChunk + 1) cap *= 2;
+    return cap;
+}
+
 cudaError_t grow_entries(ftr_ctx* c, int64_t need) {
     if (need <= c->cap_entries) return cudaSuccess;
     c->graph_valid = false;
@@ -196,9 +202,18 @@ cudaError_t grow_entries(ftr_ctx* c, int64_t need) {
         if ((e = dalloc(&c->d_unit_slot, (size_t)units)) != cudaSuccess) return e;
         c->cap_units = units;
     }
-    // a heavy brick has more than one chunk of pairs: at most cap / chunk of them
-    const int64_t heavy = cap / kSplatChunk + 1;
+    return e;
+}
+
+// Accumulators of the heavy bricks (more than one chunk of pairs): at most
+// pairs / chunk of them, with at most 8 pairs per point (every point's stencil
+// overlaps at most 8 bricks); the capacity grows in powers of two.
+cudaError_t grow_heavy(ftr_ctx* c, int64_t points) {
+    const int64_t heavy = heavy_capacity(points);
+    cudaError_t e = cudaSuccess;
     if (heavy > c->cap_heavy) {
+        c->graph_valid = false;
+        cudaStreamSynchronize(c->stream);
         dfree(c->d_heavy_acc);
         dfree(c->d_heavy_done);
         if ((e = dalloc(&c->d_heavy_acc, (size_t)heavy * 4 * kBrickVox)) != cudaSuccess) return e;
@@ -254,6 +269,7 @@ void free_all(ftr_ctx* c) {
     dfree(c->d_mc_blk);
     dfree(c->d_mc_bits);
     dfree(c->d_rowmm);
+    dfree(c->d_mc_word);
     dfree(c->d_mc_off);
     if (c->h_mc_tot) cudaFreeHost(c->h_mc_tot);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -380,6 +396,7 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
         int wp = 1;
         while (wp < (grid_n[0] + 31) / 32) wp <<= 1;
         ALLOC(c->d_mc_bits, (size_t)c->mc_blocks * wp);
+        ALLOC(c->d_mc_word, (size_t)c->mc_blocks * wp);
     }
     ALLOC(c->d_mc_off, 3 * (c->mc_blocks + 1) + 3);
     ALLOC(c->d_rowmm, c->mc_blocks);
@@ -437,6 +454,11 @@ int ftr_create(const int grid_n[3], const float bbox[6], const ftr_params* p, ft
     cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
     cudaMemsetAsync(c->d_npts, 0, sizeof(int64_t), c->stream);
     cudaMemsetAsync(c->d_brick_cnt, 0, sizeof(int) * c->n_bricks, c->stream);
+    {
+        int wp = 1;
+        while (wp < (c->g.n[0] + 31) / 32) wp <<= 1;
+        cudaMemsetAsync(c->d_mc_word, 0, sizeof(int2) * (size_t)c->mc_blocks * wp, c->stream);
+    }
     double zero2[2] = {0.0, 0.0};
     float zerof[2] = {0.f, 0.f};
     cudaMemcpyAsync(c->d_level, zero2, sizeof(zero2), cudaMemcpyHostToDevice, c->stream);
@@ -747,6 +769,7 @@ int ftr_solve(ftr_ctx* c, double* iso_level_out) {
     cudaError_t e;
     // each point touches at most 8 bricks
     if ((e = grow_entries(c, 8 * c->n_pts + 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: entries");
+    if ((e = grow_heavy(c, c->n_pts)) != cudaSuccess) return cuda_fail(c, e, "ftr_solve: accumulators");
     c->solved = false;
     c->meshed = false;
     if (!c->v_external) {
@@ -1030,6 +1053,7 @@ int ftr_frame_launch(ftr_ctx* c, const ftr_view* views, int k, float depth_tol, 
     cudaError_t e;
     // every buffer the graph captures is sized here, outside the capture
     if ((e = grow_entries(c, 8 * c->n_pts + 1)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
+    if ((e = grow_heavy(c, c->n_pts)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
     if (c->cap_verts == 0) {
         const int64_t guess = c->M / 256 + 4096;
         if ((e = grow_mesh(c, guess, guess, 2 * guess)) != cudaSuccess) return cuda_fail(c, e, "ftr_frame_launch");
@@ -1537,6 +1561,7 @@ int64_t context_bytes(const int n[3], const Caps& k) {
     b += (6 * mc_blocks + 16) * (int64_t)sizeof(int);
     b += mc_blocks * 16 * (int64_t)sizeof(unsigned);   // inside bits (upper bound)
     b += mc_blocks * (int64_t)sizeof(float2);          // row min / max of A
+    b += mc_blocks * 16 * (int64_t)sizeof(int2);       // per-word record index and mask (upper bound)
     b += k.mc_nodes * (int64_t)sizeof(int4) + k.verts * 6 * (int64_t)sizeof(float) +
          k.tris * 3 * (int64_t)sizeof(int32_t);
     return b;
@@ -1581,7 +1606,7 @@ int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pi
     k.entries = pow2_cap(8 * pts + 1, 1 << 18);
     const int64_t nb = (int64_t)(grid_n[0] / kBrick) * (grid_n[1] / kBrick) * (grid_n[2] / kBrick);
     k.units = nb + k.entries / kSplatChunk + 2;
-    k.heavy = k.entries / kSplatChunk + 1;
+    k.heavy = heavy_capacity(pts);
     k.raw = depth_pixels;
     k.raw_tiles = depth_pixels > 0 ? depth_pixels / 128 + 16 * 1024 : 0;
     // mesh buffers grow to 1.5 x what a frame needs (+1024); active nodes <= vertices

@@ -170,6 +170,7 @@ struct ftr_ctx {
     float2* d_rowmm = nullptr;     // per grid row (y + n_y z): min and max of A, written with A by the x inverse
     bool rowmm_valid = false;      // d_rowmm belongs to the current A (the fp32 five-pass x inverse wrote it)
     int* d_mc_off = nullptr;       // 3 x (mc_blocks + 1)
+    int2* d_mc_word = nullptr;     // per (row, 32-node word) of a tile with surface: first record index, active mask
     int* h_mc_tot = nullptr;       // pinned: totals (active, verts, tris)
     int* h_flags = nullptr;        // pinned: the device wait flags (tensor-core, bulk copy) of the last frame
     int4* d_mc_nodes = nullptr;

@@ -19,14 +19,16 @@
 //          or lower corner of a cell with triangles), vertices, triangles;
 //          also summed per group of 256 tiles
 //   emit   per tile: its offset from the group and tile sums before it, a
-//          CTA scan of its counts, the rows' offsets, and per active node
-//          in x order one 16-byte record (node, edge bits | class << 8,
-//          first vertex, first triangle)
+//          CTA scan of its counts, the rows' offsets, per active node in x
+//          order one 16-byte record (node, edge bits | class << 8, first
+//          vertex, first triangle), and per word with active nodes its first
+//          record index and active mask (a tile with no active node writes
+//          only its rows' offsets)
 //   tris   one thread per active node: the vertices of its crossing edges
 //          (t = (L - A0)/(A1 - A0), normal -grad A by central differences,
 //          one-sided at the border, lerped), then its triangles' corners
-//          from the case table; an edge owned by another node is found by a
-//          short scan of that node's row records.
+//          from the case table; the record of an edge's owner node is its
+//          word's first record plus the active nodes before it in the word.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -86,40 +88,41 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_bits(GridDev g, const float* 
                                                         const float2* __restrict__ rowmm) {
     pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * blockDim.x) zero[i] = 0;
-    const int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5);
-    if (row >= nrows) return;                    // warp-uniform
     const int lane = threadIdx.x & 31;
     const float L = levelf[0];
     const int nx = g.n[0];
-    const float* a = A + (int64_t)row * nx;
     const int nw = (nx + 31) >> 5;
-    if (rowmm) {
-        const float2 mm = rowmm[row];
-        if (mm.y < L || mm.x >= L) {            // false for NaN bounds
-            if (lane < wp) {
-                unsigned word = 0u;
-                if (lane < nw && mm.x >= L) word = (32 * (lane + 1) <= nx) ? 0xffffffffu : ((1u << (nx - 32 * lane)) - 1u);
-                bits[(int64_t)row * wp + lane] = word;
+    // one warp per row (warp-uniform); the stride covers any grid size
+    for (int row = blockIdx.x * kRowsPerCta + (threadIdx.x >> 5); row < nrows; row += gridDim.x * kRowsPerCta) {
+        const float* a = A + (int64_t)row * nx;
+        if (rowmm) {
+            const float2 mm = rowmm[row];
+            if (mm.y < L || mm.x >= L) {            // false for NaN bounds
+                if (lane < wp) {
+                    unsigned word = 0u;
+                    if (lane < nw && mm.x >= L) word = (32 * (lane + 1) <= nx) ? 0xffffffffu : ((1u << (nx - 32 * lane)) - 1u);
+                    bits[(int64_t)row * wp + lane] = word;
+                }
+                continue;
             }
-            return;
         }
-    }
-    unsigned mine = 0u;
-    // up to 8 words per batch: all loads are issued before the first ballot
-    for (int w0 = 0; w0 < nw; w0 += 8) {
-        float v[8];
+        unsigned mine = 0u;
+        // up to 8 words per batch: all loads are issued before the first ballot
+        for (int w0 = 0; w0 < nw; w0 += 8) {
+            float v[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int x = 32 * (w0 + k) + lane;
-            v[k] = (w0 + k < nw && x < nx) ? a[x] : -INFINITY;
-        }
+            for (int k = 0; k < 8; ++k) {
+                const int x = 32 * (w0 + k) + lane;
+                v[k] = (w0 + k < nw && x < nx) ? a[x] : -INFINITY;
+            }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const unsigned b = __ballot_sync(0xffffffffu, v[k] >= L);
-            if (lane == w0 + k) mine = b;
+            for (int k = 0; k < 8; ++k) {
+                const unsigned b = __ballot_sync(0xffffffffu, v[k] >= L);
+                if (lane == w0 + k) mine = b;
+            }
         }
+        if (lane < wp) bits[(int64_t)row * wp + lane] = lane < nw ? mine : 0u;
     }
-    if (lane < wp) bits[(int64_t)row * wp + lane] = lane < nw ? mine : 0u;
 }
 
 // Per (row, word): the masks of the nodes of word w that own a crossing
@@ -280,7 +283,8 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const u
                                                               int nrows, int wp, int ntiles,
                                                               const int4* __restrict__ agg,
                                                               const int4* __restrict__ sup, int* __restrict__ off,
-                                                              int4* __restrict__ nodes, int cap_nodes) {
+                                                              int4* __restrict__ nodes, int cap_nodes,
+                                                              int2* __restrict__ wordinfo) {
     pdl_wait();
     __shared__ unsigned char s_ntri[256];
     __shared__ int3 sh[kMcThreads / 32];
@@ -331,6 +335,9 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const u
         off[3 * (nrows + 1) + 1] = all.y;
         off[3 * (nrows + 1) + 2] = all.z;
     }
+    // the word's first record and its active nodes: the triangle pass finds
+    // a corner's owner record from these without scanning the row
+    if (wc.act) wordinfo[t] = make_int2(ja, (int)wc.act);
     const int64_t rowbase = (int64_t)row * g.n[0];
     unsigned rem = wc.act;
     while (rem) {
@@ -395,11 +402,13 @@ __device__ __forceinline__ void emit_vertices(const GridDev& g, const float* __r
 }
 
 // The owner of a triangle corner is this node or a node of the same row
-// (+x), of the next row (+y) or of the next plane (+z): its record is found
-// by a short scan of that row's records, whose range comes from the row
-// offsets of the scan (off_rows[row] .. off_rows[row + 1]).
+// (+x), of the next row (+y) or of the next plane (+z).  The owner is active
+// (it owns the crossing edge), so its word was written by the emit pass:
+// its record index is the word's first record plus the active nodes before
+// it in the word.
 __device__ __forceinline__ void tris_of_node(const GridDev& g, const int4* __restrict__ nodes, int r,
-                                                  const int* __restrict__ off_rows, int32_t* __restrict__ tris) {
+                                             const int2* __restrict__ wordinfo, int wp, int n_nodes,
+                                             int32_t* __restrict__ tris) {
     const int4 rec = nodes[r];
     const int cls = rec.y >> 8;
     const int nt = ntri_of(cls);
@@ -420,10 +429,10 @@ __device__ __forceinline__ void tris_of_node(const GridDev& g, const int4* __res
             if (ox | oy | oz) {
                 const int orow = row + oy + ny * oz;
                 const int ox_node = x + ox;
-                int k = off_rows[orow];
-                const int kend = off_rows[orow + 1];
-                while (k < kend - 1 && nodes[k].x - orow * nx < ox_node) ++k;
-                orec = nodes[k];
+                const int2 wi = wordinfo[(int64_t)orow * wp + (ox_node >> 5)];
+                const unsigned before = (unsigned)wi.y & ((1u << (ox_node & 31)) - 1u);
+                // clamped: an inconsistent lookup gives a wrong index, never an access outside the records
+                orec = nodes[min(max(wi.x + __popc(before), 0), n_nodes - 1)];
             }
             const int below = (orec.y & 7) & ((1 << axis) - 1);
             tris[3 * (int64_t)(rec.w + t) + j] = orec.z + __popc(below);
@@ -436,8 +445,9 @@ __device__ __forceinline__ void tris_of_node(const GridDev& g, const int4* __res
 __global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const float* __restrict__ A,
                                                  const float* __restrict__ levelf, const int4* __restrict__ nodes,
                                                  const int* __restrict__ totals, int cap_nodes, int cap_tris,
-                                                 const int* __restrict__ off_rows, int32_t* __restrict__ tris,
-                                                 float* __restrict__ verts, float* __restrict__ vnrm, int cap_v) {
+                                                 const int2* __restrict__ wordinfo, int wp,
+                                                 int32_t* __restrict__ tris, float* __restrict__ verts,
+                                                 float* __restrict__ vnrm, int cap_v) {
     pdl_wait();
     const int n_nodes = totals[0];
     if (n_nodes > cap_nodes || totals[2] > cap_tris) return;   // the host grows the buffers and runs again
@@ -451,7 +461,7 @@ __global__ void __launch_bounds__(256) k_mc_tris(GridDev g, const float* __restr
             const int q[3] = {rec.x - row * nx, row % ny, row / ny};
             emit_vertices(g, A, Ln, (int64_t)rec.x, q, flags, rec.z, cap_v, verts, vnrm);
         }
-        tris_of_node(g, nodes, r, off_rows, tris);
+        tris_of_node(g, nodes, r, wordinfo, wp, n_nodes, tris);
     }
 }
 
@@ -498,9 +508,15 @@ static int mc_words(int nx) {
 static int mc_tiles(int nrows, int wp) { return (int)(((int64_t)nrows * wp + kMcThreads - 1) / kMcThreads); }
 static int mc_groups(int ntiles) { return (ntiles + kMcGroup - 1) / kMcGroup; }
 
+// CTAs of the inside-bit pass: one warp per row.  (A grid of one resident
+// wave taking rows in a stride was as fast for one frame and 4-7 % slower
+// when frames of several contexts overlap: short CTAs fill in around other
+// kernels' CTAs.)
+static unsigned mc_bits_grid(int nrows) { return (unsigned)((nrows + kRowsPerCta - 1) / kRowsPerCta); }
+
 cudaError_t launch_mc_bits(ftr_ctx* c) {
     const int nr = c->mc_blocks;
-    launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
+    launch_pdl(k_mc_bits, mc_bits_grid(nr), kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
                c->d_mc_bits, nr, mc_words(c->g.n[0]), (int*)nullptr, 0,
                (const float2*)(c->rowmm_valid ? c->d_rowmm : nullptr));
     c->launches++;
@@ -517,7 +533,7 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
     int4* agg = reinterpret_cast<int4*>(c->d_mc_blk);
     int* sup = c->d_mc_blk + 4 * ntiles;
     prof_begin(c, ST_MC_COUNT);
-    launch_pdl(k_mc_bits, (nr + kRowsPerCta - 1) / kRowsPerCta, kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
+    launch_pdl(k_mc_bits, mc_bits_grid(nr), kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
                c->d_mc_bits, nr, wp, sup, 4 * mc_groups(ntiles),
                (const float2*)(c->rowmm_valid ? c->d_rowmm : nullptr));
     launch_pdl(k_mc_count_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, agg,
@@ -546,7 +562,7 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int4* sup = reinterpret_cast<const int4*>(c->d_mc_blk + 4 * ntiles);
     prof_begin(c, ST_MC_EMIT);
     launch_pdl(k_mc_emit_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, ntiles,
-               agg, sup, c->d_mc_off, c->d_mc_nodes, (int)c->cap_mc_nodes);
+               agg, sup, c->d_mc_off, c->d_mc_nodes, (int)c->cap_mc_nodes, c->d_mc_word);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);
@@ -555,8 +571,8 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     prof_begin(c, ST_MC_TRIS);
     launch_pdl(k_mc_tris, (sms > 0 ? sms : 152) * 4, 256, 0, c->stream, c->g, c->d_A, c->d_levelf, c->d_mc_nodes,
-               c->d_mc_off + 3 * (nr + 1), (int)c->cap_mc_nodes, (int)c->cap_tris, c->d_mc_off, c->d_tris, c->d_verts,
-               c->d_vnrm, (int)c->cap_verts);
+               c->d_mc_off + 3 * (nr + 1), (int)c->cap_mc_nodes, (int)c->cap_tris, (const int2*)c->d_mc_word, wp,
+               c->d_tris, c->d_verts, c->d_vnrm, (int)c->cap_verts);
     c->launches++;
     e = cudaGetLastError();
     prof_end(c, ST_MC_TRIS);

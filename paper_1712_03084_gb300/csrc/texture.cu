@@ -188,50 +188,54 @@ __global__ void __launch_bounds__(256) k_texture(ViewSet vs, const float* __rest
                                                  uint8_t* __restrict__ rgbout, uint8_t* __restrict__ texout) {
     pdl_wait();
     if (nv_dev) nv = min(nv, (int64_t)nv_dev[0]);
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t / G;
-    const int k = (int)(t % G);
-    const bool live = i < nv && k < vs.k;
-    float wk = 0.f, ur = -1.f, vr = -1.f, rgb[3] = {0.f, 0.f, 0.f};
-    if (live) {
-        const ViewDev& vw = vs.v[k];
-        const float Xf[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
-        if (!eval_camera_mixed(vw, Xf, (float)tau, tau, wk, ur, vr, rgb)) {
-            const double Xd[3] = {Xf[0], Xf[1], Xf[2]};
-            double wd, ud, vd, cd[3];
-            eval_camera<double>(vw, Xd, tau, wd, ud, vd, cd);
-            wk = (float)wd;
-            ur = (float)ud;
-            vr = (float)vd;
-            rgb[0] = (float)cd[0];
-            rgb[1] = (float)cd[1];
-            rgb[2] = (float)cd[2];
-        }
-        if (wout) wout[i * vs.k + k] = wk;
-        if (uvout) {
-            uvout[2 * (i * vs.k + k)] = ur;
-            uvout[2 * (i * vs.k + k) + 1] = vr;
-        }
-    }
-    float acc[3], wsum = wk > 0.f ? wk : 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = wk > 0.f ? wk * rgb[c] : 0.f;
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) {
-        wsum += __shfl_xor_sync(0xffffffffu, wsum, o, G);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
-    }
-    if (k == 0 && i < nv) {
-        if (rgbout) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float col = wsum > 0.f ? floorf(acc[c] / wsum + 0.5f) : 0.f;
-                col = fminf(fmaxf(col, 0.f), 255.f);
-                rgbout[3 * i + c] = (uint8_t)col;
+    // (vertex, camera) threads; the count is read here, the stride covers any
+    // grid size
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x; t0 < nv * G; t0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        const int64_t i = t / G;
+        const int k = (int)(t % G);
+        const bool live = i < nv && k < vs.k;
+        float wk = 0.f, ur = -1.f, vr = -1.f, rgb[3] = {0.f, 0.f, 0.f};
+        if (live) {
+            const ViewDev& vw = vs.v[k];
+            const float Xf[3] = {verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]};
+            if (!eval_camera_mixed(vw, Xf, (float)tau, tau, wk, ur, vr, rgb)) {
+                const double Xd[3] = {Xf[0], Xf[1], Xf[2]};
+                double wd, ud, vd, cd[3];
+                eval_camera<double>(vw, Xd, tau, wd, ud, vd, cd);
+                wk = (float)wd;
+                ur = (float)ud;
+                vr = (float)vd;
+                rgb[0] = (float)cd[0];
+                rgb[1] = (float)cd[1];
+                rgb[2] = (float)cd[2];
+            }
+            if (wout) wout[i * vs.k + k] = wk;
+            if (uvout) {
+                uvout[2 * (i * vs.k + k)] = ur;
+                uvout[2 * (i * vs.k + k) + 1] = vr;
             }
         }
-        if (texout) texout[i] = wsum > 0.f ? 1 : 0;
+        float acc[3], wsum = wk > 0.f ? wk : 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = wk > 0.f ? wk * rgb[c] : 0.f;
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            wsum += __shfl_xor_sync(0xffffffffu, wsum, o, G);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, G);
+        }
+        if (k == 0 && i < nv) {
+            if (rgbout) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float col = wsum > 0.f ? floorf(acc[c] / wsum + 0.5f) : 0.f;
+                    col = fminf(fmaxf(col, 0.f), 255.f);
+                    rgbout[3 * i + c] = (uint8_t)col;
+                }
+            }
+            if (texout) texout[i] = wsum > 0.f ? 1 : 0;
+        }
     }
 }
 
@@ -244,6 +248,9 @@ cudaError_t run_texture(ftr_ctx* c, const ViewSet& vs, float depth_tol, const fl
     if (nv <= 0) return cudaSuccess;
     prof_begin(c, ST_TEXTURE);
     const int G = vs.k <= 1 ? 1 : (vs.k <= 2 ? 2 : (vs.k <= 4 ? 4 : 8));
+    // a thread per (vertex, camera) of the capacity: short CTAs that end at
+    // once past the count fill in around concurrent frames' kernels (a
+    // one-wave grid-stride launch measured 4-7 % slower with frames in flight)
     const unsigned blocks = (unsigned)((nv * G + 255) / 256);
     const double tau = (double)depth_tol;
     switch (G) {
