@@ -144,11 +144,18 @@ __device__ __forceinline__ void ingest_one(const float* p, const float* q, const
     }
     const int4 rec = make_int4(fl[0], fl[1], fl[2], ok ? (1 | (up << 1)) : 0);
     pbase[dst] = rec;
-    int lo[3], hi[3];
-    if (stencil_bricks(rec, g.mode, lo, hi)) {
-        for (int bz = lo[2]; bz <= hi[2]; ++bz)
-            for (int by = lo[1]; by <= hi[1]; ++by)
-                for (int bx = lo[0]; bx <= hi[0]; ++bx) atomicAdd(&cnt[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
+    // per brick slot k of the at most 2 x 2 x 2 bricks the stencil overlaps,
+    // the lanes counting into the same brick add their number with one atomic
+    const unsigned act = __activemask();
+    int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+    const bool any = stencil_bricks(rec, g.mode, lo, hi);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int bx = lo[0] + (k & 1), by = lo[1] + ((k >> 1) & 1), bz = lo[2] + (k >> 2);
+        const bool valid = any && bx <= hi[0] && by <= hi[1] && bz <= hi[2];
+        const int b = valid ? bx + g.nb[0] * (by + g.nb[1] * bz) : -1;
+        const unsigned peers = __match_any_sync(act, b);
+        if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[b], __popc(peers));
     }
     const float wi = wp ? *wp : 1.0f;
     if (ok && !(wi >= 0.f && wi <= 1.f)) atomicOr(wild_weights, 1);   // outside the fast path's range
@@ -186,19 +193,35 @@ __global__ void k_ingest_sets(IngestSets S, GridDev g, int4* pbase, float4* pfra
 
 // Grid-stride over the stored points; the count is read on the device, so the
 // launch does not depend on it.
+// A warp takes 32 consecutive points (neighbouring pixels of one camera,
+// mostly the same bricks): per brick slot k of the at most 2 x 2 x 2 bricks
+// a stencil overlaps, the lanes that append to the same brick reserve their
+// places with one atomic (the lowest lane's) and write at their rank.
 __global__ void k_brick_fill(const int4* __restrict__ pbase, const int64_t* __restrict__ npts, GridDev g,
                              int* cursor, int* entries) {
     pdl_wait();
     const int64_t n = *npts;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int lo[3], hi[3];
-        if (!stencil_bricks(pbase[i], g.mode, lo, hi)) continue;
-        for (int bz = lo[2]; bz <= hi[2]; ++bz)
-            for (int by = lo[1]; by <= hi[1]; ++by)
-                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
-                    int pos = atomicAdd(&cursor[bx + g.nb[0] * (by + g.nb[1] * bz)], 1);
-                    entries[pos] = (int)i;
-                }
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform loop: every lane reaches each match below
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const int64_t i = i0 + lane;
+        int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+        const bool ok = i < n && stencil_bricks(pbase[i], g.mode, lo, hi);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int bx = lo[0] + (k & 1), by = lo[1] + ((k >> 1) & 1), bz = lo[2] + (k >> 2);
+            const bool valid = ok && bx <= hi[0] && by <= hi[1] && bz <= hi[2];
+            const int b = valid ? bx + g.nb[0] * (by + g.nb[1] * bz) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, b);
+            if (valid) {
+                const int leader = __ffs(peers) - 1;
+                int pos = 0;
+                if (lane == leader) pos = atomicAdd(&cursor[b], __popc(peers));
+                pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+                entries[pos] = (int)i;
+            }
+        }
     }
 }
 
