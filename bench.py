@@ -529,6 +529,7 @@ def run_ours(args, rank, world, local_rank):
     if args.path is not None:
         ctx.set_transform_path(args.path)
     plan = ctx.plan()
+    mc_plan = ctx.mc_plan()
     path = ctx.transform_path()
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -688,6 +689,7 @@ def run_ours(args, rank, world, local_rank):
                    "triangles": int(info["n_tris"]), "cameras": K, "parallelism": f"replicas{world}",
                    "plan": {"lines_per_cta_y_z_iy": list(plan),
                             "transform_path": PATH_NAMES[path],
+                            "marching_cubes_tile_threads_and_triangle_ctas_per_sm": list(mc_plan),
                             "autotune_us_per_launch": [[round(float(v), 2) for v in row] for row in tune_us],
                             "autotune_chain_us": {"five_pass": round(float(chain_us[0]), 2),
                                                   "plane_fused": round(float(chain_us[1]), 2),

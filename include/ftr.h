@@ -333,8 +333,10 @@ int64_t ftr_estimate_bytes(const int grid_n[3], int64_t points, int64_t depth_pi
  * inverse-y passes of the five-pass path (0 = not timed: cached or not a
  * candidate), [12], [13] and [15] microseconds of the five-pass, the
  * plane-fused and the persistent y+z chain (0: not timed), [14] the path
- * kept.  Waits for the stream.  Split precision contexts keep F = 16 and the five passes (their
- * passes have no variants).
+ * kept.  Before the transform timing, when the last frame was solved and
+ * meshed, it also times the marching-cubes block sizes (ftr_set_mc_plan).
+ * Waits for the stream.  Split precision contexts keep F = 16 and the five
+ * passes (their passes have no variants).
  */
 int ftr_autotune(ftr_ctx* ctx, float* report);
 
@@ -346,6 +348,22 @@ int ftr_get_plan(const ftr_ctx* ctx, int* plan);
  * when 16 divides n_z and n_y <= 256, or for the z pass when 16 divides
  * n_y; else FTR_EINVAL. */
 int ftr_set_plan(ftr_ctx* ctx, const int* plan);
+
+/*
+ * Marching-cubes block sizes (Sec. III-B, marching cubes [35]; the sizes are
+ * this library's, the paper names none): plan[0] = (row, 32-node word)
+ * threads per tile of the count and emit passes (128, 256 or 512), plan[1] =
+ * CTAs per SM of the triangle pass (1 to 16, 256 threads each, grid stride).
+ * Every choice gives the same mesh bit for bit: node records, vertex ids and
+ * triangles follow node order, not the tiling.  Defaults 256 and 4;
+ * ftr_autotune times 128/256/512 x 2/4/8 on the last frame's indicator and
+ * level when that frame was solved and meshed and the grid's plans are not
+ * cached yet, and keeps the fastest (cached with the tile plan).  Set:
+ * FTR_EINVAL outside those ranges, FTR_ESTATE while a frame is pending; the
+ * next extraction uses it.
+ */
+int ftr_get_mc_plan(const ftr_ctx* ctx, int* plan);
+int ftr_set_mc_plan(ftr_ctx* ctx, const int* plan);
 
 /*
  * Transform path of the FP32 transforms: 0 = five axis passes, 1 =

@@ -1306,7 +1306,9 @@ int ftr_stats(const ftr_ctx* c, int64_t* points_in, int64_t* points_dropped) {
 
 namespace {
 std::mutex g_plan_mu;
-std::map<std::tuple<int, int, int, int>, std::array<int, 4>> g_plans;   // (device, n) -> lines per CTA, path
+// (device, n) -> lines per CTA of the y, z, inverse-y passes, transform path,
+// marching-cubes tile size and triangle CTAs per SM (0, 0: not timed)
+std::map<std::tuple<int, int, int, int>, std::array<int, 6>> g_plans;
 
 bool valid_lines(int f) { return f == 8 || f == 16 || f == 32; }
 
@@ -1333,6 +1335,24 @@ int ftr_set_plan(ftr_ctx* c, const int* plan) {
             return set_err(c, FTR_EINVAL, "ftr_set_plan: lines per CTA must be 8, 16 or 32 and divide the grid");
     if (c->p.precision != FTR_PREC_FP32) return set_err(c, FTR_EINVAL, "ftr_set_plan: fp32 passes only");
     for (int i = 0; i < 3; ++i) c->plan_lines[i] = plan[i];
+    c->graph_valid = false;
+    return FTR_OK;
+}
+
+int ftr_get_mc_plan(const ftr_ctx* c, int* plan) {
+    if (!c || !plan) return FTR_EINVAL;
+    plan[0] = c->mc_tile;
+    plan[1] = c->mc_tris_per_sm;
+    return FTR_OK;
+}
+
+int ftr_set_mc_plan(ftr_ctx* c, const int* plan) {
+    if (!c || !plan) return FTR_EINVAL;
+    if (!mc_plan_valid(plan[0], plan[1]))
+        return set_err(c, FTR_EINVAL, "ftr_set_mc_plan: tile 128, 256 or 512 and 1 to 16 triangle CTAs per SM");
+    if (c->mesh_pending) return set_err(c, FTR_ESTATE, "ftr_set_mc_plan: a frame is pending");
+    c->mc_tile = plan[0];
+    c->mc_tris_per_sm = plan[1];
     c->graph_valid = false;
     return FTR_OK;
 }
@@ -1402,12 +1422,61 @@ int ftr_autotune(ftr_ctx* c, float* report) {
             if (pth == 2 && !(c->yz_ok && ensure_yz_ring(c) == cudaSuccess)) pth = 0;
             c->fused = (pth == 1 && c->fused_ok) || pth == 2 ? pth : 0;
             if (c->fused != 2) release_yz_ring(c);
+            if (mc_plan_valid(it->second[4], it->second[5])) {
+                c->mc_tile = it->second[4];
+                c->mc_tris_per_sm = it->second[5];
+            }
             c->graph_valid = false;
             return FTR_OK;
         }
     }
     cudaError_t e;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "ftr_autotune");
+    // marching-cubes block sizes, timed on the last frame's indicator and level
+    // while they are still valid (the transform timing below overwrites them):
+    // the count and emit tiles and the triangle pass's CTAs per SM; every
+    // choice gives the same mesh (records, vertices and triangles follow node
+    // order)
+    int mc_best[2] = {0, 0};
+    if (c->solved && c->meshed && c->n_verts > 0) {
+        cudaEvent_t m0, m1;
+        cudaEventCreate(&m0);
+        cudaEventCreate(&m1);
+        const int tiles[3] = {128, 256, 512}, per_sm[3] = {2, 4, 8};
+        float best_us = 1e30f;
+        for (int ti = 0; ti < 3; ++ti)
+            for (int mi = 0; mi < 3; ++mi) {
+                c->mc_tile = tiles[ti];
+                c->mc_tris_per_sm = per_sm[mi];
+                auto run = [&]() {
+                    cudaError_t r = launch_mc_count(c);
+                    return r == cudaSuccess ? launch_mc_emit(c) : r;
+                };
+                if (run() != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaEventRecord(m0, c->stream);
+                for (int r = 0; r < 5; ++r) run();
+                cudaEventRecord(m1, c->stream);
+                if (cudaEventSynchronize(m1) != cudaSuccess) {
+                    cudaEventDestroy(m0);
+                    cudaEventDestroy(m1);
+                    return cuda_fail(c, cudaGetLastError(), "ftr_autotune: marching cubes");
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, m0, m1);
+                if (1000.f * ms / 5 < best_us) {
+                    best_us = 1000.f * ms / 5;
+                    mc_best[0] = tiles[ti];
+                    mc_best[1] = per_sm[mi];
+                }
+            }
+        cudaEventDestroy(m0);
+        cudaEventDestroy(m1);
+        c->mc_tile = mc_best[0] ? mc_best[0] : 256;
+        c->mc_tris_per_sm = mc_best[1] ? mc_best[1] : 4;
+    }
     // the live z-slab of the last solved frame when there is one (the forward
     // passes skip planes outside it), else every plane live; a later splat
     // rewrites these values
@@ -1524,7 +1593,7 @@ int ftr_autotune(ftr_ctx* c, float* report) {
     c->meshed = false;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        g_plans[key] = {best[0], best[1], best[2], path};
+        g_plans[key] = {best[0], best[1], best[2], path, mc_best[0], mc_best[1]};
     }
     return FTR_OK;
 }

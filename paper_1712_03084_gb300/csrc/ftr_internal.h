@@ -165,6 +165,8 @@ struct ftr_ctx {
 
     // marching cubes
     int mc_blocks = 0;             // grid rows n_y n_z
+    int mc_tile = 256;             // (row, word) threads per tile of the count and emit passes: 128, 256, 512
+    int mc_tris_per_sm = 4;        // CTAs per SM of the triangle pass (256 threads each, grid stride)
     int* d_mc_blk = nullptr;       // 3 x mc_blocks ints: tile and group sums of the marching-cubes count
     unsigned* d_mc_bits = nullptr; // inside bits, 32 nodes per word, rows padded to a power-of-two word count
     float2* d_rowmm = nullptr;     // per grid row (y + n_y z): min and max of A, written with A by the x inverse
@@ -321,6 +323,7 @@ cudaError_t launch_tc_pass(ftr_ctx* c, int pass);
 cudaError_t tc_prepare(ftr_ctx* c);
 cudaError_t launch_mc_bits(ftr_ctx* c);        // inside bits A >= L only
 int mc_words_per_row(int nx);                  // padded words per grid row of the inside bits
+bool mc_plan_valid(int tile, int tris_per_sm);
 cudaError_t launch_mc_count(ftr_ctx* c);       // inside bits, then tile and group counts
 cudaError_t launch_mc_emit(ftr_ctx* c);        // offsets and node records, then vertices and triangles
 cudaError_t launch_mc_totals(ftr_ctx* c);      // totals (active, verts, tris) to h_mc_tot

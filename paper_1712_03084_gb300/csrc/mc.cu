@@ -176,7 +176,8 @@ __device__ __forceinline__ int cell_class(const WordMasks& m, int i) {
     return cls;
 }
 
-// Block-wide exclusive scan of 3 ints (kMcThreads threads); returns totals.
+// Block-wide exclusive scan of 3 ints (T threads); returns totals.
+template <int T>
 __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int3 inc = v;
@@ -194,7 +195,7 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
     if (lane == 31) sh[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        int3 w = lane < kMcThreads / 32 ? sh[lane] : make_int3(0, 0, 0);
+        int3 w = lane < T / 32 ? sh[lane] : make_int3(0, 0, 0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int a = __shfl_up_sync(0xffffffffu, w.x, o);
@@ -206,11 +207,11 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
                 w.z += c;
             }
         }
-        if (lane < kMcThreads / 32) sh[lane] = w;
+        if (lane < T / 32) sh[lane] = w;
     }
     __syncthreads();
     const int3 before = wid ? sh[wid - 1] : make_int3(0, 0, 0);
-    total = sh[kMcThreads / 32 - 1];
+    total = sh[T / 32 - 1];
     __syncthreads();
     return make_int3(before.x + inc.x - v.x, before.y + inc.y - v.y, before.z + inc.z - v.z);
 }
@@ -258,18 +259,19 @@ __device__ __forceinline__ WordCounts word_counts(const GridDev& g, const unsign
 
 constexpr int kMcGroup = 256;     // tiles per group sum
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_count_tiles(GridDev g, const unsigned* __restrict__ bits,
+template <int T>
+__global__ void __launch_bounds__(T) k_mc_count_tiles(GridDev g, const unsigned* __restrict__ bits,
                                                                int nrows, int wp, int4* __restrict__ agg,
                                                                int* __restrict__ sup) {
     pdl_wait();
     __shared__ unsigned char s_ntri[256];
-    __shared__ int3 sh[kMcThreads / 32];
+    __shared__ int3 sh[T / 32];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
     __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const WordCounts wc = word_counts(g, bits, t, nrows, wp, s_ntri);
     int3 tot;
-    block_scan3(wc.c, tot, sh);
+    block_scan3<T>(wc.c, tot, sh);
     if (threadIdx.x == 0) {
         agg[blockIdx.x] = make_int4(tot.x, tot.y, tot.z, 0);
         int* s = sup + 4 * (blockIdx.x / kMcGroup);
@@ -279,7 +281,8 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_count_tiles(GridDev g, const 
     }
 }
 
-__global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const unsigned* __restrict__ bits,
+template <int T>
+__global__ void __launch_bounds__(T) k_mc_emit_tiles(GridDev g, const unsigned* __restrict__ bits,
                                                               int nrows, int wp, int ntiles,
                                                               const int4* __restrict__ agg,
                                                               const int4* __restrict__ sup, int* __restrict__ off,
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const u
                                                               int2* __restrict__ wordinfo) {
     pdl_wait();
     __shared__ unsigned char s_ntri[256];
-    __shared__ int3 sh[kMcThreads / 32];
+    __shared__ int3 sh[T / 32];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) s_ntri[k] = (unsigned char)c_ntri[k];
     // the sums of every tile before this one: whole groups, then this group's tiles
     const int tile = blockIdx.x, grp = tile / kMcGroup;
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const u
     }
     __syncthreads();
     int3 base;
-    block_scan3(pre, base, sh);
+    block_scan3<T>(pre, base, sh);
     const int64_t t = (int64_t)tile * blockDim.x + threadIdx.x;
     // a tile the count found empty (most of the grid) has only its rows'
     // offsets to write
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(kMcThreads) k_mc_emit_tiles(GridDev g, const u
     int3 tot = make_int3(0, 0, 0), ex = make_int3(0, 0, 0);
     if ((mine.x | mine.y | mine.z) != 0) {
         wc = word_counts(g, bits, t, nrows, wp, s_ntri);
-        ex = block_scan3(wc.c, tot, sh);
+        ex = block_scan3<T>(wc.c, tot, sh);
     } else {
         wc.act = 0u;
     }
@@ -502,10 +505,11 @@ static int mc_words(int nx) {
     return wp;
 }
 
-// Tiles of kMcThreads (row, word) threads, and where the tile sums and the
+// Tiles of T (row, word) threads (T = the context's marching-cubes tile size),
+// and where the tile sums and the
 // group sums sit in the per-row count buffer (3 x n_rows ints: room for both
 // with up to 16 words per row, every supported grid).
-static int mc_tiles(int nrows, int wp) { return (int)(((int64_t)nrows * wp + kMcThreads - 1) / kMcThreads); }
+static int mc_tiles(int nrows, int wp, int t) { return (int)(((int64_t)nrows * wp + t - 1) / t); }
 static int mc_groups(int ntiles) { return (ntiles + kMcGroup - 1) / kMcGroup; }
 
 // CTAs of the inside-bit pass: one warp per row.  (A grid of one resident
@@ -525,10 +529,26 @@ cudaError_t launch_mc_bits(ftr_ctx* c) {
 
 int mc_words_per_row(int nx) { return mc_words(nx); }
 
+// A launch of the count or emit kernel instantiated for the tile size T.
+template <template <int> class K, class... Args>
+void launch_tiles(int t, int ntiles, cudaStream_t st, Args... args) {
+    switch (t) {
+        case 128: launch_pdl(K<128>::fn, ntiles, 128, 0, st, args...); break;
+        case 512: launch_pdl(K<512>::fn, ntiles, 512, 0, st, args...); break;
+        default: launch_pdl(K<256>::fn, ntiles, 256, 0, st, args...); break;
+    }
+}
+template <int T> struct CountK { static constexpr auto fn = k_mc_count_tiles<T>; };
+template <int T> struct EmitK { static constexpr auto fn = k_mc_emit_tiles<T>; };
+
+bool mc_plan_valid(int tile, int tris_per_sm) {
+    return (tile == 128 || tile == 256 || tile == 512) && tris_per_sm >= 1 && tris_per_sm <= 16;
+}
+
 cudaError_t launch_mc_count(ftr_ctx* c) {
     const int nr = c->mc_blocks;              // grid rows n_y n_z
     const int wp = mc_words(c->g.n[0]);
-    const int ntiles = mc_tiles(nr, wp);
+    const int ntiles = mc_tiles(nr, wp, c->mc_tile);
     if (4 * (ntiles + mc_groups(ntiles)) > 3 * nr) return cudaErrorInvalidValue;
     int4* agg = reinterpret_cast<int4*>(c->d_mc_blk);
     int* sup = c->d_mc_blk + 4 * ntiles;
@@ -536,8 +556,7 @@ cudaError_t launch_mc_count(ftr_ctx* c) {
     launch_pdl(k_mc_bits, mc_bits_grid(nr), kMcThreads, 0, c->stream, c->g, c->d_A, c->d_levelf,
                c->d_mc_bits, nr, wp, sup, 4 * mc_groups(ntiles),
                (const float2*)(c->rowmm_valid ? c->d_rowmm : nullptr));
-    launch_pdl(k_mc_count_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, agg,
-               sup);
+    launch_tiles<CountK>(c->mc_tile, ntiles, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, agg, sup);
     c->launches += 2;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_COUNT);
@@ -557,12 +576,12 @@ cudaError_t launch_mc_totals(ftr_ctx* c) {
 cudaError_t launch_mc_emit(ftr_ctx* c) {
     const int nr = c->mc_blocks;
     const int wp = mc_words(c->g.n[0]);
-    const int ntiles = mc_tiles(nr, wp);
+    const int ntiles = mc_tiles(nr, wp, c->mc_tile);
     const int4* agg = reinterpret_cast<const int4*>(c->d_mc_blk);
     const int4* sup = reinterpret_cast<const int4*>(c->d_mc_blk + 4 * ntiles);
     prof_begin(c, ST_MC_EMIT);
-    launch_pdl(k_mc_emit_tiles, ntiles, kMcThreads, 0, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, ntiles,
-               agg, sup, c->d_mc_off, c->d_mc_nodes, (int)c->cap_mc_nodes, c->d_mc_word);
+    launch_tiles<EmitK>(c->mc_tile, ntiles, c->stream, c->g, (const unsigned*)c->d_mc_bits, nr, wp, ntiles, agg, sup,
+                        c->d_mc_off, c->d_mc_nodes, (int)c->cap_mc_nodes, c->d_mc_word);
     c->launches++;
     cudaError_t e = cudaGetLastError();
     prof_end(c, ST_MC_EMIT);
@@ -570,7 +589,7 @@ cudaError_t launch_mc_emit(ftr_ctx* c) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     prof_begin(c, ST_MC_TRIS);
-    launch_pdl(k_mc_tris, (sms > 0 ? sms : 152) * 4, 256, 0, c->stream, c->g, c->d_A, c->d_levelf, c->d_mc_nodes,
+    launch_pdl(k_mc_tris, (sms > 0 ? sms : 152) * c->mc_tris_per_sm, 256, 0, c->stream, c->g, c->d_A, c->d_levelf, c->d_mc_nodes,
                c->d_mc_off + 3 * (nr + 1), (int)c->cap_mc_nodes, (int)c->cap_tris, (const int2*)c->d_mc_word, wp,
                c->d_tris, c->d_verts, c->d_vnrm, (int)c->cap_verts);
     c->launches++;

@@ -122,6 +122,8 @@ _SIGNATURES = [
     ("ftr_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_get_mc_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ftr_set_mc_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ftr_get_transform_path", ctypes.c_int, [ctypes.c_void_p]),
     ("ftr_set_transform_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ftr_get_field_V", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -432,6 +434,20 @@ def ftr_set_plan(ctx, plan):
     _check(load().ftr_set_plan(ctx, arr.ctypes.data), ctx)
 
 
+def ftr_get_mc_plan(ctx):
+    """(count/emit tile threads, triangle-pass CTAs per SM)."""
+    plan = np.zeros(2, np.int32)
+    _check(load().ftr_get_mc_plan(ctx, plan.ctypes.data), ctx)
+    return tuple(int(v) for v in plan)
+
+
+def ftr_set_mc_plan(ctx, plan):
+    arr = np.ascontiguousarray(plan, dtype=np.int32)
+    if arr.shape != (2,):
+        raise ValueError("ftr_set_mc_plan: two ints (tile threads, triangle CTAs per SM)")
+    _check(load().ftr_set_mc_plan(ctx, arr.ctypes.data), ctx)
+
+
 def ftr_get_transform_path(ctx):
     """0: five axis passes, 1: plane-fused, 2: five passes with the y and z
     passes in one persistent kernel."""
@@ -627,6 +643,12 @@ class Context:
 
     def set_plan(self, plan):
         ftr_set_plan(self.h, plan)
+
+    def mc_plan(self):
+        return ftr_get_mc_plan(self.h)
+
+    def set_mc_plan(self, plan):
+        ftr_set_mc_plan(self.h, plan)
 
     def transform_path(self):
         return ftr_get_transform_path(self.h)

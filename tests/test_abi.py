@@ -92,3 +92,15 @@ def test_estimate_bytes_needs_no_device(lib):
         ftr.ftr_estimate_bytes((100, 256, 256), 0, 0, 0, 0)
     with pytest.raises(ftr.FtrError):
         ftr.ftr_estimate_bytes((256, 256, 256), -1, 0, 0, 0)
+
+
+def test_marching_cubes_plan_arguments_are_checked_without_gpu(lib):
+    """ftr_set_mc_plan takes two ints; the binding refuses other shapes before
+    the library is called (the library's own range check needs a context)."""
+    from paper_1712_03084_gb300 import ftr
+    with pytest.raises(ValueError):
+        ftr.ftr_set_mc_plan(None, (256,))
+    with pytest.raises(ValueError):
+        ftr.ftr_set_mc_plan(None, (256, 4, 1))
+    assert lib.ftr_get_mc_plan(None, None) == -1      # FTR_EINVAL
+    assert lib.ftr_set_mc_plan(None, None) == -1

@@ -166,3 +166,60 @@ def test_autotune_before_the_first_frame_on_reused_memory(ftr):
     ref_p, ref_pL = _field(ftr, "human96", plan, path)
     assert np.array_equal(A, ref_p) and L == ref_pL
     assert G.rel_l2(A, ref) <= 2e-6
+
+
+def _mesh(F, name, mc_plan=None):
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    ctx = F.Context(c["grid"], c["bbox"])
+    if mc_plan is not None:
+        ctx.set_mc_plan(mc_plan)
+    ctx.reset()
+    ctx.splat(P, N, W)
+    ctx.solve()
+    m = ctx.mesh_numpy()
+    ctx.close()
+    return m
+
+
+@pytest.mark.parametrize("name", ["human96", "human_aniso"])
+def test_every_marching_cubes_plan_gives_the_same_mesh(ftr, name):
+    """Count/emit tiles of 128, 256 or 512 threads and 1-16 triangle CTAs per
+    SM: node records, vertex ids and triangles follow node order, so the mesh
+    is bit-identical whatever the block sizes."""
+    ref = _mesh(ftr, name, (256, 4))
+    assert len(ref["vertices"]) > 1000
+    for plan in itertools.product((128, 256, 512), (1, 2, 8, 16)):
+        m = _mesh(ftr, name, plan)
+        for k in ("vertices", "normals", "tris"):
+            assert np.array_equal(m[k], ref[k]), (plan, k)
+
+
+def test_autotune_picks_a_marching_cubes_plan_on_a_meshed_frame(ftr):
+    """The autotuner times the marching-cubes block sizes on the last meshed
+    frame, keeps a valid choice, and the next context of the grid takes it
+    from the cache; the mesh after tuning equals the untuned one.  (A grid
+    that no other test tunes, so that the timing runs here.)"""
+    name = "human_aniso"
+    c = G.CASES[name]
+    P, N, W, _ = G.case_inputs(name)
+    ref = _mesh(ftr, name)
+    ctx = ftr.Context(c["grid"], c["bbox"])
+    ctx.reset()
+    ctx.splat(P, N, W)
+    ctx.solve()
+    ctx.mesh_numpy()
+    ctx.autotune()
+    tile, per_sm = ctx.mc_plan()
+    assert tile in (128, 256, 512) and per_sm in (2, 4, 8)
+    ctx.reset()
+    ctx.splat(P, N, W)
+    ctx.solve()
+    m = ctx.mesh_numpy()
+    ctx.close()
+    for k in ("vertices", "normals", "tris"):
+        assert np.array_equal(m[k], ref[k]), k
+    ctx2 = ftr.Context(c["grid"], c["bbox"])
+    ctx2.autotune()                       # cached: no frame needed
+    assert ctx2.mc_plan() == (tile, per_sm)
+    ctx2.close()
