@@ -16,7 +16,7 @@ constexpr int kBrick = 8;                 // splat accumulation brick edge (node
 constexpr int kBrickVox = kBrick * kBrick * kBrick;
 constexpr int kMaxViews = 8;
 constexpr int kBrickScanTile = 256;   // bricks per tile of the brick-count scan (one block scan per CTA)
-constexpr int kMcThreads = 256;           // marching-cubes CTA size (chunks of 8 grid rows)
+constexpr int kMcThreads = 256;           // CTA size of the inside-bit pass (8 grid rows, a warp each)
 constexpr int kMaxTrisPerCase = 5;
 constexpr int kSplatChunk = 1024;          // (point, brick) pairs per accumulation work unit
 

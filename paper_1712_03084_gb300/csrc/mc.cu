@@ -218,7 +218,8 @@ __device__ __forceinline__ int3 block_scan3(int3 v, int3& total, int3* sh) {
 
 // ------------------------------------------------- tiles: count, then emit
 // Both kernels run over the (row, word) threads in node order in the same
-// tiles of kMcThreads.  The count kernel writes each tile's sums (active
+// tiles of T threads (the context's marching-cubes tile size: 128, 256 or
+// 512; the mesh does not depend on it).  The count kernel writes each tile's sums (active
 // nodes, vertices, triangles) and adds them into its group's sums (256 tiles
 // per group; integer atomics, so the order does not matter).  The emit
 // kernel's tile gets its offset from the groups before it and the tiles
