@@ -94,6 +94,21 @@ def test_estimate_bytes_needs_no_device(lib):
         ftr.ftr_estimate_bytes((256, 256, 256), -1, 0, 0, 0)
 
 
+def test_estimate_per_point_terms_scale_with_the_frame(lib):
+    """The point-dependent buffers (point store, (point, brick) pairs, work
+    units, heavy-brick accumulators) follow the frame's point count: a
+    10,000-point frame adds a few MB to a 96^3 context, not the tens of MB
+    that accumulators sized for the minimum pair capacity would take, and a
+    frame 16x larger adds about 16x as much."""
+    from paper_1712_03084_gb300 import ftr
+    g = (96, 96, 96)
+    base = ftr.ftr_estimate_bytes(g, 0, 0, 0, 0)
+    small = ftr.ftr_estimate_bytes(g, 10000, 0, 0, 0) - base
+    big = ftr.ftr_estimate_bytes(g, 160000, 0, 0, 0) - base
+    assert 0 < small < 8 << 20
+    assert 8 * small < big < 32 * small
+
+
 def test_marching_cubes_plan_arguments_are_checked_without_gpu(lib):
     """ftr_set_mc_plan takes two ints; the binding refuses other shapes before
     the library is called (the library's own range check needs a context)."""
